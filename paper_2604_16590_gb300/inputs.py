@@ -1,0 +1,94 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds no arithmetic of the attention method: it only draws
+random tensors and names the workloads.  Both the oracle-based tests and the
+CUDA path take their inputs from here, so the two sides see the same bytes.
+
+The paper measures on ERA5 and HRRR reanalysis tensors (Sec. IV, Datasets),
+which are not available here; the synthetic stand-ins below keep the paper's
+shapes (patch-token grids of frames x latitude x longitude, Tab. III(a) uses a
+32 x 64 spatial grid with long temporal context) with iid Gaussian Q, K, V.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+
+@dataclass(frozen=True)
+class Workload:
+    """One synthetic GPA workload: grid, tile spec, heads and input law."""
+
+    name: str
+    B: int
+    nh: int
+    d: int
+    grid: tuple  # (T, Y, X)
+    core: tuple  # (c_t, c_y, c_x)
+    halo: tuple  # (h_t, h_y, h_x)
+    std: float = 1.0
+    seed: int = 0
+    dtype: str = "fp32"  # input dtype: "fp32" or "bf16"
+    notes: str = field(default="", compare=False)
+
+    @property
+    def N(self) -> int:
+        T, Y, X = self.grid
+        return T * Y * X
+
+    @property
+    def shape(self):
+        return (self.B, self.nh, self.N, self.d)
+
+
+# The workloads the library is measured and checked on.
+WORKLOADS = {
+    # plain method, forward: 64 x 64 single frame, 16 tiles of 16 x 16 with a 4-token halo
+    "c1_4k": Workload("c1_4k", 1, 1, 64, (1, 64, 64), (1, 16, 16), (0, 4, 4), 1.0, 20261, "fp32"),
+    # 32 frames x 64 x 128 patch grid, Tiles = 16 (paper regime): core 32 x 16 x 32, halo 0/4/8
+    "c2_262k_p": Workload("c2_262k_p", 4, 16, 64, (32, 64, 128), (32, 16, 32), (0, 4, 8), 0.5, 20262, "bf16"),
+    # same grid, small tiles near the HBM/tensor ridge: core 1 x 16 x 16, halo 0/4/4
+    "c2_262k_s": Workload("c2_262k_s", 4, 16, 64, (32, 64, 128), (1, 16, 16), (0, 4, 4), 0.5, 20262, "bf16"),
+    # long temporal context: 2048 frames x 32 x 64, d = 128, Tiles = 16 along time, halo 8 frames
+    "c3_4m_p": Workload("c3_4m_p", 1, 8, 128, (2048, 32, 64), (128, 32, 64), (8, 0, 0), 0.5, 20263, "bf16"),
+    # gradient check size: 32 x 32, 2 heads, d = 32
+    "c4_grad": Workload("c4_grad", 1, 2, 32, (1, 32, 32), (1, 16, 16), (0, 4, 4), 1.0, 20264, "fp32"),
+    # backward throughput: 16 x 256 x 256, 8 heads, Tiles = 16
+    "c4_1m_p": Workload("c4_1m_p", 1, 8, 64, (16, 256, 256), (16, 64, 64), (0, 8, 8), 0.5, 20264, "bf16"),
+}
+
+
+def qkv(shape, seed: int, std: float = 1.0, dtype: str = "fp32", device="cpu", n: int = 3):
+    """n iid N(0, std^2) tensors of `shape` from one seeded generator.
+
+    dtype "bf16" rounds the fp32 draws to bfloat16 (round to nearest even) and
+    returns bfloat16 tensors; "fp32" returns the fp32 draws.
+    """
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    out = []
+    for _ in range(n):
+        t = torch.randn(shape, generator=gen, device=device, dtype=torch.float32)
+        if std != 1.0:
+            t.mul_(std)
+        if dtype == "bf16":
+            t = t.to(torch.bfloat16)
+        elif dtype != "fp32":
+            raise ValueError(dtype)
+        out.append(t)
+    return out
+
+
+def upstream_grad(shape, seed: int, dtype: str = "fp32", device="cpu"):
+    """dOut ~ iid N(0, 1), seeded independently of Q, K, V."""
+    (g,) = qkv(shape, seed + 7919, 1.0, dtype, device, n=1)
+    return g
+
+
+def workload_inputs(w: Workload, device="cpu", with_grad: bool = True):
+    """(q, k, v[, dout]) for a named workload."""
+    q, k, v = qkv(w.shape, w.seed, w.std, w.dtype, device)
+    if not with_grad:
+        return q, k, v
+    return q, k, v, upstream_grad(w.shape, w.seed, w.dtype, device)
