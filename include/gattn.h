@@ -1,0 +1,167 @@
+/*
+ * gattn.h -- C ABI of the GB300 (sm_103a) STORM global propagation attention
+ * library (STORM-GPA, arXiv 2604.16590, Sec. III-C "STORM-GPA:
+ * Linear-Complexity Global Attention", Fig. 3(a)).
+ *
+ * The operator.  Tokens live on a (T, Y, X) grid of frames x latitude x
+ * longitude patches; N = T*Y*X and token i = (t*Y + y)*X + x.  The grid is
+ * cut into tiles of core size core[3]; each tile is extended by halo[3]
+ * tokens on both sides of every dimension (clipped to the grid), so that
+ * neighbouring extended tiles overlap (Sec. III-C, first two paragraphs).
+ * Softmax attention runs independently inside every extended tile, every
+ * token of the tile being both a query and a key/value (Sec. III-C: interior
+ * tokens attend to halo tokens; Sec. III-D Level 5: FlashAttention inside a
+ * tile).  Where extended tiles overlap, the per-tile outputs are averaged
+ * with Hanning weights that trust tile centres more than tile edges
+ * (Sec. III-C, "average denoised outputs in overlapping halos" and the
+ * closing sentence on the Hanning window):
+ *
+ *     O_t(i)  = sum_{j in E_t} softmax_j(s q_i.k_j) v_j          (i in E_t)
+ *     Out(i)  = sum_{t : i in E_t} w_t(i) O_t(i) / sum_t w_t(i)
+ *     w_t(i)  = prod_a sin^2(pi (n_a + 1/2) / (c_a + 2 h_a))
+ *
+ * with n_a the offset of i from the nominal (unclipped) start k_a c_a - h_a
+ * of tile t in dimension a; a dimension with a single tile and no halo
+ * contributes weight 1.  The paper does not print the window; this
+ * half-sample Hann (strictly positive, symmetric) is the reading taken, and
+ * window = GATTN_WINDOW_FLAT gives a plain mean.  One tile with no halo is
+ * exact global softmax attention (Sec. IV-B: Tiles = 1 is STORM-DiT
+ * without GPA).  The cost is linear in N for a fixed tile size.
+ *
+ * Memory layout: Q, K, V, Out, dOut, dQ, dK, dV are dense [B, nh, N, d]
+ * row-major tensors (d contiguous), 16-byte aligned, in device memory owned
+ * by the caller.  The library allocates nothing on the fwd/bwd path: the
+ * caller passes the saved-state and workspace buffers, sized by the query
+ * functions below.  Every call is asynchronous on the given CUDA stream.
+ *
+ * Errors.  Argument and shape errors are returned synchronously, before any
+ * launch.  A failed launch returns GATTN_ERR_CUDA.  Device-side conditions
+ * (a bounded wait that ran out, a debug bounds check) set a per-library
+ * device status word and the kernel exits cleanly; gattn_stream_status()
+ * synchronises the stream and reports and clears that word.
+ */
+#ifndef GATTN_H
+#define GATTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *gattn_stream_t;
+
+typedef enum {
+  GATTN_OK = 0,
+  GATTN_ERR_INVALID_ARG = 1,   /* NULL pointer, bad shape, misaligned pointer */
+  GATTN_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  GATTN_ERR_WORKSPACE = 3,     /* saved/workspace buffer smaller than required */
+  GATTN_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed */
+  GATTN_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+  GATTN_ERR_OOM = 6,           /* serving: request does not fit the HBM budget */
+  GATTN_ERR_BUSY = 7,          /* serving: no free slot */
+  GATTN_ERR_DEVICE_BOUNDS = 8, /* debug bounds check tripped on the device */
+  GATTN_ERR_NOT_FOUND = 9      /* serving: unknown request id */
+} gattn_status;
+
+typedef enum { GATTN_BF16 = 0, GATTN_FP32 = 1 } gattn_dtype;
+typedef enum { GATTN_WINDOW_HANN = 0, GATTN_WINDOW_FLAT = 1 } gattn_window;
+
+/* flags */
+#define GATTN_FLAG_DEBUG_BOUNDS 0x1u /* device-side index checks on global accesses */
+
+/*
+ * Problem descriptor.
+ *   B, nh, d      batch, heads, head dim.  d in {32, 64, 128} for FP32 inputs,
+ *                 d in {64, 128} for BF16 inputs (tensor-core path).
+ *   T, Y, X       token grid; N = T*Y*X < 2^31.
+ *   core[3]       tile core size along (t, y, x), each >= 1; the last tile of a
+ *                 dimension may be short when the grid is not a multiple.
+ *   halo[3]       halo width along (t, y, x), each >= 0.
+ *   window        gattn_window.
+ *   in_dtype      dtype of Q, K, V and dOut.  GATTN_BF16 runs the tcgen05
+ *                 tensor-core kernels (FP32 accumulation in TMEM);
+ *                 GATTN_FP32 runs the plain FP32 SIMT kernels.
+ *   out_dtype     dtype of Out, dQ, dK, dV (BF16 or FP32).
+ *   scale         softmax scale s; 0 means 1/sqrt(d).
+ *   flags         GATTN_FLAG_*.
+ */
+typedef struct {
+  int32_t B, nh, d;
+  int32_t T, Y, X;
+  int32_t core[3];
+  int32_t halo[3];
+  int32_t window;
+  int32_t in_dtype;
+  int32_t out_dtype;
+  float scale;
+  uint32_t flags;
+} gattn_desc;
+
+/* Version of this ABI (bumped on any incompatible change). */
+int32_t gattn_abi_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *gattn_status_string(gattn_status s);
+
+/* Checks a descriptor without touching the GPU. */
+gattn_status gattn_validate(const gattn_desc *desc);
+
+/* Number of tiles, prod_a ceil(G_a / core_a). Negative on an invalid desc. */
+int64_t gattn_num_tiles(const gattn_desc *desc);
+
+/*
+ * Bytes of the saved-state buffer that gattn_fwd fills and gattn_bwd reads:
+ * the per-(tile, row) log-sum-exp of every extended-tile row, and the FP32
+ * per-tile outputs O_t of the rows covered by more than one tile (the
+ * operands of the Hann-weighted merge).  Returns 0 on an invalid desc.
+ */
+size_t gattn_saved_bytes(const gattn_desc *desc);
+
+/* Bytes of the backward workspace (per-row softmax statistics and the FP32
+ * per-tile gradients of multiply-covered rows).  0 on an invalid desc. */
+size_t gattn_bwd_workspace_bytes(const gattn_desc *desc);
+
+/*
+ * Forward: out = GPA(q, k, v).
+ *   q, k, v   [B, nh, N, d] in in_dtype (device).
+ *   out       [B, nh, N, d] in out_dtype (device), fully overwritten.
+ *   saved     device buffer of at least gattn_saved_bytes(desc) bytes; its
+ *             contents after the call are what gattn_bwd needs.
+ * Launches: the tile-attention kernel (tcgen05 for BF16, SIMT for FP32),
+ * then the deterministic merge of multiply-covered tokens (fixed ascending
+ * tile order; no atomics, bitwise reproducible).
+ */
+gattn_status gattn_fwd(const gattn_desc *desc, const void *q, const void *k, const void *v,
+                       void *out, void *saved, size_t saved_bytes, gattn_stream_t stream);
+
+/*
+ * Backward of the loss sum(out * dout):
+ *   q, k, v   the forward's inputs (in_dtype);
+ *   out       the forward's output (out_dtype);
+ *   dout      upstream gradient [B, nh, N, d] in in_dtype;
+ *   saved     the buffer the forward filled (unchanged since);
+ *   dq,dk,dv  [B, nh, N, d] in out_dtype, fully overwritten;
+ *   ws        device workspace of at least gattn_bwd_workspace_bytes(desc).
+ * Per tile: dO_t = (w_t / sum w) dout, P recomputed from the saved
+ * log-sum-exp (never stored), dV_t = P^T dO_t, dS = P (dO_t V^T - D),
+ * dQ_t = s dS K, dK_t = s dS^T Q; each input gradient is the fixed-order sum
+ * of its tiles' contributions (deterministic, no atomics).
+ */
+gattn_status gattn_bwd(const gattn_desc *desc, const void *q, const void *k, const void *v,
+                       const void *out, const void *dout, const void *saved, size_t saved_bytes,
+                       void *dq, void *dk, void *dv, void *ws, size_t ws_bytes,
+                       gattn_stream_t stream);
+
+/* Synchronises `stream`, then returns (and clears) the device status word of
+ * this library on the current device: GATTN_OK, GATTN_ERR_TIMEOUT or
+ * GATTN_ERR_DEVICE_BOUNDS; GATTN_ERR_CUDA if the stream reported an error. */
+gattn_status gattn_stream_status(gattn_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GATTN_H */

@@ -1,0 +1,184 @@
+// gattn_abi.cu -- the C ABI of libgattn (declared in include/gattn.h):
+// descriptor validation, buffer sizing and the launch sequence of the
+// forward and backward of STORM-GPA (arXiv 2604.16590, Sec. III-C).
+#include <math.h>
+#include <string.h>
+
+#include "internal.cuh"
+
+namespace gattn {
+
+static bool dtype_ok(int32_t t) { return t == GATTN_BF16 || t == GATTN_FP32; }
+
+bool make_geom(const gattn_desc* desc, Geom* g) {
+  if (!desc || !g) return false;
+  memset(g, 0, sizeof(*g));
+  const gattn_desc& d = *desc;
+  if (d.B < 1 || d.nh < 1 || d.T < 1 || d.Y < 1 || d.X < 1) return false;
+  if (!dtype_ok(d.in_dtype) || !dtype_ok(d.out_dtype)) return false;
+  if (d.window != GATTN_WINDOW_HANN && d.window != GATTN_WINDOW_FLAT) return false;
+  if (d.in_dtype == GATTN_FP32 && d.d != 32 && d.d != 64 && d.d != 128) return false;
+  if (d.in_dtype == GATTN_BF16 && d.d != 64 && d.d != 128) return false;
+  if (!(d.scale >= 0.f) || !isfinite(d.scale)) return false;
+  const int64_t N = (int64_t)d.T * d.Y * d.X;
+  if (N >= (1LL << 31)) return false;
+  g->B = d.B;
+  g->nh = d.nh;
+  g->d = d.d;
+  g->G[0] = d.T;
+  g->G[1] = d.Y;
+  g->G[2] = d.X;
+  g->N = N;
+  int64_t ntiles = 1, Lmax = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (d.core[a] < 1 || d.halo[a] < 0 || d.halo[a] > (1 << 24)) return false;
+    g->c[a] = d.core[a];
+    g->h[a] = d.halo[a];
+    g->n[a] = (g->G[a] + g->c[a] - 1) / g->c[a];
+    int emax = 0;
+    for (int k = 0; k < g->n[a]; ++k) {
+      int lo = k * g->c[a] - g->h[a], hi = (k + 1) * g->c[a] + g->h[a];
+      lo = lo < 0 ? 0 : lo;
+      hi = hi > g->G[a] ? g->G[a] : hi;
+      emax = hi - lo > emax ? hi - lo : emax;
+    }
+    g->emax[a] = emax;
+    g->tiled[a] = (g->n[a] > 1 || g->h[a] > 0) ? 1 : 0;
+    ntiles *= g->n[a];
+    Lmax *= emax;
+  }
+  if (ntiles > 65535 || Lmax >= (1LL << 31)) return false;
+  if ((int64_t)d.B * d.nh > 65535) return false;
+  g->ntiles = (int32_t)ntiles;
+  g->Lmax = (int32_t)Lmax;
+  g->window = d.window;
+  g->scale = d.scale > 0.f ? d.scale : 1.0f / sqrtf((float)d.d);
+  g->scale_log2 = g->scale * 1.4426950408889634f;
+  return true;
+}
+
+// Some token is covered by more than one tile (a tiled dimension with a halo).
+static bool has_overlap(const Geom& g) {
+  for (int a = 0; a < 3; ++a)
+    if (g.n[a] > 1 && g.h[a] > 0) return true;
+  return false;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static gattn_status from_cuda(cudaError_t e) { return e == cudaSuccess ? GATTN_OK : GATTN_ERR_CUDA; }
+
+}  // namespace gattn
+
+using namespace gattn;
+
+extern "C" {
+
+int32_t gattn_abi_version(void) { return 1; }
+
+const char* gattn_status_string(gattn_status s) {
+  switch (s) {
+    case GATTN_OK: return "ok";
+    case GATTN_ERR_INVALID_ARG: return "invalid argument";
+    case GATTN_ERR_UNSUPPORTED: return "unsupported";
+    case GATTN_ERR_WORKSPACE: return "saved/workspace buffer too small";
+    case GATTN_ERR_CUDA: return "CUDA error";
+    case GATTN_ERR_TIMEOUT: return "device wait timed out";
+    case GATTN_ERR_OOM: return "request exceeds the HBM budget";
+    case GATTN_ERR_BUSY: return "no free slot";
+    case GATTN_ERR_DEVICE_BOUNDS: return "device bounds check failed";
+    case GATTN_ERR_NOT_FOUND: return "unknown request";
+  }
+  return "unknown status";
+}
+
+gattn_status gattn_validate(const gattn_desc* desc) {
+  Geom g;
+  return make_geom(desc, &g) ? GATTN_OK : GATTN_ERR_INVALID_ARG;
+}
+
+int64_t gattn_num_tiles(const gattn_desc* desc) {
+  Geom g;
+  return make_geom(desc, &g) ? (int64_t)g.ntiles : -1;
+}
+
+size_t gattn_saved_bytes(const gattn_desc* desc) {
+  Geom g;
+  return make_geom(desc, &g) ? saved_layout(g).bytes : 0;
+}
+
+size_t gattn_bwd_workspace_bytes(const gattn_desc* desc) {
+  Geom g;
+  return make_geom(desc, &g) ? bwd_layout(g).bytes : 0;
+}
+
+gattn_status gattn_fwd(const gattn_desc* desc, const void* q, const void* k, const void* v, void* out,
+                       void* saved, size_t saved_bytes, gattn_stream_t stream) {
+  Geom g;
+  if (!make_geom(desc, &g)) return GATTN_ERR_INVALID_ARG;
+  if (!q || !k || !v || !out || !saved) return GATTN_ERR_INVALID_ARG;
+  if (!aligned16(q) || !aligned16(k) || !aligned16(v) || !aligned16(out) || !aligned16(saved))
+    return GATTN_ERR_INVALID_ARG;
+  const SavedLayout sl = saved_layout(g);
+  if (saved_bytes < sl.bytes) return GATTN_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  float* lse2 = reinterpret_cast<float*>(static_cast<char*>(saved) + sl.lse_off);
+  float* ot = reinterpret_cast<float*>(static_cast<char*>(saved) + sl.ot_off);
+  cudaError_t e;
+  if (desc->in_dtype == GATTN_FP32)
+    e = launch_simt_fwd(g, (const float*)q, (const float*)k, (const float*)v, out, desc->out_dtype, lse2, ot, st);
+  else
+    e = launch_sm103_fwd(g, (const __nv_bfloat16*)q, (const __nv_bfloat16*)k, (const __nv_bfloat16*)v, out,
+                         desc->out_dtype, lse2, ot, desc->flags, st);
+  if (e == cudaErrorNotSupported) return GATTN_ERR_UNSUPPORTED;
+  if (e != cudaSuccess) return GATTN_ERR_CUDA;
+  if (has_overlap(g)) e = launch_merge_fwd(g, ot, out, desc->out_dtype, st);
+  return from_cuda(e);
+}
+
+gattn_status gattn_bwd(const gattn_desc* desc, const void* q, const void* k, const void* v, const void* out,
+                       const void* dout, const void* saved, size_t saved_bytes, void* dq, void* dk, void* dv,
+                       void* ws, size_t ws_bytes, gattn_stream_t stream) {
+  Geom g;
+  if (!make_geom(desc, &g)) return GATTN_ERR_INVALID_ARG;
+  const void* ptrs[] = {q, k, v, out, dout, saved, dq, dk, dv, ws};
+  for (const void* p : ptrs)
+    if (!p || !aligned16(p)) return GATTN_ERR_INVALID_ARG;
+  const SavedLayout sl = saved_layout(g);
+  const BwdLayout bl = bwd_layout(g);
+  if (saved_bytes < sl.bytes || ws_bytes < bl.bytes) return GATTN_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const float* lse2 = reinterpret_cast<const float*>(static_cast<const char*>(saved) + sl.lse_off);
+  const float* ot = reinterpret_cast<const float*>(static_cast<const char*>(saved) + sl.ot_off);
+  char* w = static_cast<char*>(ws);
+  float* lse2c = reinterpret_cast<float*>(w + bl.lse_off);
+  float* dd = reinterpret_cast<float*>(w + bl.dd_off);
+  float* dq_s = reinterpret_cast<float*>(w + bl.dq_off);
+  float* dk_s = reinterpret_cast<float*>(w + bl.dk_off);
+  float* dv_s = reinterpret_cast<float*>(w + bl.dv_off);
+  cudaError_t e = launch_bwd_prep(g, out, desc->out_dtype, dout, desc->in_dtype, lse2, ot, lse2c, dd, st);
+  if (e != cudaSuccess) return GATTN_ERR_CUDA;
+  if (desc->in_dtype == GATTN_FP32)
+    e = launch_simt_bwd(g, (const float*)q, (const float*)k, (const float*)v, (const float*)dout, lse2c, dd, dq, dk,
+                        dv, desc->out_dtype, dq_s, dk_s, dv_s, st);
+  else
+    e = launch_sm103_bwd(g, (const __nv_bfloat16*)q, (const __nv_bfloat16*)k, (const __nv_bfloat16*)v,
+                         (const __nv_bfloat16*)dout, lse2c, dd, dq, dk, dv, desc->out_dtype, dq_s, dk_s, dv_s,
+                         desc->flags, st);
+  if (e == cudaErrorNotSupported) return GATTN_ERR_UNSUPPORTED;
+  if (e != cudaSuccess) return GATTN_ERR_CUDA;
+  if (has_overlap(g)) e = launch_merge_bwd(g, dq_s, dk_s, dv_s, dq, dk, dv, desc->out_dtype, st);
+  return from_cuda(e);
+}
+
+gattn_status gattn_stream_status(gattn_stream_t stream) {
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return GATTN_ERR_CUDA;
+  uint32_t words[] = {fetch_status_simt(), fetch_status_merge(), fetch_status_sm103_fwd(), fetch_status_sm103_bwd()};
+  for (uint32_t w : words)
+    if (w == ~0u) return GATTN_ERR_CUDA;
+  for (uint32_t w : words)
+    if (w) return (gattn_status)w;
+  return GATTN_OK;
+}
+
+}  // extern "C"

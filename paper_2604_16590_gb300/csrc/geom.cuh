@@ -1,0 +1,130 @@
+// geom.cuh -- tile geometry of STORM-GPA shared by every kernel of the library
+// (arXiv 2604.16590, Sec. III-C: tiles, halos, Hann-weighted overlap average).
+//
+// Grid (T, Y, X) = G[0..2]; core c[a], halo h[a]; n[a] = ceil(G[a]/c[a]) tiles
+// per dimension; tile index = (k_t * n_y + k_y) * n_x + k_x (so ascending tile
+// index is the fixed merge order).  Extended interval of tile k along a:
+// [max(k c - h, 0), min((k+1) c + h, G)).  Rows of an extended tile are
+// numbered r = (lt * e_y + ly) * e_x + lx over its clipped extents e[3].
+// Per-(tile, row) state (log-sum-exp, per-tile outputs, softmax statistics)
+// lives at slot ((bh * ntiles + tile) * Lmax + r), Lmax = prod_a max_k e_a(k).
+#pragma once
+
+#include <stdint.h>
+
+#include "gattn.h"
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#define __forceinline__ inline
+#endif
+
+namespace gattn {
+
+struct Geom {
+  int32_t B, nh, d;
+  int32_t G[3];     // T, Y, X
+  int32_t c[3];     // core
+  int32_t h[3];     // halo
+  int32_t n[3];     // tiles per dimension
+  int32_t emax[3];  // largest clipped extended extent per dimension
+  int32_t tiled[3]; // 0: dimension has one tile and no halo (window factor 1)
+  int32_t ntiles;
+  int32_t Lmax;
+  int32_t window;   // gattn_window
+  int64_t N;
+  float scale;      // softmax scale s
+  float scale_log2; // s * log2(e)
+};
+
+__host__ __device__ __forceinline__ int floordiv(int a, int b) {
+  int q = a / b;
+  return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+struct TileBox {
+  int lo[3];
+  int e[3];
+  int L;
+};
+
+__host__ __device__ __forceinline__ void tile_box(const Geom& g, int tile, TileBox& tb) {
+  int k[3];
+  k[2] = tile % g.n[2];
+  k[1] = (tile / g.n[2]) % g.n[1];
+  k[0] = tile / (g.n[2] * g.n[1]);
+  tb.L = 1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int lo = k[a] * g.c[a] - g.h[a];
+    int hi = (k[a] + 1) * g.c[a] + g.h[a];
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > g.G[a] ? g.G[a] : hi;
+    tb.lo[a] = lo;
+    tb.e[a] = hi - lo;
+    tb.L *= tb.e[a];
+  }
+}
+
+// grid token index of row r of the extended tile
+__host__ __device__ __forceinline__ int64_t tile_token(const Geom& g, const TileBox& tb, int r) {
+  int lx = r % tb.e[2];
+  int rr = r / tb.e[2];
+  int ly = rr % tb.e[1];
+  int lt = rr / tb.e[1];
+  return ((int64_t)(tb.lo[0] + lt) * g.G[1] + (tb.lo[1] + ly)) * g.G[2] + (tb.lo[2] + lx);
+}
+
+__host__ __device__ __forceinline__ void token_pos(const Geom& g, int64_t i, int p[3]) {
+  p[2] = (int)(i % g.G[2]);
+  int64_t r = i / g.G[2];
+  p[1] = (int)(r % g.G[1]);
+  p[0] = (int)(r / g.G[1]);
+}
+
+// tiles along dimension a that cover grid position p: [k0, k1]
+__host__ __device__ __forceinline__ void cover_dim(const Geom& g, int a, int p, int& k0, int& k1) {
+  k0 = floordiv(p - g.h[a], g.c[a]);
+  k1 = floordiv(p + g.h[a], g.c[a]);
+  k0 = k0 < 0 ? 0 : k0;
+  k1 = k1 > g.n[a] - 1 ? g.n[a] - 1 : k1;
+}
+
+// true if exactly one tile covers grid position p
+__host__ __device__ __forceinline__ bool single_cover(const Geom& g, const int p[3]) {
+  bool one = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int k0, k1;
+    cover_dim(g, a, p[a], k0, k1);
+    one = one && (k0 == k1);
+  }
+  return one;
+}
+
+__host__ __device__ __forceinline__ int64_t slot_index(const Geom& g, int bh, int tile, int r) {
+  return ((int64_t)bh * g.ntiles + tile) * g.Lmax + r;
+}
+
+#ifdef __CUDACC__
+// Window factor of tile index k along dimension a at grid position p:
+// sin^2(pi (n + 1/2) / M), n = p - (k c - h), M = c + 2h (half-sample Hann).
+__device__ __forceinline__ float window_dim(const Geom& g, int a, int p, int k) {
+  if (g.window == GATTN_WINDOW_FLAT || !g.tiled[a]) return 1.0f;
+  int n = p - (k * g.c[a] - g.h[a]);
+  int M = g.c[a] + 2 * g.h[a];
+  float s = sinpif(((float)n + 0.5f) / (float)M);
+  return s * s;
+}
+
+// w_t(p) for the tile with per-dimension indices k[3]
+__device__ __forceinline__ float tile_weight(const Geom& g, const int p[3], const int k[3]) {
+  return window_dim(g, 0, p[0], k[0]) * window_dim(g, 1, p[1], k[1]) * window_dim(g, 2, p[2], k[2]);
+}
+#endif
+
+// Host-side construction; returns false on an invalid descriptor.
+bool make_geom(const gattn_desc* desc, Geom* g);
+
+}  // namespace gattn

@@ -1,0 +1,130 @@
+// internal.cuh -- buffer layouts, device status word and launcher declarations
+// shared by the translation units of libgattn.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "geom.cuh"
+
+namespace gattn {
+
+constexpr size_t kAlign = 256;
+__host__ __device__ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Saved state written by the forward, read by the backward.
+//   lse2 : float[S]     log2-domain log-sum-exp of every (tile, row) slot
+//   ot   : float[S * d] per-tile output O_t of rows covered by >1 tile
+// S = B * nh * ntiles * Lmax.
+struct SavedLayout {
+  size_t S, lse_off, ot_off, bytes;
+};
+inline SavedLayout saved_layout(const Geom& g) {
+  SavedLayout s;
+  s.S = (size_t)g.B * g.nh * g.ntiles * g.Lmax;
+  s.lse_off = 0;
+  s.ot_off = align_up(s.S * sizeof(float));
+  s.bytes = s.ot_off + align_up(s.S * g.d * sizeof(float));
+  return s;
+}
+
+// Backward workspace.
+//   lse2c : float[S]      log2-domain LSE minus log2(w_t / sum w) (folds dO_t scaling into P)
+//   dd    : float[S]      D = dOut . O_t per slot
+//   dq_s, dk_s, dv_s : float[S * d]  per-tile gradients of multiply-covered rows
+struct BwdLayout {
+  size_t S, lse_off, dd_off, dq_off, dk_off, dv_off, bytes;
+};
+inline BwdLayout bwd_layout(const Geom& g) {
+  BwdLayout b;
+  b.S = (size_t)g.B * g.nh * g.ntiles * g.Lmax;
+  size_t vec = align_up(b.S * sizeof(float));
+  size_t mat = align_up(b.S * g.d * sizeof(float));
+  b.lse_off = 0;
+  b.dd_off = vec;
+  b.dq_off = 2 * vec;
+  b.dk_off = b.dq_off + mat;
+  b.dv_off = b.dk_off + mat;
+  b.bytes = b.dv_off + mat;
+  return b;
+}
+
+// Device status codes (subset of gattn_status) set by kernels.
+enum : uint32_t { kStatusOk = 0, kStatusTimeout = GATTN_ERR_TIMEOUT, kStatusBounds = GATTN_ERR_DEVICE_BOUNDS };
+
+// One status word per translation unit; the ABI reads and clears all of them.
+#define GATTN_DEFINE_STATUS(NAME)                                                       \
+  static __device__ uint32_t g_status_word;                                             \
+  static __device__ __forceinline__ void set_status(uint32_t code) {                    \
+    atomicCAS(&g_status_word, 0u, code);                                                \
+  }                                                                                     \
+  namespace gattn {                                                                     \
+  uint32_t fetch_status_##NAME() {                                                      \
+    uint32_t v = 0, z = 0;                                                              \
+    if (cudaMemcpyFromSymbol(&v, g_status_word, sizeof(v)) != cudaSuccess) return ~0u;  \
+    if (v) cudaMemcpyToSymbol(g_status_word, &z, sizeof(z));                            \
+    return v;                                                                           \
+  }                                                                                     \
+  }
+
+uint32_t fetch_status_simt();
+uint32_t fetch_status_merge();
+uint32_t fetch_status_sm103_fwd();
+uint32_t fetch_status_sm103_bwd();
+
+// ---- launchers (return cudaGetLastError() of their launches)
+cudaError_t launch_simt_fwd(const Geom& g, const float* q, const float* k, const float* v, void* out,
+                            int out_dtype, float* lse2, float* ot, cudaStream_t st);
+cudaError_t launch_simt_bwd(const Geom& g, const float* q, const float* k, const float* v,
+                            const float* dout, const float* lse2c, const float* dd, void* dq, void* dk,
+                            void* dv, int out_dtype, float* dq_s, float* dk_s, float* dv_s,
+                            cudaStream_t st);
+cudaError_t launch_merge_fwd(const Geom& g, const float* ot, void* out, int out_dtype, cudaStream_t st);
+cudaError_t launch_bwd_prep(const Geom& g, const void* out, int out_dtype, const void* dout,
+                            int in_dtype, const float* lse2, const float* ot, float* lse2c, float* dd,
+                            cudaStream_t st);
+cudaError_t launch_merge_bwd(const Geom& g, const float* dq_s, const float* dk_s, const float* dv_s,
+                             void* dq, void* dk, void* dv, int out_dtype, cudaStream_t st);
+cudaError_t launch_sm103_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k,
+                             const __nv_bfloat16* v, void* out, int out_dtype, float* lse2, float* ot,
+                             uint32_t flags, cudaStream_t st);
+cudaError_t launch_sm103_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k,
+                             const __nv_bfloat16* v, const __nv_bfloat16* dout, const float* lse2c,
+                             const float* dd, void* dq, void* dk, void* dv, int out_dtype, float* dq_s,
+                             float* dk_s, float* dv_s, uint32_t flags, cudaStream_t st);
+
+// ---- small device helpers
+#ifdef __CUDACC__
+template <typename T>
+__device__ __forceinline__ void store4(T* p, float4 v);
+template <>
+__device__ __forceinline__ void store4<float>(float* p, float4 v) {
+  *reinterpret_cast<float4*>(p) = v;
+}
+template <>
+__device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16* p, float4 v) {
+  __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+  __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+  uint2 u;
+  u.x = *reinterpret_cast<uint32_t*>(&a);
+  u.y = *reinterpret_cast<uint32_t*>(&b);
+  *reinterpret_cast<uint2*>(p) = u;
+}
+template <typename T>
+__device__ __forceinline__ float4 load4(const T* p);
+template <>
+__device__ __forceinline__ float4 load4<float>(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+template <>
+__device__ __forceinline__ float4 load4<__nv_bfloat16>(const __nv_bfloat16* p) {
+  uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&u.x);
+  __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&u.y);
+  float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+  return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+#endif
+
+}  // namespace gattn

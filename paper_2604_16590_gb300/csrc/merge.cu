@@ -1,0 +1,233 @@
+// merge.cu -- the Hann-weighted overlap average of STORM-GPA (arXiv 2604.16590,
+// Sec. III-C "average denoised outputs in overlapping halos" + Hanning window)
+// and its backward counterparts.  Shared by the BF16 and FP32 forms.
+//
+// The tile kernels write rows covered by a single tile straight into the
+// output tensor and park the FP32 per-tile value of every multiply-covered row
+// in a (tile, row) slot.  These kernels finish the multiply-covered tokens by
+// visiting their covering tiles in ascending tile order (fixed order, no
+// atomics: bitwise reproducible run to run).
+#include "internal.cuh"
+
+GATTN_DEFINE_STATUS(merge)
+
+namespace gattn {
+namespace {
+
+constexpr int kThreads = 256;
+
+// Token position and, per dimension, the covering tile range and the clipped
+// extended box origin/extents needed to find the token's row in each tile.
+struct Cover {
+  int p[3];
+  int k0[3], k1[3];
+};
+
+__device__ __forceinline__ bool cover_of(const Geom& g, int64_t i, Cover& c) {
+  token_pos(g, i, c.p);
+  bool multi = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cover_dim(g, a, c.p[a], c.k0[a], c.k1[a]);
+    multi = multi || (c.k1[a] > c.k0[a]);
+  }
+  return multi;
+}
+
+// row of grid position p inside tile (k[0], k[1], k[2])
+__device__ __forceinline__ int row_in_tile(const Geom& g, const int p[3], const int k[3], int* tile) {
+  int lo[3], e[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int l = k[a] * g.c[a] - g.h[a];
+    int h = (k[a] + 1) * g.c[a] + g.h[a];
+    l = l < 0 ? 0 : l;
+    h = h > g.G[a] ? g.G[a] : h;
+    lo[a] = l;
+    e[a] = h - l;
+  }
+  *tile = (k[0] * g.n[1] + k[1]) * g.n[2] + k[2];
+  return ((p[0] - lo[0]) * e[1] + (p[1] - lo[1])) * e[2] + (p[2] - lo[2]);
+}
+
+// One thread per (batch*head, token, float4 of d).
+template <typename OutT>
+__global__ void __launch_bounds__(kThreads) merge_fwd_kernel(Geom g, const float* __restrict__ ot,
+                                                             OutT* __restrict__ out) {
+  const int F4 = g.d / 4;
+  const int64_t total = (int64_t)g.B * g.nh * g.N * F4;
+  for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * kThreads) {
+    const int f = (int)(idx % F4);
+    const int64_t bi = idx / F4;
+    const int bh = (int)(bi / g.N);
+    const int64_t i = bi % g.N;
+    Cover c;
+    if (!cover_of(g, i, c)) continue;  // single-cover: written by the tile kernel
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float wsum = 0.f;
+    int k[3];
+    for (k[0] = c.k0[0]; k[0] <= c.k1[0]; ++k[0])
+      for (k[1] = c.k0[1]; k[1] <= c.k1[1]; ++k[1])
+        for (k[2] = c.k0[2]; k[2] <= c.k1[2]; ++k[2]) {
+          int tile;
+          int r = row_in_tile(g, c.p, k, &tile);
+          float w = tile_weight(g, c.p, k);
+          float4 o = __ldg(reinterpret_cast<const float4*>(ot + slot_index(g, bh, tile, r) * g.d) + f);
+          acc.x = fmaf(w, o.x, acc.x);
+          acc.y = fmaf(w, o.y, acc.y);
+          acc.z = fmaf(w, o.z, acc.z);
+          acc.w = fmaf(w, o.w, acc.w);
+          wsum += w;
+        }
+    const float inv = 1.f / wsum;
+    store4<OutT>(out + bi * g.d + 4 * f, make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv));
+  }
+}
+
+// Per (batch*head, tile, row) slot: fold the merge weight c = w_t / sum w into
+// the log-sum-exp (lse2c = lse2 - log2 c, so exp2(s - lse2c) = c P) and form
+// D = dOut . O_t.  O_t is the output itself for single-cover rows, else the
+// FP32 per-tile value saved by the forward.  One lane group of d/4 lanes per slot.
+template <typename OutT, typename InT>
+__global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* __restrict__ out,
+                                                            const InT* __restrict__ dout,
+                                                            const float* __restrict__ lse2,
+                                                            const float* __restrict__ ot,
+                                                            float* __restrict__ lse2c, float* __restrict__ dd) {
+  const int F4 = g.d / 4;  // 8, 16 or 32 lanes per slot
+  const int64_t S = (int64_t)g.B * g.nh * g.ntiles * g.Lmax;
+  const int64_t total = S * F4;
+  // the grid-stride loop keeps all lanes of a group together (total % F4 == 0)
+  for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx - threadIdx.x % 32 < total;
+       idx += (int64_t)gridDim.x * kThreads) {
+    const bool in = idx < total;
+    const int f = (int)(idx % F4);
+    const int64_t slot = in ? idx / F4 : 0;
+    const int r = (int)(slot % g.Lmax);
+    const int64_t ut = slot / g.Lmax;
+    const int tile = (int)(ut % g.ntiles);
+    const int bh = (int)(ut / g.ntiles);
+    TileBox tb;
+    tile_box(g, tile, tb);
+    const bool valid = in && r < tb.L;
+    float part = 0.f;
+    int p[3];
+    int64_t tok = 0;
+    bool single = true;
+    if (valid) {
+      tok = tile_token(g, tb, r);
+      token_pos(g, tok, p);
+      single = single_cover(g, p);
+      const int64_t off = ((int64_t)bh * g.N + tok) * g.d + 4 * f;
+      float4 a = load4<InT>(dout + off);
+      float4 o = single ? load4<OutT>(out + off) : __ldg(reinterpret_cast<const float4*>(ot + slot * g.d) + f);
+      part = a.x * o.x + a.y * o.y + a.z * o.z + a.w * o.w;
+    }
+    for (int o = 1; o < F4; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (valid && f == 0) {
+      float lc = lse2[slot];
+      if (!single) {
+        // c = w_t / sum over covering tiles of w
+        Cover c;
+        cover_of(g, tok, c);
+        int kt[3];
+        kt[0] = tile / (g.n[1] * g.n[2]);
+        kt[1] = (tile / g.n[2]) % g.n[1];
+        kt[2] = tile % g.n[2];
+        float wt = tile_weight(g, p, kt), ws = 0.f;
+        int k[3];
+        for (k[0] = c.k0[0]; k[0] <= c.k1[0]; ++k[0])
+          for (k[1] = c.k0[1]; k[1] <= c.k1[1]; ++k[1])
+            for (k[2] = c.k0[2]; k[2] <= c.k1[2]; ++k[2]) ws += tile_weight(g, p, k);
+        lc -= log2f(wt / ws);
+      }
+      lse2c[slot] = lc;
+      dd[slot] = part;
+    }
+  }
+}
+
+// Input gradients of multiply-covered tokens: ascending-tile sums of the
+// per-tile FP32 gradients.
+template <typename OutT>
+__global__ void __launch_bounds__(kThreads) merge_bwd_kernel(Geom g, const float* __restrict__ dq_s,
+                                                             const float* __restrict__ dk_s,
+                                                             const float* __restrict__ dv_s, OutT* __restrict__ dq,
+                                                             OutT* __restrict__ dk, OutT* __restrict__ dv) {
+  const int F4 = g.d / 4;
+  const int64_t total = (int64_t)g.B * g.nh * g.N * F4;
+  for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * kThreads) {
+    const int f = (int)(idx % F4);
+    const int64_t bi = idx / F4;
+    const int bh = (int)(bi / g.N);
+    const int64_t i = bi % g.N;
+    Cover c;
+    if (!cover_of(g, i, c)) continue;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, e = a;
+    int k[3];
+    for (k[0] = c.k0[0]; k[0] <= c.k1[0]; ++k[0])
+      for (k[1] = c.k0[1]; k[1] <= c.k1[1]; ++k[1])
+        for (k[2] = c.k0[2]; k[2] <= c.k1[2]; ++k[2]) {
+          int tile;
+          int r = row_in_tile(g, c.p, k, &tile);
+          const int64_t off = slot_index(g, bh, tile, r) * g.d;
+          float4 x = __ldg(reinterpret_cast<const float4*>(dq_s + off) + f);
+          float4 y = __ldg(reinterpret_cast<const float4*>(dk_s + off) + f);
+          float4 z = __ldg(reinterpret_cast<const float4*>(dv_s + off) + f);
+          a.x += x.x; a.y += x.y; a.z += x.z; a.w += x.w;
+          b.x += y.x; b.y += y.y; b.z += y.z; b.w += y.w;
+          e.x += z.x; e.y += z.y; e.z += z.z; e.w += z.w;
+        }
+    store4<OutT>(dq + bi * g.d + 4 * f, a);
+    store4<OutT>(dk + bi * g.d + 4 * f, b);
+    store4<OutT>(dv + bi * g.d + 4 * f, e);
+  }
+}
+
+inline unsigned grid_for(int64_t total) {
+  int64_t blocks = (total + kThreads - 1) / kThreads;
+  const int64_t cap = 152LL * 16 * 8;  // grid-stride beyond this
+  return (unsigned)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_merge_fwd(const Geom& g, const float* ot, void* out, int out_dtype, cudaStream_t st) {
+  const int64_t total = (int64_t)g.B * g.nh * g.N * (g.d / 4);
+  if (out_dtype == GATTN_BF16)
+    merge_fwd_kernel<__nv_bfloat16><<<grid_for(total), kThreads, 0, st>>>(g, ot, static_cast<__nv_bfloat16*>(out));
+  else
+    merge_fwd_kernel<float><<<grid_for(total), kThreads, 0, st>>>(g, ot, static_cast<float*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_prep(const Geom& g, const void* out, int out_dtype, const void* dout, int in_dtype,
+                            const float* lse2, const float* ot, float* lse2c, float* dd, cudaStream_t st) {
+  const int64_t total = (int64_t)g.B * g.nh * g.ntiles * g.Lmax * (g.d / 4);
+  const unsigned grid = grid_for(total);
+  using bf = __nv_bfloat16;
+  if (out_dtype == GATTN_BF16 && in_dtype == GATTN_BF16)
+    bwd_prep_kernel<bf, bf><<<grid, kThreads, 0, st>>>(g, (const bf*)out, (const bf*)dout, lse2, ot, lse2c, dd);
+  else if (out_dtype == GATTN_BF16)
+    bwd_prep_kernel<bf, float><<<grid, kThreads, 0, st>>>(g, (const bf*)out, (const float*)dout, lse2, ot, lse2c, dd);
+  else if (in_dtype == GATTN_BF16)
+    bwd_prep_kernel<float, bf><<<grid, kThreads, 0, st>>>(g, (const float*)out, (const bf*)dout, lse2, ot, lse2c, dd);
+  else
+    bwd_prep_kernel<float, float><<<grid, kThreads, 0, st>>>(g, (const float*)out, (const float*)dout, lse2, ot, lse2c, dd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_bwd(const Geom& g, const float* dq_s, const float* dk_s, const float* dv_s, void* dq,
+                             void* dk, void* dv, int out_dtype, cudaStream_t st) {
+  const int64_t total = (int64_t)g.B * g.nh * g.N * (g.d / 4);
+  using bf = __nv_bfloat16;
+  if (out_dtype == GATTN_BF16)
+    merge_bwd_kernel<bf><<<grid_for(total), kThreads, 0, st>>>(g, dq_s, dk_s, dv_s, (bf*)dq, (bf*)dk, (bf*)dv);
+  else
+    merge_bwd_kernel<float><<<grid_for(total), kThreads, 0, st>>>(g, dq_s, dk_s, dv_s, (float*)dq, (float*)dk, (float*)dv);
+  return cudaGetLastError();
+}
+
+}  // namespace gattn

@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libgattn (include/gattn.h): STORM global propagation
+attention (STORM-GPA, arXiv 2604.16590, Sec. III-C) on GB300.
+
+Argument marshalling only: every step of the operator runs in the library's
+CUDA kernels.  PyTorch is used for device memory and streams.  There is no
+fallback: if ``libgattn.so`` has not been built, importing the library
+raises.
+
+The functions ``gattn_*`` mirror the C ABI one to one (same names, same
+arguments; tensors may be passed where the C side takes device pointers).
+``GlobalAttention`` wraps forward and backward as a torch.autograd.Function.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgattn.so")
+
+GATTN_BF16, GATTN_FP32 = 0, 1
+GATTN_WINDOW_HANN, GATTN_WINDOW_FLAT = 0, 1
+GATTN_FLAG_DEBUG_BOUNDS = 0x1
+
+STATUS = {
+    0: "GATTN_OK",
+    1: "GATTN_ERR_INVALID_ARG",
+    2: "GATTN_ERR_UNSUPPORTED",
+    3: "GATTN_ERR_WORKSPACE",
+    4: "GATTN_ERR_CUDA",
+    5: "GATTN_ERR_TIMEOUT",
+    6: "GATTN_ERR_OOM",
+    7: "GATTN_ERR_BUSY",
+    8: "GATTN_ERR_DEVICE_BOUNDS",
+    9: "GATTN_ERR_NOT_FOUND",
+}
+_DTYPES = {"bf16": GATTN_BF16, "fp32": GATTN_FP32, torch.bfloat16: GATTN_BF16, torch.float32: GATTN_FP32}
+_TORCH_DTYPE = {GATTN_BF16: torch.bfloat16, GATTN_FP32: torch.float32}
+
+
+class GattnError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {STATUS.get(self.status, self.status)}")
+
+
+class gattn_desc(ctypes.Structure):
+    _fields_ = [
+        ("B", ctypes.c_int32),
+        ("nh", ctypes.c_int32),
+        ("d", ctypes.c_int32),
+        ("T", ctypes.c_int32),
+        ("Y", ctypes.c_int32),
+        ("X", ctypes.c_int32),
+        ("core", ctypes.c_int32 * 3),
+        ("halo", ctypes.c_int32 * 3),
+        ("window", ctypes.c_int32),
+        ("in_dtype", ctypes.c_int32),
+        ("out_dtype", ctypes.c_int32),
+        ("scale", ctypes.c_float),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libgattn.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build it with `python -m paper_2604_16590_gb300.build` "
+            "(the operator has no non-CUDA implementation)"
+        )
+    lib = ctypes.CDLL(path)
+    P, S, D = ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(gattn_desc)
+    sig = {
+        "gattn_abi_version": ([], ctypes.c_int32),
+        "gattn_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "gattn_validate": ([D], ctypes.c_int),
+        "gattn_num_tiles": ([D], ctypes.c_int64),
+        "gattn_saved_bytes": ([D], S),
+        "gattn_bwd_workspace_bytes": ([D], S),
+        "gattn_fwd": ([D, P, P, P, P, P, S, P], ctypes.c_int),
+        "gattn_bwd": ([D, P, P, P, P, P, P, S, P, P, P, P, S, P], ctypes.c_int),
+        "gattn_stream_status": ([P], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(int(x))
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _nbytes(x, given):
+    if given is not None:
+        return int(given)
+    return x.numel() * x.element_size()
+
+
+def make_desc(B, nh, d, grid, core, halo, window="hann", in_dtype="bf16", out_dtype=None, scale=0.0, flags=0):
+    """Build a gattn_desc.  grid = (T, Y, X); core/halo along (t, y, x)."""
+    desc = gattn_desc()
+    desc.B, desc.nh, desc.d = int(B), int(nh), int(d)
+    desc.T, desc.Y, desc.X = (int(g) for g in grid)
+    for a in range(3):
+        desc.core[a] = int(core[a])
+        desc.halo[a] = int(halo[a])
+    desc.window = GATTN_WINDOW_HANN if window == "hann" else GATTN_WINDOW_FLAT
+    desc.in_dtype = _DTYPES[in_dtype]
+    desc.out_dtype = _DTYPES[out_dtype if out_dtype is not None else in_dtype]
+    desc.scale = float(scale or 0.0)
+    desc.flags = int(flags)
+    return desc
+
+
+# ---------------------------------------------------------------- the C ABI, one to one
+def gattn_abi_version() -> int:
+    return load_library().gattn_abi_version()
+
+
+def gattn_status_string(status: int) -> str:
+    return load_library().gattn_status_string(int(status)).decode()
+
+
+def gattn_validate(desc) -> int:
+    return load_library().gattn_validate(ctypes.byref(desc))
+
+
+def gattn_num_tiles(desc) -> int:
+    return load_library().gattn_num_tiles(ctypes.byref(desc))
+
+
+def gattn_saved_bytes(desc) -> int:
+    return load_library().gattn_saved_bytes(ctypes.byref(desc))
+
+
+def gattn_bwd_workspace_bytes(desc) -> int:
+    return load_library().gattn_bwd_workspace_bytes(ctypes.byref(desc))
+
+
+def gattn_fwd(desc, q, k, v, out, saved, saved_bytes=None, stream=None) -> int:
+    return load_library().gattn_fwd(
+        ctypes.byref(desc), _ptr(q), _ptr(k), _ptr(v), _ptr(out), _ptr(saved), _nbytes(saved, saved_bytes), _stream(stream)
+    )
+
+
+def gattn_bwd(desc, q, k, v, out, dout, saved, dq, dk, dv, ws, saved_bytes=None, ws_bytes=None, stream=None) -> int:
+    return load_library().gattn_bwd(
+        ctypes.byref(desc), _ptr(q), _ptr(k), _ptr(v), _ptr(out), _ptr(dout), _ptr(saved), _nbytes(saved, saved_bytes),
+        _ptr(dq), _ptr(dk), _ptr(dv), _ptr(ws), _nbytes(ws, ws_bytes), _stream(stream),
+    )
+
+
+def gattn_stream_status(stream=None) -> int:
+    return load_library().gattn_stream_status(_stream(stream))
+
+
+def check(status: int, what: str = "gattn") -> None:
+    if status != 0:
+        raise GattnError(status, what)
+
+
+# ---------------------------------------------------------------- torch-level API
+@dataclass(frozen=True)
+class Tiling:
+    """Token grid and tile spec of a GPA call (all along (t, y, x))."""
+
+    grid: tuple
+    core: tuple
+    halo: tuple
+    window: str = "hann"
+    scale: float = 0.0
+
+    @property
+    def N(self) -> int:
+        T, Y, X = self.grid
+        return T * Y * X
+
+
+def desc_for(q: torch.Tensor, tiling: Tiling, out_dtype=None, flags: int = 0):
+    if q.dim() != 4:
+        raise ValueError("expected [B, heads, N, d]")
+    B, nh, N, d = q.shape
+    if N != tiling.N:
+        raise ValueError(f"N={N} does not match grid {tiling.grid}")
+    return make_desc(
+        B, nh, d, tiling.grid, tiling.core, tiling.halo, tiling.window, q.dtype,
+        out_dtype if out_dtype is not None else q.dtype, tiling.scale, flags,
+    )
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("gattn needs contiguous CUDA tensors")
+
+
+def forward(q, k, v, tiling: Tiling, out_dtype=None, stream=None):
+    """Out = GPA(q, k, v) and the saved state the backward needs."""
+    _require_cuda(q, k, v)
+    desc = desc_for(q, tiling, out_dtype)
+    out = torch.empty(q.shape, dtype=_TORCH_DTYPE[desc.out_dtype], device=q.device)
+    saved = torch.empty(gattn_saved_bytes(desc), dtype=torch.uint8, device=q.device)
+    check(gattn_fwd(desc, q, k, v, out, saved, stream=stream), "gattn_fwd")
+    return out, saved
+
+
+def backward(q, k, v, out, dout, saved, tiling: Tiling, stream=None):
+    """(dq, dk, dv) of sum(out * dout)."""
+    _require_cuda(q, k, v, out, dout, saved)
+    desc = desc_for(q, tiling, out.dtype)
+    if dout.dtype != q.dtype:
+        raise ValueError("dout must have the input dtype")
+    dq = torch.empty_like(out)
+    dk = torch.empty_like(out)
+    dv = torch.empty_like(out)
+    ws = torch.empty(gattn_bwd_workspace_bytes(desc), dtype=torch.uint8, device=q.device)
+    check(gattn_bwd(desc, q, k, v, out, dout, saved, dq, dk, dv, ws, stream=stream), "gattn_bwd")
+    return dq, dk, dv
+
+
+class GlobalAttention(torch.autograd.Function):
+    """STORM-GPA as an autograd op: forward and hand-written backward in CUDA."""
+
+    @staticmethod
+    def forward(ctx, q, k, v, tiling: Tiling):
+        out, saved = forward(q, k, v, tiling)
+        ctx.tiling = tiling
+        ctx.save_for_backward(q, k, v, out, saved)
+        return out
+
+    @staticmethod
+    def backward(ctx, dout):
+        q, k, v, out, saved = ctx.saved_tensors
+        dout = dout.contiguous()
+        if dout.dtype != q.dtype:
+            raise ValueError("upstream gradient must have the input dtype")
+        dq, dk, dv = backward(q, k, v, out, dout, saved, ctx.tiling)
+        return dq, dk, dv, None
+
+
+def global_attention(q, k, v, tiling: Tiling):
+    return GlobalAttention.apply(q, k, v, tiling)
