@@ -1,0 +1,67 @@
+"""Parity of the BF16 tensor-core form (tcgen05 kernels) with the FP64 oracle.
+
+The oracle runs on the same BF16-rounded inputs (as FP64), so input
+quantisation is not counted as error.  Tolerance of the BF16 form, per output
+and (batch, head): max-rel <= 2e-2 and rms-rel <= 3e-3 (P is rounded to BF16
+before the P V product; accumulation is FP32 in tensor memory).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2604_16590_gb300 import build, gattn
+from paper_2604_16590_gb300.inputs import qkv, upstream_grad
+from tests._parity import assert_close
+
+pytestmark = pytest.mark.gpu
+
+MAX_REL, RMS_REL = 2e-2, 3e-3
+
+FWD_CASES = [
+    # name, B, nh, d, grid, core, halo
+    ("p_like_small", 1, 2, 64, (4, 16, 32), (4, 8, 16), (0, 2, 4)),
+    ("s_spec", 1, 1, 64, (2, 32, 32), (1, 16, 16), (0, 4, 4)),
+    ("one_tile_1024", 1, 1, 64, (1, 32, 32), (1, 32, 32), (0, 0, 0)),
+    ("ragged_all_dims", 2, 3, 64, (3, 10, 13), (2, 4, 5), (1, 2, 2)),
+    ("d128_temporal", 1, 2, 128, (16, 8, 8), (8, 8, 8), (2, 0, 0)),
+    ("long_tile_ring_wrap", 1, 1, 64, (8, 32, 32), (8, 16, 16), (0, 4, 4)),
+    ("d128_s_spec", 1, 1, 128, (1, 48, 40), (1, 16, 16), (0, 4, 4)),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    gattn.load_library()
+
+
+def _inputs(B, nh, d, grid, seed):
+    shape = (B, nh, grid[0] * grid[1] * grid[2], d)
+    q, k, v = qkv(shape, seed, 0.5, "bf16")
+    go = upstream_grad(shape, seed, "bf16")
+    return q, k, v, go
+
+
+@pytest.mark.parametrize("name,B,nh,d,grid,core,halo", FWD_CASES, ids=[c[0] for c in FWD_CASES])
+@pytest.mark.parametrize("out_dtype", [torch.float32, torch.bfloat16], ids=["out_fp32", "out_bf16"])
+def test_bf16_forward_matches_oracle(name, B, nh, d, grid, core, halo, out_dtype):
+    q, k, v, _ = _inputs(B, nh, d, grid, 300 + len(name))
+    dev = torch.device("cuda:0")
+    tiling = gattn.Tiling(grid, core, halo)
+    out, _ = gattn.forward(q.to(dev), k.to(dev), v.to(dev), tiling, out_dtype=out_dtype)
+    st = gattn.gattn_stream_status()
+    assert st == 0, gattn.STATUS.get(st, st)
+    geo = oracle.Geometry(B, nh, d, *grid, core, halo)
+    ref = oracle.forward(geo, q.double().numpy(), k.double().numpy(), v.double().numpy())
+    assert_close(f"{name}/out", out.double().cpu().numpy(), ref, MAX_REL, RMS_REL)
+
+
+def test_bf16_forward_is_deterministic():
+    grid, core, halo = (4, 32, 32), (2, 16, 16), (1, 4, 4)
+    q, k, v, _ = _inputs(1, 2, 64, grid, 11)
+    dev = torch.device("cuda:0")
+    tiling = gattn.Tiling(grid, core, halo)
+    a, _ = gattn.forward(q.to(dev), k.to(dev), v.to(dev), tiling, out_dtype=torch.float32)
+    b, _ = gattn.forward(q.to(dev), k.to(dev), v.to(dev), tiling, out_dtype=torch.float32)
+    assert torch.equal(a, b)
