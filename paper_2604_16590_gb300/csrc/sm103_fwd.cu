@@ -87,6 +87,141 @@ __device__ __forceinline__ bool accumulate_pv(float (&O)[D], float& mO, float mp
   return true;
 }
 
+
+// Online-softmax state of one query row.
+template <int D>
+struct RowState {
+  float O[D];  // sum of P V relative to max mO
+  float m;     // running row max (log2 domain, scaled)
+  float l;     // running row sum relative to m
+  float mO;    // max the register accumulator O is expressed against
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int e = 0; e < D; ++e) O[e] = 0.f;
+    m = -INFINITY;
+    l = 0.f;
+    mO = -INFINITY;
+  }
+};
+
+template <int N>
+__device__ __forceinline__ float tree_max(float (&v)[N]) {
+#pragma unroll
+  for (int w = N / 2; w >= 1; w /= 2)
+#pragma unroll
+    for (int i = 0; i < w; ++i) v[i] = fmaxf(v[i], v[i + w]);
+  return v[0];
+}
+template <int N>
+__device__ __forceinline__ float tree_sum(float (&v)[N]) {
+#pragma unroll
+  for (int w = N / 2; w >= 1; w /= 2)
+#pragma unroll
+    for (int i = 0; i < w; ++i) v[i] += v[i + w];
+  return v[0];
+}
+
+// Exponentiate 32 scores of TMEM chunk c into BF16 P in shared memory
+// (128-byte swizzled, K-major: row = query, 64 keys per 128-byte line).
+template <bool MASK>
+__device__ __forceinline__ void exp_store_chunk(const uint32_t (&r)[32], int c, uint32_t mbits, float sl2, float mnew,
+                                                float (&acc)[8], uint32_t sP, int row) {
+  uint32_t pk[16];
+#pragma unroll
+  for (int i = 0; i < 32; i += 2) {
+    float p0 = sm103::ex2(fmaf(__uint_as_float(r[i]), sl2, -mnew));
+    float p1 = sm103::ex2(fmaf(__uint_as_float(r[i + 1]), sl2, -mnew));
+    if (MASK) {
+      p0 = (mbits >> i) & 1u ? p0 : 0.f;
+      p1 = (mbits >> (i + 1)) & 1u ? p1 : 0.f;
+    }
+    acc[(i >> 1) & 7] += p0 + p1;
+    pk[i >> 1] = sm103::pack_bf16(p0, p1);
+  }
+  const uint32_t base = sP + (c >> 1) * 16384 + row * 128;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const uint32_t unit = ((c & 1) * 4 + u) ^ (row & 7);
+    sm103::st_shared_v4(base + unit * 16, pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+  }
+}
+
+template <bool MASK>
+__device__ __forceinline__ void chunk_max(const uint32_t (&r)[32], uint32_t mbits, float (&mx)[8]) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    float x = __uint_as_float(r[i]);
+    if (MASK) x = (mbits >> i) & 1u ? x : -INFINITY;
+    mx[i & 7] = fmaxf(mx[i & 7], x);
+  }
+}
+
+// One 128-key block of the online softmax for this thread's query row:
+// row max, fold of the previous block's P V (if any), P = exp2(...) to shared
+// memory, row-sum update.  For d = 64 the whole 128-column score row is kept
+// in registers; for d = 128 (larger accumulator) the scores are read from
+// TMEM twice, 64 columns at a time.
+template <int D, bool MASK>
+__device__ __forceinline__ bool softmax_block(RowState<D>& rs, uint32_t tS, uint32_t tO, uint32_t sP, int row,
+                                              const uint32_t (&kmask)[4], float sl2, bool has_prev, uint32_t G,
+                                              uint64_t* pv_done, volatile int* abort_flag) {
+  using namespace sm103;
+  float mx[8], acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    mx[i] = -INFINITY;
+    acc[i] = 0.f;
+  }
+  uint32_t r0[32], r1[32];
+  if constexpr (D == 64) {
+    uint32_t r2[32], r3[32];
+    tmem_ld32(tS, r0);
+    tmem_ld32(tS + 32, r1);
+    tmem_ld32(tS + 64, r2);
+    tmem_ld32(tS + 96, r3);
+    tmem_wait_ld(r0);
+    tmem_wait_ld(r1);
+    tmem_wait_ld(r2);
+    tmem_wait_ld(r3);
+    chunk_max<MASK>(r0, kmask[0], mx);
+    chunk_max<MASK>(r1, kmask[1], mx);
+    chunk_max<MASK>(r2, kmask[2], mx);
+    chunk_max<MASK>(r3, kmask[3], mx);
+    const float mnew = fmaxf(rs.m, tree_max(mx) * sl2);
+    if (has_prev && !accumulate_pv<D>(rs.O, rs.mO, rs.m, G - 1, tO, pv_done, abort_flag)) return false;
+    exp_store_chunk<MASK>(r0, 0, kmask[0], sl2, mnew, acc, sP, row);
+    exp_store_chunk<MASK>(r1, 1, kmask[1], sl2, mnew, acc, sP, row);
+    exp_store_chunk<MASK>(r2, 2, kmask[2], sl2, mnew, acc, sP, row);
+    exp_store_chunk<MASK>(r3, 3, kmask[3], sl2, mnew, acc, sP, row);
+    rs.l = rs.l * ex2(rs.m - mnew) + tree_sum(acc);
+    rs.m = mnew;
+  } else {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      tmem_ld32(tS + 64 * h, r0);
+      tmem_ld32(tS + 64 * h + 32, r1);
+      tmem_wait_ld(r0);
+      tmem_wait_ld(r1);
+      chunk_max<MASK>(r0, kmask[2 * h], mx);
+      chunk_max<MASK>(r1, kmask[2 * h + 1], mx);
+    }
+    const float mnew = fmaxf(rs.m, tree_max(mx) * sl2);
+    if (has_prev && !accumulate_pv<D>(rs.O, rs.mO, rs.m, G - 1, tO, pv_done, abort_flag)) return false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      tmem_ld32(tS + 64 * h, r0);
+      tmem_ld32(tS + 64 * h + 32, r1);
+      tmem_wait_ld(r0);
+      tmem_wait_ld(r1);
+      exp_store_chunk<MASK>(r0, 2 * h, kmask[2 * h], sl2, mnew, acc, sP, row);
+      exp_store_chunk<MASK>(r1, 2 * h + 1, kmask[2 * h + 1], sl2, mnew, acc, sP, row);
+    }
+    rs.l = rs.l * ex2(rs.m - mnew) + tree_sum(acc);
+    rs.m = mnew;
+  }
+  return true;
+}
+
 template <int D, typename OutT>
 __global__ void __launch_bounds__(192, 1)
     sm103_fwd_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
@@ -121,9 +256,9 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(s_full + s, 1);
-      mbar_init(s_empty + s, 128);
+      mbar_init(s_empty + s, 4);
     }
-    mbar_init(p_full, 128);
+    mbar_init(p_full, 4);
     mbar_init(pv_done, 1);
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -253,10 +388,9 @@ __global__ void __launch_bounds__(192, 1)
   } else {
     // ------------------------------------------------------------ softmax + epilogue
     const int quad = warp & 3;
-    const int row = quad * 32 + lane;               // TMEM lane = block row
+    const int row = quad * 32 + lane;  // TMEM lane = block row
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     const uint32_t sP = smem_u32(smem + C::kP);
-    const float sl2 = g.scale_log2;
     uint32_t G = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
@@ -270,97 +404,58 @@ __global__ void __launch_bounds__(192, 1)
       block_row(bs, qo, row, ql);
       const bool qvalid = inside(tbk, ql);
 
-      float O[D];
-#pragma unroll
-      for (int e = 0; e < D; ++e) O[e] = 0.f;
-      float m = -INFINITY, l = 0.f, mO = -INFINITY, mprev = -INFINITY;
-      uint32_t r[32];
-
+      RowState<D> rs;
+      rs.init();
       for (int j = 0; j < tbk.NB; ++j, ++G) {
         const uint32_t sb = G & 1;
         int ko[3];
         block_origin(tbk, bs, j, ko);
+        // key validity of the block's 128 columns, one ballot per 32 columns
+        uint32_t kmask[4];
         const bool full = block_full(tbk, bs, ko);
+        if (!full) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            int kl[3];
+            block_row(bs, ko, c * 32 + lane, kl);
+            kmask[c] = __ballot_sync(0xffffffffu, inside(tbk, kl));
+          }
+        }
         if (!(ok = mbar_wait<set_status_fwd>(s_full + sb, (G >> 1) & 1, abort_flag))) break;
         tc_fence_after();
-        const uint32_t tS = tl + sb * 128;
-        // pass 1: row max over the valid keys of the block
-        float mx = -INFINITY;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          tmem_ld32(tS + c * 32, r);
-          tmem_wait_ld(r);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            float x = __uint_as_float(r[i]);
-            if (!full) {
-              int kl[3];
-              block_row(bs, ko, c * 32 + i, kl);
-              if (!inside(tbk, kl)) x = -INFINITY;
-            }
-            mx = fmaxf(mx, x);
-          }
-        }
-        const float mnew = fmaxf(m, mx * sl2);
-        // fold the previous block's P V into the register accumulator
-        if (j > 0 && !(ok = accumulate_pv<D>(O, mO, mprev, G - 1, tl + C::kColO, pv_done, abort_flag))) break;
-        // pass 2: P = exp2(s S log2e - m) -> BF16 shared memory (128B-swizzled, K-major)
-        float ls = 0.f;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          tmem_ld32(tS + c * 32, r);
-          tmem_wait_ld(r);
-          uint32_t pk[16];
-#pragma unroll
-          for (int i = 0; i < 32; i += 2) {
-            float p0 = ex2(fmaf(__uint_as_float(r[i]), sl2, -mnew));
-            float p1 = ex2(fmaf(__uint_as_float(r[i + 1]), sl2, -mnew));
-            if (!full) {
-              int kl[3];
-              block_row(bs, ko, c * 32 + i, kl);
-              if (!inside(tbk, kl)) p0 = 0.f;
-              block_row(bs, ko, c * 32 + i + 1, kl);
-              if (!inside(tbk, kl)) p1 = 0.f;
-            }
-            ls += p0 + p1;
-            pk[i >> 1] = pack_bf16(p0, p1);
-          }
-          const uint32_t base = sP + (c >> 1) * 16384 + row * 128;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const uint32_t unit = ((c & 1) * 4 + u) ^ (row & 7);
-            st_shared_v4(base + unit * 16, pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
-          }
-        }
-        l = l * ex2(m - mnew) + ls;
-        m = mnew;
-        mprev = mnew;
+        if (full)
+          ok = softmax_block<D, false>(rs, tl + sb * 128, tl + C::kColO, sP, row, kmask, g.scale_log2, j > 0, G, pv_done, abort_flag);
+        else
+          ok = softmax_block<D, true>(rs, tl + sb * 128, tl + C::kColO, sP, row, kmask, g.scale_log2, j > 0, G, pv_done, abort_flag);
+        if (!ok) break;
         tc_fence_before();
-        mbar_arrive(s_empty + sb);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(s_empty + sb);
         fence_proxy_async_smem();
-        mbar_arrive(p_full);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(p_full);
       }
       if (!ok) break;
-      if (!(ok = accumulate_pv<D>(O, mO, mprev, G - 1, tl + C::kColO, pv_done, abort_flag))) break;
+      if (!(ok = accumulate_pv<D>(rs.O, rs.mO, rs.m, G - 1, tl + C::kColO, pv_done, abort_flag))) break;
       tc_fence_before();
       // ---- epilogue
       if (qvalid) {
         const int r_local = (ql[0] * tbk.tb.e[1] + ql[1]) * tbk.tb.e[2] + ql[2];
         const int64_t slot = slot_index(g, bh, tile, r_local);
-        a.lse2[slot] = m + __log2f(l);
+        a.lse2[slot] = rs.m + __log2f(rs.l);
         const int p[3] = {tbk.tb.lo[0] + ql[0], tbk.tb.lo[1] + ql[1], tbk.tb.lo[2] + ql[2]};
         const int64_t tok = ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2];
-        const float inv = 1.f / l;
+        const float inv = 1.f / rs.l;
         if (single_cover(g, p)) {
           OutT* dst = static_cast<OutT*>(a.out) + ((int64_t)bh * g.N + tok) * D;
 #pragma unroll
           for (int e = 0; e < D; e += 4)
-            store4<OutT>(dst + e, make_float4(O[e] * inv, O[e + 1] * inv, O[e + 2] * inv, O[e + 3] * inv));
+            store4<OutT>(dst + e, make_float4(rs.O[e] * inv, rs.O[e + 1] * inv, rs.O[e + 2] * inv, rs.O[e + 3] * inv));
         } else {
           float* dst = a.ot + slot * D;
 #pragma unroll
           for (int e = 0; e < D; e += 4)
-            store4<float>(dst + e, make_float4(O[e] * inv, O[e + 1] * inv, O[e + 2] * inv, O[e + 3] * inv));
+            store4<float>(dst + e, make_float4(rs.O[e] * inv, rs.O[e + 1] * inv, rs.O[e + 2] * inv, rs.O[e + 3] * inv));
         }
       }
     }

@@ -15,6 +15,7 @@ namespace gattn {
 namespace sm103 {
 
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s
+constexpr uint32_t kSuspendHintNs = 1000000u;       // 1 ms per try_wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -49,6 +50,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait with a suspend-time hint: the thread sleeps until the phase
+// completes (or the hint elapses) instead of spinning on the issue port.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity), "r"(kSuspendHintNs)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for the phase with the given parity to complete.  Returns false if the
 // CTA is aborting (another waiter timed out) or if this wait times out, in
 // which case the status word and the abort flag are set.
@@ -61,14 +76,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(a, parity)) return true;
-    if ((it & 31u) == 0) {
-      if (honor_abort && *abort_flag) return false;
-      if (globaltimer() - t0 > kWaitTimeoutNs || it > (1u << 30)) {
-        *abort_flag = 1;
-        SetStatus(GATTN_ERR_TIMEOUT);
-        return false;
-      }
+    if (mbar_try_wait_sleep(a, parity)) return true;
+    if (honor_abort && *abort_flag) return false;
+    if (globaltimer() - t0 > kWaitTimeoutNs || it > (1u << 24)) {
+      *abort_flag = 1;
+      SetStatus(GATTN_ERR_TIMEOUT);
+      return false;
     }
   }
 }
