@@ -10,6 +10,54 @@ namespace gattn {
 
 static bool dtype_ok(int32_t t) { return t == GATTN_BF16 || t == GATTN_FP32; }
 
+static int clipped_extent(const Geom& g, int a, int k) {
+  int lo = k * g.c[a] - g.h[a], hi = (k + 1) * g.c[a] + g.h[a];
+  lo = lo < 0 ? 0 : lo;
+  hi = hi > g.G[a] ? g.G[a] : hi;
+  return hi - lo;
+}
+
+// Box shape (bt, by, bx), bt*by*bx = 128, powers of two.  The attention work of
+// a tile grows with the square of its box count, so the shape minimising
+// sum_tiles NB_t^2 = prod_a sum_k ceil(e_a(k)/b_a)^2 (the sum factorises over
+// dimensions) wins; ties go to the longest contiguous x run.
+static void choose_box(Geom* g) {
+  double best_cost = -1.0;
+  int best[3] = {1, 1, 128};
+  for (int lt = 0; lt <= 7; ++lt)
+    for (int ly = 0; ly + lt <= 7; ++ly) {
+      const int lx = 7 - lt - ly;
+      const int b[3] = {1 << lt, 1 << ly, 1 << lx};
+      double cost = 1.0;
+      for (int a = 0; a < 3; ++a) {
+        double sum = 0.0;
+        for (int k = 0; k < g->n[a]; ++k) {
+          const double nb = (double)((clipped_extent(*g, a, k) + b[a] - 1) / b[a]);
+          sum += nb * nb;
+        }
+        cost *= sum;
+      }
+      if (best_cost < 0 || cost < best_cost * (1 - 1e-12) || (cost <= best_cost * (1 + 1e-12) && b[2] > best[2])) {
+        best_cost = cost;
+        best[0] = b[0];
+        best[1] = b[1];
+        best[2] = b[2];
+      }
+    }
+  g->bt = best[0];
+  g->by = best[1];
+  g->bx = best[2];
+  g->lt = __builtin_ctz(best[0]);
+  g->ly = __builtin_ctz(best[1]);
+  g->lx = __builtin_ctz(best[2]);
+  g->nbmax_tot = 1;
+  for (int a = 0; a < 3; ++a) {
+    g->nbmax[a] = (g->emax[a] + best[a] - 1) / best[a];
+    g->nbmax_tot *= g->nbmax[a];
+  }
+  g->per_tile = g->nbmax_tot * 128;
+}
+
 bool make_geom(const gattn_desc* desc, Geom* g) {
   if (!desc || !g) return false;
   memset(g, 0, sizeof(*g));
@@ -54,6 +102,8 @@ bool make_geom(const gattn_desc* desc, Geom* g) {
   g->window = d.window;
   g->scale = d.scale > 0.f ? d.scale : 1.0f / sqrtf((float)d.d);
   g->scale_log2 = g->scale * 1.4426950408889634f;
+  choose_box(g);
+  if ((int64_t)g->nbmax_tot * 128 >= (1LL << 31)) return false;
   return true;
 }
 

@@ -6,8 +6,16 @@
 // index is the fixed merge order).  Extended interval of tile k along a:
 // [max(k c - h, 0), min((k+1) c + h, G)).  Rows of an extended tile are
 // numbered r = (lt * e_y + ly) * e_x + lx over its clipped extents e[3].
-// Per-(tile, row) state (log-sum-exp, per-tile outputs, softmax statistics)
-// lives at slot ((bh * ntiles + tile) * Lmax + r), Lmax = prod_a max_k e_a(k).
+// Every extended tile is also covered by 3-D boxes of bt x by x bx = 128 tokens
+// (powers of two; the box shape is chosen per problem on the host).  Box j of
+// a tile with nb[3] boxes per dimension has origin ((j / (nb_y nb_x)) bt,
+// ((j / nb_x) % nb_y) by, (j % nb_x) bx) in tile-local coordinates and its row
+// rho sits at box offset (rho >> (ly + lx), (rho >> lx) & (by - 1),
+// rho & (bx - 1)).  Per-(tile, row) state (log-sum-exp, per-tile outputs,
+// softmax statistics, per-tile gradients) lives at slot
+//     ((bh * ntiles + tile) * per_tile + j * 128 + rho),  per_tile = nbmax * 128,
+// so the 128 rows of one box are contiguous -- the order the tensor-core
+// kernels process them in.
 #pragma once
 
 #include <stdint.h>
@@ -33,6 +41,11 @@ struct Geom {
   int32_t ntiles;
   int32_t Lmax;
   int32_t window;   // gattn_window
+  int32_t bt, by, bx;   // 128-token box shape
+  int32_t lt, ly, lx;   // log2 of the box extents
+  int32_t nbmax[3];     // most boxes any tile needs per dimension
+  int32_t nbmax_tot;    // nbmax[0] * nbmax[1] * nbmax[2]
+  int32_t per_tile;     // slots per tile = nbmax_tot * 128
   int64_t N;
   float scale;      // softmax scale s
   float scale_log2; // s * log2(e)
@@ -103,8 +116,38 @@ __host__ __device__ __forceinline__ bool single_cover(const Geom& g, const int p
   return one;
 }
 
-__host__ __device__ __forceinline__ int64_t slot_index(const Geom& g, int bh, int tile, int r) {
-  return ((int64_t)bh * g.ntiles + tile) * g.Lmax + r;
+// tile-local coordinates of row r (row-major over the clipped extents)
+__host__ __device__ __forceinline__ void tile_local(const TileBox& tb, int r, int l[3]) {
+  l[2] = r % tb.e[2];
+  const int rr = r / tb.e[2];
+  l[1] = rr % tb.e[1];
+  l[0] = rr / tb.e[1];
+}
+
+// slot of the token at tile-local coordinates l[3] of a tile with extents e[3]
+__host__ __device__ __forceinline__ int64_t slot_of(const Geom& g, int bh, int tile, const int e[3], const int l[3]) {
+  const int nby = (e[1] + g.by - 1) >> g.ly;
+  const int nbx = (e[2] + g.bx - 1) >> g.lx;
+  const int j = ((l[0] >> g.lt) * nby + (l[1] >> g.ly)) * nbx + (l[2] >> g.lx);
+  const int rho = ((l[0] & (g.bt - 1)) << (g.ly + g.lx)) | ((l[1] & (g.by - 1)) << g.lx) | (l[2] & (g.bx - 1));
+  return ((int64_t)bh * g.ntiles + tile) * g.per_tile + (int64_t)j * 128 + rho;
+}
+
+// inverse of slot_of within one tile: tile-local coordinates of row rho of
+// box j of a tile with extents e[3]; false if that row lies outside the tile
+__host__ __device__ __forceinline__ bool slot_local(const Geom& g, const int e[3], int j, int rho, int l[3]) {
+  const int nby = (e[1] + g.by - 1) >> g.ly;
+  const int nbx = (e[2] + g.bx - 1) >> g.lx;
+  const int jx = j % nbx, jr = j / nbx;
+  const int jy = jr % nby, jt = jr / nby;
+  l[0] = (jt << g.lt) + (rho >> (g.ly + g.lx));
+  l[1] = (jy << g.ly) + ((rho >> g.lx) & (g.by - 1));
+  l[2] = (jx << g.lx) + (rho & (g.bx - 1));
+  return l[0] < e[0] && l[1] < e[1] && l[2] < e[2];
+}
+
+__host__ __device__ __forceinline__ int64_t grid_token(const Geom& g, const TileBox& tb, const int l[3]) {
+  return ((int64_t)(tb.lo[0] + l[0]) * g.G[1] + (tb.lo[1] + l[1])) * g.G[2] + (tb.lo[2] + l[2]);
 }
 
 #ifdef __CUDACC__
@@ -124,7 +167,7 @@ __device__ __forceinline__ float tile_weight(const Geom& g, const int p[3], cons
 }
 #endif
 
-// Host-side construction; returns false on an invalid descriptor.
+// Host-side construction (including the box shape); false on an invalid descriptor.
 bool make_geom(const gattn_desc* desc, Geom* g);
 
 }  // namespace gattn

@@ -16,13 +16,13 @@ __host__ __device__ inline size_t align_up(size_t x) { return (x + kAlign - 1) /
 // Saved state written by the forward, read by the backward.
 //   lse2 : float[S]     log2-domain log-sum-exp of every (tile, row) slot
 //   ot   : float[S * d] per-tile output O_t of rows covered by >1 tile
-// S = B * nh * ntiles * Lmax.
+// S = B * nh * ntiles * per_tile (box-ordered slots, see geom.cuh).
 struct SavedLayout {
   size_t S, lse_off, ot_off, bytes;
 };
 inline SavedLayout saved_layout(const Geom& g) {
   SavedLayout s;
-  s.S = (size_t)g.B * g.nh * g.ntiles * g.Lmax;
+  s.S = (size_t)g.B * g.nh * g.ntiles * g.per_tile;
   s.lse_off = 0;
   s.ot_off = align_up(s.S * sizeof(float));
   s.bytes = s.ot_off + align_up(s.S * g.d * sizeof(float));
@@ -38,7 +38,7 @@ struct BwdLayout {
 };
 inline BwdLayout bwd_layout(const Geom& g) {
   BwdLayout b;
-  b.S = (size_t)g.B * g.nh * g.ntiles * g.Lmax;
+  b.S = (size_t)g.B * g.nh * g.ntiles * g.per_tile;
   size_t vec = align_up(b.S * sizeof(float));
   size_t mat = align_up(b.S * g.d * sizeof(float));
   b.lse_off = 0;

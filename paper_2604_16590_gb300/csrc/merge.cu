@@ -34,20 +34,20 @@ __device__ __forceinline__ bool cover_of(const Geom& g, int64_t i, Cover& c) {
   return multi;
 }
 
-// row of grid position p inside tile (k[0], k[1], k[2])
-__device__ __forceinline__ int row_in_tile(const Geom& g, const int p[3], const int k[3], int* tile) {
-  int lo[3], e[3];
+// slot of grid position p in tile (k[0], k[1], k[2]) of batch*head bh
+__device__ __forceinline__ int64_t slot_in_tile(const Geom& g, int bh, const int p[3], const int k[3]) {
+  int e[3], l[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    int l = k[a] * g.c[a] - g.h[a];
-    int h = (k[a] + 1) * g.c[a] + g.h[a];
-    l = l < 0 ? 0 : l;
-    h = h > g.G[a] ? g.G[a] : h;
-    lo[a] = l;
-    e[a] = h - l;
+    int lo = k[a] * g.c[a] - g.h[a];
+    int hi = (k[a] + 1) * g.c[a] + g.h[a];
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > g.G[a] ? g.G[a] : hi;
+    e[a] = hi - lo;
+    l[a] = p[a] - lo;
   }
-  *tile = (k[0] * g.n[1] + k[1]) * g.n[2] + k[2];
-  return ((p[0] - lo[0]) * e[1] + (p[1] - lo[1])) * e[2] + (p[2] - lo[2]);
+  const int tile = (k[0] * g.n[1] + k[1]) * g.n[2] + k[2];
+  return slot_of(g, bh, tile, e, l);
 }
 
 // One thread per (batch*head, token, float4 of d).
@@ -70,10 +70,8 @@ __global__ void __launch_bounds__(kThreads) merge_fwd_kernel(Geom g, const float
     for (k[0] = c.k0[0]; k[0] <= c.k1[0]; ++k[0])
       for (k[1] = c.k0[1]; k[1] <= c.k1[1]; ++k[1])
         for (k[2] = c.k0[2]; k[2] <= c.k1[2]; ++k[2]) {
-          int tile;
-          int r = row_in_tile(g, c.p, k, &tile);
           float w = tile_weight(g, c.p, k);
-          float4 o = __ldg(reinterpret_cast<const float4*>(ot + slot_index(g, bh, tile, r) * g.d) + f);
+          float4 o = __ldg(reinterpret_cast<const float4*>(ot + slot_in_tile(g, bh, c.p, k) * g.d) + f);
           acc.x = fmaf(w, o.x, acc.x);
           acc.y = fmaf(w, o.y, acc.y);
           acc.z = fmaf(w, o.z, acc.z);
@@ -88,7 +86,9 @@ __global__ void __launch_bounds__(kThreads) merge_fwd_kernel(Geom g, const float
 // Per (batch*head, tile, row) slot: fold the merge weight c = w_t / sum w into
 // the log-sum-exp (lse2c = lse2 - log2 c, so exp2(s - lse2c) = c P) and form
 // D = dOut . O_t.  O_t is the output itself for single-cover rows, else the
-// FP32 per-tile value saved by the forward.  One lane group of d/4 lanes per slot.
+// FP32 per-tile value saved by the forward.  Slots of a box that fall outside
+// the tile get lse2c = +inf and D = 0, so the tensor-core backward can run
+// whole boxes without masking queries.  One lane group of d/4 lanes per slot.
 template <typename OutT, typename InT>
 __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* __restrict__ out,
                                                             const InT* __restrict__ dout,
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* 
                                                             const float* __restrict__ ot,
                                                             float* __restrict__ lse2c, float* __restrict__ dd) {
   const int F4 = g.d / 4;  // 8, 16 or 32 lanes per slot
-  const int64_t S = (int64_t)g.B * g.nh * g.ntiles * g.Lmax;
+  const int64_t S = (int64_t)g.B * g.nh * g.ntiles * g.per_tile;
   const int64_t total = S * F4;
   // the grid-stride loop keeps all lanes of a group together (total % F4 == 0)
   for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx - threadIdx.x % 32 < total;
@@ -104,19 +104,20 @@ __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* 
     const bool in = idx < total;
     const int f = (int)(idx % F4);
     const int64_t slot = in ? idx / F4 : 0;
-    const int r = (int)(slot % g.Lmax);
-    const int64_t ut = slot / g.Lmax;
+    const int within = (int)(slot % g.per_tile);
+    const int64_t ut = slot / g.per_tile;
     const int tile = (int)(ut % g.ntiles);
     const int bh = (int)(ut / g.ntiles);
     TileBox tb;
     tile_box(g, tile, tb);
-    const bool valid = in && r < tb.L;
+    int lr[3];
+    const bool valid = in && slot_local(g, tb.e, within >> 7, within & 127, lr) && (within >> 7) < g.nbmax_tot;
     float part = 0.f;
     int p[3];
     int64_t tok = 0;
     bool single = true;
     if (valid) {
-      tok = tile_token(g, tb, r);
+      tok = grid_token(g, tb, lr);
       token_pos(g, tok, p);
       single = single_cover(g, p);
       const int64_t off = ((int64_t)bh * g.N + tok) * g.d + 4 * f;
@@ -125,6 +126,11 @@ __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* 
       part = a.x * o.x + a.y * o.y + a.z * o.z + a.w * o.w;
     }
     for (int o = 1; o < F4; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (in && !valid && f == 0) {
+      // padding slot of a box that sticks out of the tile: probability 0
+      lse2c[slot] = INFINITY;
+      dd[slot] = 0.f;
+    }
     if (valid && f == 0) {
       float lc = lse2[slot];
       if (!single) {
@@ -170,9 +176,7 @@ __global__ void __launch_bounds__(kThreads) merge_bwd_kernel(Geom g, const float
     for (k[0] = c.k0[0]; k[0] <= c.k1[0]; ++k[0])
       for (k[1] = c.k0[1]; k[1] <= c.k1[1]; ++k[1])
         for (k[2] = c.k0[2]; k[2] <= c.k1[2]; ++k[2]) {
-          int tile;
-          int r = row_in_tile(g, c.p, k, &tile);
-          const int64_t off = slot_index(g, bh, tile, r) * g.d;
+          const int64_t off = slot_in_tile(g, bh, c.p, k) * g.d;
           float4 x = __ldg(reinterpret_cast<const float4*>(dq_s + off) + f);
           float4 y = __ldg(reinterpret_cast<const float4*>(dk_s + off) + f);
           float4 z = __ldg(reinterpret_cast<const float4*>(dv_s + off) + f);
@@ -205,7 +209,7 @@ cudaError_t launch_merge_fwd(const Geom& g, const float* ot, void* out, int out_
 
 cudaError_t launch_bwd_prep(const Geom& g, const void* out, int out_dtype, const void* dout, int in_dtype,
                             const float* lse2, const float* ot, float* lse2c, float* dd, cudaStream_t st) {
-  const int64_t total = (int64_t)g.B * g.nh * g.ntiles * g.Lmax * (g.d / 4);
+  const int64_t total = (int64_t)g.B * g.nh * g.ntiles * g.per_tile * (g.d / 4);
   const unsigned grid = grid_for(total);
   using bf = __nv_bfloat16;
   if (out_dtype == GATTN_BF16 && in_dtype == GATTN_BF16)

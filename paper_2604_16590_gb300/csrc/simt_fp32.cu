@@ -159,7 +159,9 @@ __global__ void __launch_bounds__(kThreads) simt_fwd_kernel(Geom g, const float*
   }
   if (!active) return;
   const float inv = 1.f / l;
-  const int64_t slot = slot_index(g, bh, tile, r);
+  int lr[3];
+  tile_local(tb, r, lr);
+  const int64_t slot = slot_of(g, bh, tile, tb.e, lr);
   if (grp == 0) lse2[slot] = m + log2f(l);
   int p[3];
   token_pos(g, tok, p);
@@ -194,7 +196,9 @@ __global__ void __launch_bounds__(kThreads) simt_dq_kernel(Geom g, const float* 
   const bool active = r < tb.L;
   const int64_t base = (int64_t)bh * g.N * D;
   int64_t tok = active ? tile_token(g, tb, r) : 0;
-  const int64_t slot = slot_index(g, bh, tile, active ? r : 0);
+  int lr[3];
+  tile_local(tb, active ? r : 0, lr);
+  const int64_t slot = slot_of(g, bh, tile, tb.e, lr);
 
   float q[kDPT], go[kDPT], acc[kDPT], accc[kDPT];
   if (active) {
@@ -278,7 +282,9 @@ __global__ void __launch_bounds__(kThreads) simt_dkdv_kernel(Geom g, const float
     stage_rows<D>(g, tb, i0, Q + base, dO + base, Qs, Os);
     if (threadIdx.x < kKC) {
       int i = i0 + threadIdx.x;
-      int64_t s = slot_index(g, bh, tile, i < tb.L ? i : 0);
+      int li[3];
+      tile_local(tb, i < tb.L ? i : 0, li);
+      int64_t s = slot_of(g, bh, tile, tb.e, li);
       Ls[threadIdx.x] = i < tb.L ? lse2c[s] : INFINITY;
       Ds[threadIdx.x] = i < tb.L ? dd[s] : 0.f;
     }
@@ -303,7 +309,9 @@ __global__ void __launch_bounds__(kThreads) simt_dkdv_kernel(Geom g, const float
     }
   }
   if (!active) return;
-  const int64_t slot = slot_index(g, bh, tile, r);
+  int lr[3];
+  tile_local(tb, r, lr);
+  const int64_t slot = slot_of(g, bh, tile, tb.e, lr);
   int p[3];
   token_pos(g, tok, p);
   if (single_cover(g, p)) {

@@ -50,17 +50,15 @@ struct FwdCfg {
 
 struct FwdArgs {
   Geom g;
-  BlockShape bs;
   void* out;
   float* lse2;
   float* ot;
-  int nbmax;  // blocks per tile, padded (product over dims of nbmax)
-  int items;  // B*nh * ntiles * nbmax
+  int items;  // B*nh * ntiles * nbmax_tot
 };
 
 __device__ __forceinline__ void decode_item(const FwdArgs& a, int w, int& bh, int& tile, int& qb) {
-  qb = w % a.nbmax;
-  const int r = w / a.nbmax;
+  qb = w % a.g.nbmax_tot;
+  const int r = w / a.g.nbmax_tot;
   tile = r % a.g.ntiles;
   bh = r / a.g.ntiles;
 }
@@ -276,7 +274,6 @@ __global__ void __launch_bounds__(192, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const Geom& g = a.g;
-  const BlockShape& bs = a.bs;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -290,10 +287,10 @@ __global__ void __launch_bounds__(192, 1)
         int bh, tile, qb;
         decode_item(a, w, bh, tile, qb);
         TileBlocks tbk;
-        tile_blocks(g, bs, tile, tbk);
+        tile_blocks(g, tile, tbk);
         if (qb >= tbk.NB) continue;
         int o[3];
-        block_origin(tbk, bs, qb, o);
+        block_origin(g, tbk, qb, o);
         if (!(ok = mbar_wait<set_status_fwd>(q_empty, (W & 1) ^ 1, abort_flag))) break;
         mbar_arrive_expect_tx(q_full, C::kBlock);
         q_arm = 1;
@@ -303,7 +300,7 @@ __global__ void __launch_bounds__(192, 1)
                       tbk.tb.lo[0] + o[0], bh);
         for (int j = 0; j < tbk.NB; ++j, ++G) {
           const uint32_t st = G % C::kStages, n = G / C::kStages;
-          block_origin(tbk, bs, j, o);
+          block_origin(g, tbk, j, o);
           const int c1 = tbk.tb.lo[2] + o[2], c2 = tbk.tb.lo[1] + o[1], c3 = tbk.tb.lo[0] + o[0];
           if (!(ok = mbar_wait<set_status_fwd>(k_empty + st, (n & 1) ^ 1, abort_flag))) break;
           mbar_arrive_expect_tx(k_full + st, C::kBlock);
@@ -357,7 +354,7 @@ __global__ void __launch_bounds__(192, 1)
         int bh, tile, qb;
         decode_item(a, w, bh, tile, qb);
         TileBlocks tbk;
-        tile_blocks(g, bs, tile, tbk);
+        tile_blocks(g, tile, tbk);
         if (qb >= tbk.NB) continue;
         if (!(ok = mbar_wait<set_status_fwd>(q_full, W & 1, abort_flag))) break;
         tc_fence_after();
@@ -397,11 +394,11 @@ __global__ void __launch_bounds__(192, 1)
       int bh, tile, qb;
       decode_item(a, w, bh, tile, qb);
       TileBlocks tbk;
-      tile_blocks(g, bs, tile, tbk);
+      tile_blocks(g, tile, tbk);
       if (qb >= tbk.NB) continue;
       int qo[3], ql[3];
-      block_origin(tbk, bs, qb, qo);
-      block_row(bs, qo, row, ql);
+      block_origin(g, tbk, qb, qo);
+      block_row(g, qo, row, ql);
       const bool qvalid = inside(tbk, ql);
 
       RowState<D> rs;
@@ -409,15 +406,15 @@ __global__ void __launch_bounds__(192, 1)
       for (int j = 0; j < tbk.NB; ++j, ++G) {
         const uint32_t sb = G & 1;
         int ko[3];
-        block_origin(tbk, bs, j, ko);
+        block_origin(g, tbk, j, ko);
         // key validity of the block's 128 columns, one ballot per 32 columns
         uint32_t kmask[4];
-        const bool full = block_full(tbk, bs, ko);
+        const bool full = block_full(g, tbk, ko);
         if (!full) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             int kl[3];
-            block_row(bs, ko, c * 32 + lane, kl);
+            block_row(g, ko, c * 32 + lane, kl);
             kmask[c] = __ballot_sync(0xffffffffu, inside(tbk, kl));
           }
         }
@@ -440,8 +437,7 @@ __global__ void __launch_bounds__(192, 1)
       tc_fence_before();
       // ---- epilogue
       if (qvalid) {
-        const int r_local = (ql[0] * tbk.tb.e[1] + ql[1]) * tbk.tb.e[2] + ql[2];
-        const int64_t slot = slot_index(g, bh, tile, r_local);
+        const int64_t slot = tile_slot0(g, bh, tile) + qb * 128 + row;
         a.lse2[slot] = rs.m + __log2f(rs.l);
         const int p[3] = {tbk.tb.lo[0] + ql[0], tbk.tb.lo[1] + ql[1], tbk.tb.lo[2] + ql[2]};
         const int64_t tok = ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2];
@@ -474,19 +470,17 @@ cudaError_t run_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
   using C = FwdCfg<D>;
   FwdArgs a;
   a.g = g;
-  a.bs = choose_block_shape(g);
   a.out = out;
   a.lse2 = lse2;
   a.ot = ot;
-  a.nbmax = a.bs.nbmax[0] * a.bs.nbmax[1] * a.bs.nbmax[2];
-  const int64_t items = (int64_t)g.B * g.nh * g.ntiles * a.nbmax;
+  const int64_t items = (int64_t)g.B * g.nh * g.ntiles * g.nbmax_tot;
   if (items >= (1LL << 31)) return cudaErrorNotSupported;
   a.items = (int)items;
   const int BH = g.B * g.nh;
   CUtensorMap mq, mk, mv;
-  if (!make_tmap_5d(&mq, q, D, g.G[2], g.G[1], g.G[0], BH, a.bs.bx, a.bs.by, a.bs.bt) ||
-      !make_tmap_5d(&mk, k, D, g.G[2], g.G[1], g.G[0], BH, a.bs.bx, a.bs.by, a.bs.bt) ||
-      !make_tmap_5d(&mv, v, D, g.G[2], g.G[1], g.G[0], BH, a.bs.bx, a.bs.by, a.bs.bt))
+  if (!make_tmap_5d(&mq, q, D, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
+      !make_tmap_5d(&mk, k, D, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
+      !make_tmap_5d(&mv, v, D, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt))
     return cudaErrorInvalidValue;
   auto kern = sm103_fwd_kernel<D, OutT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);

@@ -65,3 +65,39 @@ def test_bf16_forward_is_deterministic():
     a, _ = gattn.forward(q.to(dev), k.to(dev), v.to(dev), tiling, out_dtype=torch.float32)
     b, _ = gattn.forward(q.to(dev), k.to(dev), v.to(dev), tiling, out_dtype=torch.float32)
     assert torch.equal(a, b)
+
+
+BWD_CASES = [c for c in FWD_CASES if c[0] != "long_tile_ring_wrap"] + [
+    ("bwd_long_tile", 1, 1, 64, (4, 32, 32), (4, 16, 16), (0, 4, 4)),
+]
+
+
+@pytest.mark.parametrize("name,B,nh,d,grid,core,halo", BWD_CASES, ids=[c[0] for c in BWD_CASES])
+@pytest.mark.parametrize("out_dtype", [torch.float32, torch.bfloat16], ids=["out_fp32", "out_bf16"])
+def test_bf16_backward_matches_oracle(name, B, nh, d, grid, core, halo, out_dtype):
+    q, k, v, go = _inputs(B, nh, d, grid, 500 + len(name))
+    dev = torch.device("cuda:0")
+    tq, tk, tv, tg = (t.to(dev) for t in (q, k, v, go))
+    tiling = gattn.Tiling(grid, core, halo)
+    out, saved = gattn.forward(tq, tk, tv, tiling, out_dtype=out_dtype)
+    dq, dk, dv = gattn.backward(tq, tk, tv, out, tg, saved, tiling)
+    st = gattn.gattn_stream_status()
+    assert st == 0, gattn.STATUS.get(st, st)
+    geo = oracle.Geometry(B, nh, d, *grid, core, halo)
+    f64 = [t.double().numpy() for t in (q, k, v, go)]
+    rq, rk, rv = oracle.backward(geo, *f64)
+    for key, got, ref in (("dq", dq, rq), ("dk", dk, rk), ("dv", dv, rv)):
+        assert_close(f"{name}/{key}", got.double().cpu().numpy(), ref, MAX_REL, RMS_REL)
+
+
+def test_bf16_backward_is_deterministic():
+    grid, core, halo = (4, 32, 32), (2, 16, 16), (1, 4, 4)
+    q, k, v, go = _inputs(1, 2, 64, grid, 12)
+    dev = torch.device("cuda:0")
+    tq, tk, tv, tg = (t.to(dev) for t in (q, k, v, go))
+    tiling = gattn.Tiling(grid, core, halo)
+    out, saved = gattn.forward(tq, tk, tv, tiling, out_dtype=torch.float32)
+    a = gattn.backward(tq, tk, tv, out, tg, saved, tiling)
+    b = gattn.backward(tq, tk, tv, out, tg, saved, tiling)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
