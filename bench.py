@@ -1,0 +1,403 @@
+"""Benchmark of the STORM-GPA hot path (arXiv 2604.16590, Sec. III-C) on GB300.
+
+One step = one forward + backward of the halo-tiled global propagation
+attention over one batch of synthetic tokens, through the C ABI of libgattn
+(gattn_fwd + gattn_bwd: tile kernels, Hann-weighted merge, backward prep,
+dK/dV and dQ kernels, gradient merge).  Default workload: 32 frames x 64 x 128
+lat-lon patch tokens (N = 262,144), batch 4, 16 heads, d = 64, BF16 inputs
+iid N(0, 0.5), upstream gradient iid N(0, 1), Tiles = 16 (core 32x16x32,
+halo 0/4/8).  Q, K, V are 6.4 GB (> L2), so no L2 flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gattn|reference]
+
+N > 1 runs under torchrun, one rank per GPU: every rank runs its own replica
+of the workload (independent (batch, head) units; no collective on the data
+path) -> weak scaling.  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "global-attn fwd+bwd Gtokens/s & HBM-roofline %, BF16 vs FP32; serve p50/p99"
+UNIT = "Gtokens/s"
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
+# from the ncu capture summarised in profiles/ (None until captured for the
+# kernel as built now).
+TRAFFIC_PER_LAUNCH = {}
+
+
+def _extents(G, c, h):
+    return [min((k + 1) * c + h, G) - max(k * c - h, 0) for k in range(-(-G // c))]
+
+
+def sum_L2(w):
+    """sum over tiles of L_t^2 (separable over the three dimensions)."""
+    out = 1
+    for a in range(3):
+        out *= sum(e * e for e in _extents(w.grid[a], w.core[a], w.halo[a]))
+    return out
+
+
+def kernel_flops(w):
+    """Algorithmic FLOPs per launch of each tile kernel (all batch*heads)."""
+    s = sum_L2(w) * w.B * w.nh * w.d
+    return {"fwd_tiles": 4 * s, "bwd_dkdv": 8 * s, "bwd_dq": 6 * s}
+
+
+def sum_L(w):
+    out = 1
+    for a in range(3):
+        out *= sum(_extents(w.grid[a], w.core[a], w.halo[a]))
+    return out
+
+
+def algorithmic_bytes(w, in_bytes=2, out_bytes=2):
+    """Unique HBM bytes of one fwd+bwd step: forward reads Q, K, V and writes
+    Out and the per-row log-sum-exp; backward reads Q, K, V, Out, dOut and the
+    log-sum-exp and writes dQ, dK, dV.  Halo re-reads and merge scratch are
+    overhead, not counted."""
+    nd = w.B * w.N * w.nh * w.d
+    lse = 4 * sum_L(w) * w.B * w.nh
+    fwd = 3 * nd * in_bytes + nd * out_bytes + lse
+    bwd = 4 * nd * in_bytes + nd * out_bytes + lse + 3 * nd * out_bytes
+    return fwd + bwd
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], p["bf16_tflops"], p["bf16_tflops_sustained"], "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = (
+        "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+        "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+        "clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+            )
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        hi = max(sm)
+        loaded = [x for x in sm if x >= 0.5 * hi] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(w, q, k, v, go, target_s=12.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample: query rows of
+    one (batch*head, tile) unit, forward + backward.  Returns (Gtokens/s
+    extrapolated to the whole step, threads, description)."""
+    import numpy as np
+
+    import oracle
+
+    geo = oracle.Geometry(1, 1, w.d, *w.grid, w.core, w.halo)
+    f64 = [np.ascontiguousarray(t[0, 0].double().cpu().numpy())[None, None] for t in (q, k, v, go)]
+    # the largest tile: the middle one
+    nt = geo.num_tiles()
+    tile = max(range(nt), key=geo.tile_rows)
+    L = geo.tile_rows(tile)
+    t0 = time.perf_counter()
+    oracle.unit_fwd_bwd(geo, *f64, 0, tile, 0, 64)
+    t64 = time.perf_counter() - t0
+    R = int(min(L, max(64, 64 * target_s / max(t64, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.unit_fwd_bwd(geo, *f64, 0, tile, 0, R)
+    tR = time.perf_counter() - t0
+    pairs_total = sum_L2(w) * w.B * w.nh
+    step_s = tR * pairs_total / (R * L)
+    gtok = w.B * w.N / step_s / 1e9
+    desc = (f"{R} query rows x {L} keys of one (batch*head, tile) unit, forward + backward, "
+            f"{tR:.1f} s; scaled by (query, key) pairs to the full step ({pairs_total:.3e} pairs)")
+    return gtok, oracle.threads(), desc, tR
+
+
+def run_reference(args, w):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # the oracle sample reads one (batch, head) slice: draw just that slice
+    from paper_2604_16590_gb300.inputs import qkv, upstream_grad
+
+    shape1 = (1, 1, w.N, w.d)
+    q, k, v = qkv(shape1, w.seed, w.std, w.dtype)
+    go = upstream_grad(shape1, w.seed, w.dtype)
+    vals, secs = [], []
+    for _ in range(args.warmup):
+        oracle_sample(w, q, k, v, go, target_s=2.0)
+    for _ in range(args.steps):
+        g, cores, desc, t = oracle_sample(w, q, k, v, go, target_s=8.0)
+        vals.append(g)
+        secs.append(t)
+    value = statistics.median(vals)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "B": w.B, "heads": w.nh, "d": w.d, "grid": list(w.grid),
+                   "core": list(w.core), "halo": list(w.halo)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    del torch
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gattn", choices=["gattn", "reference"])
+    ap.add_argument("--workload", default="c2_262k_p")
+    ap.add_argument("--fp32-steps", type=int, default=1, help="timed steps of the plain FP32 form (0 = skip)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+
+    from paper_2604_16590_gb300.inputs import WORKLOADS
+
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2604_16590_gb300 import build, gattn
+    from paper_2604_16590_gb300.inputs import qkv, upstream_grad
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build()
+    gattn.load_library()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---------------------------------------------------------------- inputs (per rank)
+    q, k, v = qkv(w.shape, w.seed + 1000 * rank, w.std, "bf16", device=dev)
+    go = upstream_grad(w.shape, w.seed + 1000 * rank, "bf16", device=dev)
+    tiling = gattn.Tiling(w.grid, w.core, w.halo)
+    desc = gattn.desc_for(q, tiling, torch.bfloat16)
+    out = torch.empty_like(q)
+    dq, dk, dv = torch.empty_like(q), torch.empty_like(q), torch.empty_like(q)
+    saved = torch.empty(gattn.gattn_saved_bytes(desc), dtype=torch.uint8, device=dev)
+    ws = torch.empty(gattn.gattn_bwd_workspace_bytes(desc), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(qq=q, kk=k, vv=v, gg=go, d=desc, o=out, a=dq, b=dk, c=dv, sv=saved, wsp=ws):
+        gattn.check(gattn.gattn_fwd(d, qq, kk, vv, o, sv, stream=stream), "gattn_fwd")
+        gattn.check(gattn.gattn_bwd(d, qq, kk, vv, o, gg, sv, a, b, c, wsp, stream=stream), "gattn_bwd")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = gattn.gattn_stream_status(stream)
+    if st != 0:
+        raise RuntimeError(f"device status after warm-up: {gattn.STATUS.get(st, st)}")
+
+    # ---------------------------------------------------------------- timed region (device-resident inputs)
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    gattn.gattn_profile_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    kstats = gattn.gattn_profile_read()
+    gattn.gattn_profile_enable(False)
+    st = gattn.gattn_stream_status(stream)
+    if st != 0:
+        raise RuntimeError(f"device status after timed steps: {gattn.STATUS.get(st, st)}")
+    ms = e0.elapsed_time(e1) / args.steps
+    t_max = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms = float(t_max.item())
+    tokens_per_step = w.B * w.N * world
+    value = tokens_per_step / (ms * 1e-3) / 1e9
+    launches = sum(n for n, _ in kstats.values())
+
+    # ---------------------------------------------------------------- roofline of the dominant kernel
+    hbm_peak, tc_peak, tc_sust, peak_src = measured_peaks()
+    flops = kernel_flops(w)
+    kernels = {}
+    for name, (n, tot) in kstats.items():
+        per = tot / n
+        ent = {"launches": n, "ms_per_launch": per, "share": tot / (ms * args.steps)}
+        if name in flops:
+            ent["tflops"] = flops[name] / (per * 1e-3) / 1e12
+        kernels[name] = ent
+    dom = max(kstats, key=lambda nm: kstats[nm][1])
+    dom_ms = kstats[dom][1] / kstats[dom][0]
+    achieved = flops.get(dom, 0) / (dom_ms * 1e-3) / 1e12
+    roofline = {
+        "kernel": dom, "bound": "tensor", "achieved": achieved, "peak": tc_sust, "unit": "TFLOP/s",
+        "frac": achieved / tc_sust, "peak_source": f"bf16_tflops_sustained of {peak_src}",
+        "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+    }
+    alg_bytes = algorithmic_bytes(w)
+    hbm = {"algorithmic_bytes_per_step": alg_bytes, "gbs": alg_bytes / (ms * 1e-3) / 1e9,
+           "frac_of_hbm": alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, "peak_gbs": hbm_peak, "peak_source": peak_src}
+
+    # ---------------------------------------------------------------- e2e through the public API with host buffers
+    host_in = [torch.empty(w.shape, dtype=torch.bfloat16, pin_memory=True) for _ in range(4)]
+    for h, t in zip(host_in, (q, k, v, go)):
+        h.copy_(t)
+    host_out = [torch.empty(w.shape, dtype=torch.bfloat16, pin_memory=True) for _ in range(4)]
+    dq_in, dk_in, dv_in, dgo_in = (torch.empty_like(q) for _ in range(4))
+    e2e_steps = max(1, min(args.steps, 3))
+
+    def e2e_step():
+        for d_, h_ in zip((dq_in, dk_in, dv_in, dgo_in), host_in):
+            d_.copy_(h_, non_blocking=True)
+        step(qq=dq_in, kk=dk_in, vv=dv_in, gg=dgo_in)
+        for h_, d_ in zip(host_out, (out, dq, dk, dv)):
+            h_.copy_(d_, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3) / e2e_steps
+    t_e2e = torch.tensor([e2e_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_ms = float(t_e2e.item())
+    bytes_io = 4 * q.numel() * q.element_size()
+    del dq_in, dk_in, dv_in, dgo_in, host_in, host_out
+
+    # ---------------------------------------------------------------- the plain FP32 form on the same values
+    fp32 = None
+    if args.fp32_steps > 0:
+        q32, k32, v32, g32 = (t.float() for t in (q, k, v, go))
+        d32 = gattn.desc_for(q32, tiling, torch.float32)
+        o32 = torch.empty_like(q32)
+        a32, b32, c32 = (torch.empty_like(q32) for _ in range(3))
+        sv32 = torch.empty(gattn.gattn_saved_bytes(d32), dtype=torch.uint8, device=dev)
+        ws32 = torch.empty(gattn.gattn_bwd_workspace_bytes(d32), dtype=torch.uint8, device=dev)
+
+        def step32():
+            step(qq=q32, kk=k32, vv=v32, gg=g32, d=d32, o=o32, a=a32, b=b32, c=c32, sv=sv32, wsp=ws32)
+
+        step32()
+        torch.cuda.synchronize()
+        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e4.record(stream)
+        for _ in range(args.fp32_steps):
+            step32()
+        e5.record(stream)
+        torch.cuda.synchronize()
+        ms32 = e4.elapsed_time(e5) / args.fp32_steps
+        fp32 = {"value": w.B * w.N * world / (ms32 * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms32,
+                "steps": args.fp32_steps, "bf16_speedup": ms32 / ms}
+        del q32, k32, v32, g32, o32, a32, b32, c32, sv32, ws32
+
+    # ---------------------------------------------------------------- CPU oracle baseline (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sl = (slice(0, 1), slice(0, 1))
+        g, cores, desc_s, _ = oracle_sample(w, q[sl].cpu(), k[sl].cpu(), v[sl].cpu(), go[sl].cpu())
+        cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc_s}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": w.name, "B": w.B, "heads": w.nh, "d": w.d, "grid": list(w.grid),
+                       "core": list(w.core), "halo": list(w.halo), "tiles": gattn.gattn_num_tiles(desc),
+                       "tokens_per_step": tokens_per_step, "in_dtype": "bf16", "out_dtype": "bf16",
+                       "l2": "inputs 6.4 GB per rank > L2, no flush",
+                       "parallelism": f"replicas x{world} (independent batch*head units, no collective)"},
+            "clocks": clk,
+            "e2e": {"value": w.B * w.N * world / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "hbm": hbm,
+            "kernels": kernels,
+            "fp32_form": fp32,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -160,6 +160,27 @@ gattn_status gattn_bwd(const gattn_desc *desc, const void *q, const void *k, con
  * GATTN_ERR_DEVICE_BOUNDS; GATTN_ERR_CUDA if the stream reported an error. */
 gattn_status gattn_stream_status(gattn_stream_t stream);
 
+/*
+ * Per-kernel device timing (diagnostics, used by the benchmark).  While
+ * enabled, every kernel launch of this library is bracketed by a pair of CUDA
+ * events recorded on its launch stream.  gattn_profile_read synchronises on
+ * those events and returns, per kernel name, the number of launches and the
+ * summed device time since the last enable.  Host-side state, process-wide,
+ * guarded by a mutex; at most 65536 launches are recorded per enable.
+ */
+typedef struct {
+  char name[24];    /* "fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd" */
+  int64_t launches;
+  double total_ms;
+} gattn_kernel_stat;
+
+/* enable != 0 clears the record and starts recording; 0 stops. */
+gattn_status gattn_profile_enable(int32_t enable);
+
+/* Fills up to `max` entries; returns the number of kernel names recorded, or
+ * a negative gattn_status on a CUDA error. */
+int32_t gattn_profile_read(gattn_kernel_stat *out, int32_t max);
+
 #ifdef __cplusplus
 }
 #endif

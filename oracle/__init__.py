@@ -180,8 +180,8 @@ def key_rows(geo: Geometry, q, k, v, dout, keys):
 
 
 def unit_fwd_bwd(geo: Geometry, q, k, v, dout, bh: int, tile: int, r0: int, r1: int) -> None:
-    """Per-tile backward (with its forward recompute) of query rows [r0, r1) of
-    one (batch*head, tile) unit; used to time the oracle on a bounded sample."""
+    """Per-tile forward and backward of query rows [r0, r1) of one
+    (batch*head, tile) unit; used to time the oracle on a bounded sample."""
     _load().gpa_unit_fwd_bwd(
         _ptr(geo.g), WINDOWS[geo.window], geo.scale, _ptr(q), _ptr(k), _ptr(v), _ptr(dout), int(bh), int(tile), int(r0), int(r1)
     )

@@ -458,7 +458,8 @@ void gpa_key_rows(const int32_t *g, int window, double scale, const double *q, c
 }
 
 /* Work of one (batch*head, tile) unit restricted to query rows [r0, r1):
- * the per-tile backward of those rows, which recomputes their forward.  Used only to time the
+ * the per-tile forward of those rows and their backward (which recomputes the
+ * forward, as gpa_backward does).  Used only to time the
  * oracle on a bounded sample of a large workload. */
 void gpa_unit_fwd_bwd(const int32_t *g, int window, double scale, const double *q,
                       const double *k, const double *v, const double *dout, int bh, int tile,
@@ -480,8 +481,12 @@ void gpa_unit_fwd_bwd(const int32_t *g, int window, double scale, const double *
     int a = r0 + (int)((int64_t)(r1 - r0) * id / cnt);
     int b = r0 + (int)((int64_t)(r1 - r0) * (id + 1) / cnt);
     double *buf = (double *)calloc((size_t)3 * tb.L * d, sizeof(double));
+    double *O = (double *)malloc(sizeof(double) * (size_t)(b > a ? b - a : 1) * d);
+    /* the forward of these rows, then their backward (which recomputes it) */
+    tile_attention(g, scale, &tb, q + off, k + off, v + off, a, b, O, NULL);
     tile_backward(g, window, scale, &tb, q + off, k + off, v + off, dout + off, a, b, buf,
                   buf + (size_t)tb.L * d, buf + (size_t)2 * tb.L * d);
+    free(O);
     free(buf);
   }
 }

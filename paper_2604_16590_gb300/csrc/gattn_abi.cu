@@ -4,9 +4,59 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace gattn {
+
+// ------------------------------------------------------------ kernel timing
+namespace {
+const char* const kKernelNames[kKCount] = {"fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd"};
+struct ProfRecord {
+  int kernel;
+  cudaEvent_t start, stop;
+};
+struct ProfState {
+  std::mutex mu;
+  bool on = false;
+  std::vector<ProfRecord> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t open_start[kKCount] = {};
+};
+ProfState& prof() {
+  static ProfState s;
+  return s;
+}
+cudaEvent_t take_event(ProfState& p) {
+  if (!p.pool.empty()) {
+    cudaEvent_t e = p.pool.back();
+    p.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+}  // namespace
+
+void prof_begin(int kernel, cudaStream_t st) {
+  ProfState& p = prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  if (!p.on || p.recs.size() >= 65536) return;
+  cudaEvent_t e = take_event(p);
+  if (e && cudaEventRecord(e, st) == cudaSuccess) p.open_start[kernel] = e;
+}
+
+void prof_end(int kernel, cudaStream_t st) {
+  ProfState& p = prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  if (!p.on || !p.open_start[kernel]) return;
+  cudaEvent_t e = take_event(p);
+  if (e && cudaEventRecord(e, st) == cudaSuccess) p.recs.push_back({kernel, p.open_start[kernel], e});
+  p.open_start[kernel] = nullptr;
+}
 
 static bool dtype_ok(int32_t t) { return t == GATTN_BF16 || t == GATTN_FP32; }
 
@@ -175,14 +225,20 @@ gattn_status gattn_fwd(const gattn_desc* desc, const void* q, const void* k, con
   float* lse2 = reinterpret_cast<float*>(static_cast<char*>(saved) + sl.lse_off);
   float* ot = reinterpret_cast<float*>(static_cast<char*>(saved) + sl.ot_off);
   cudaError_t e;
+  prof_begin(kKFwdTiles, st);
   if (desc->in_dtype == GATTN_FP32)
     e = launch_simt_fwd(g, (const float*)q, (const float*)k, (const float*)v, out, desc->out_dtype, lse2, ot, st);
   else
     e = launch_sm103_fwd(g, (const __nv_bfloat16*)q, (const __nv_bfloat16*)k, (const __nv_bfloat16*)v, out,
                          desc->out_dtype, lse2, ot, desc->flags, st);
+  prof_end(kKFwdTiles, st);
   if (e == cudaErrorNotSupported) return GATTN_ERR_UNSUPPORTED;
   if (e != cudaSuccess) return GATTN_ERR_CUDA;
-  if (has_overlap(g)) e = launch_merge_fwd(g, ot, out, desc->out_dtype, st);
+  if (has_overlap(g)) {
+    prof_begin(kKMergeFwd, st);
+    e = launch_merge_fwd(g, ot, out, desc->out_dtype, st);
+    prof_end(kKMergeFwd, st);
+  }
   return from_cuda(e);
 }
 
@@ -206,7 +262,9 @@ gattn_status gattn_bwd(const gattn_desc* desc, const void* q, const void* k, con
   float* dq_s = reinterpret_cast<float*>(w + bl.dq_off);
   float* dk_s = reinterpret_cast<float*>(w + bl.dk_off);
   float* dv_s = reinterpret_cast<float*>(w + bl.dv_off);
+  prof_begin(kKBwdPrep, st);
   cudaError_t e = launch_bwd_prep(g, out, desc->out_dtype, dout, desc->in_dtype, lse2, ot, lse2c, dd, st);
+  prof_end(kKBwdPrep, st);
   if (e != cudaSuccess) return GATTN_ERR_CUDA;
   if (desc->in_dtype == GATTN_FP32)
     e = launch_simt_bwd(g, (const float*)q, (const float*)k, (const float*)v, (const float*)dout, lse2c, dd, dq, dk,
@@ -217,8 +275,52 @@ gattn_status gattn_bwd(const gattn_desc* desc, const void* q, const void* k, con
                          desc->flags, st);
   if (e == cudaErrorNotSupported) return GATTN_ERR_UNSUPPORTED;
   if (e != cudaSuccess) return GATTN_ERR_CUDA;
-  if (has_overlap(g)) e = launch_merge_bwd(g, dq_s, dk_s, dv_s, dq, dk, dv, desc->out_dtype, st);
+  if (has_overlap(g)) {
+    prof_begin(kKMergeBwd, st);
+    e = launch_merge_bwd(g, dq_s, dk_s, dv_s, dq, dk, dv, desc->out_dtype, st);
+    prof_end(kKMergeBwd, st);
+  }
   return from_cuda(e);
+}
+
+gattn_status gattn_profile_enable(int32_t enable) {
+  ProfState& p = prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  if (enable) {
+    for (auto& r : p.recs) {
+      p.pool.push_back(r.start);
+      p.pool.push_back(r.stop);
+    }
+    p.recs.clear();
+  }
+  p.on = enable != 0;
+  return GATTN_OK;
+}
+
+int32_t gattn_profile_read(gattn_kernel_stat* out, int32_t max) {
+  ProfState& p = prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  int64_t n[kKCount] = {};
+  double ms[kKCount] = {};
+  for (auto& r : p.recs) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.stop) != cudaSuccess || cudaEventElapsedTime(&t, r.start, r.stop) != cudaSuccess)
+      return -(int32_t)GATTN_ERR_CUDA;
+    n[r.kernel] += 1;
+    ms[r.kernel] += t;
+  }
+  int32_t count = 0;
+  for (int k = 0; k < kKCount; ++k) {
+    if (!n[k]) continue;
+    if (out && count < max) {
+      memset(out[count].name, 0, sizeof(out[count].name));
+      strncpy(out[count].name, kKernelNames[k], sizeof(out[count].name) - 1);
+      out[count].launches = n[k];
+      out[count].total_ms = ms[k];
+    }
+    ++count;
+  }
+  return count;
 }
 
 gattn_status gattn_stream_status(gattn_stream_t stream) {

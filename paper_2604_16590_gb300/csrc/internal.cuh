@@ -73,6 +73,11 @@ uint32_t fetch_status_merge();
 uint32_t fetch_status_sm103_fwd();
 uint32_t fetch_status_sm103_bwd();
 
+// ---- per-kernel device timing (gattn_profile_*); no-ops unless enabled
+enum KernelId : int { kKFwdTiles = 0, kKMergeFwd, kKBwdPrep, kKBwdDkdv, kKBwdDq, kKMergeBwd, kKCount };
+void prof_begin(int kernel, cudaStream_t st);
+void prof_end(int kernel, cudaStream_t st);
+
 // ---- launchers (return cudaGetLastError() of their launches)
 cudaError_t launch_simt_fwd(const Geom& g, const float* q, const float* k, const float* v, void* out,
                             int out_dtype, float* lse2, float* ot, cudaStream_t st);

@@ -338,11 +338,15 @@ cudaError_t simt_bwd_dispatch(const Geom& g, const float* q, const float* k, con
                               float* dk_s, float* dv_s, cudaStream_t st) {
   constexpr int RPC = kThreads / (D / kDPT);
   dim3 grid((g.Lmax + RPC - 1) / RPC, g.ntiles, g.B * g.nh);
+  prof_begin(kKBwdDq, st);
   simt_dq_kernel<D, OutT><<<grid, kThreads, 0, st>>>(g, q, k, v, dout, lse2c, dd, static_cast<OutT*>(dq), dq_s);
+  prof_end(kKBwdDq, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  prof_begin(kKBwdDkdv, st);
   simt_dkdv_kernel<D, OutT><<<grid, kThreads, 0, st>>>(g, q, k, v, dout, lse2c, dd, static_cast<OutT*>(dk),
                                                        static_cast<OutT*>(dv), dk_s, dv_s);
+  prof_end(kKBwdDkdv, st);
   return cudaGetLastError();
 }
 

@@ -710,12 +710,16 @@ cudaError_t run_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
   auto k1 = sm103_dkdv_kernel<D, OutT>;
   cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, KvCfg<D>::kSmem);
   if (e != cudaSuccess) return e;
+  prof_begin(kKBwdDkdv, st);
   k1<<<grid, 192, KvCfg<D>::kSmem, st>>>(mq, mk, mv, mdo, a);
+  prof_end(kKBwdDkdv, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   auto k2 = sm103_dq_kernel<D, OutT>;
   e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, QCfg<D>::kSmem);
   if (e != cudaSuccess) return e;
+  prof_begin(kKBwdDq, st);
   k2<<<grid, 192, QCfg<D>::kSmem, st>>>(mq, mk, mv, mdo, a);
+  prof_end(kKBwdDq, st);
   return cudaGetLastError();
 }
 

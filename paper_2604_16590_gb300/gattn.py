@@ -47,6 +47,10 @@ class GattnError(RuntimeError):
         super().__init__(f"{what}: {STATUS.get(self.status, self.status)}")
 
 
+class gattn_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
 class gattn_desc(ctypes.Structure):
     _fields_ = [
         ("B", ctypes.c_int32),
@@ -90,6 +94,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gattn_fwd": ([D, P, P, P, P, P, S, P], ctypes.c_int),
         "gattn_bwd": ([D, P, P, P, P, P, P, S, P, P, P, P, S, P], ctypes.c_int),
         "gattn_stream_status": ([P], ctypes.c_int),
+        "gattn_profile_enable": ([ctypes.c_int32], ctypes.c_int),
+        "gattn_profile_read": ([ctypes.POINTER(gattn_kernel_stat), ctypes.c_int32], ctypes.c_int32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -177,6 +183,19 @@ def gattn_bwd(desc, q, k, v, out, dout, saved, dq, dk, dv, ws, saved_bytes=None,
 
 def gattn_stream_status(stream=None) -> int:
     return load_library().gattn_stream_status(_stream(stream))
+
+
+def gattn_profile_enable(enable: bool) -> int:
+    return load_library().gattn_profile_enable(1 if enable else 0)
+
+
+def gattn_profile_read() -> dict:
+    """{kernel name: (launches, total device ms)} since the last enable."""
+    arr = (gattn_kernel_stat * 16)()
+    n = load_library().gattn_profile_read(arr, 16)
+    if n < 0:
+        raise GattnError(-n, "gattn_profile_read")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n, 16))}
 
 
 def check(status: int, what: str = "gattn") -> None:
