@@ -155,6 +155,34 @@ gattn_status gattn_bwd(const gattn_desc *desc, const void *q, const void *k, con
                        void *dq, void *dk, void *dv, void *ws, size_t ws_bytes,
                        gattn_stream_t stream);
 
+/*
+ * Forward without a caller-provided saved buffer, for callers that cannot
+ * allocate device memory: code that runs under a memory manager which owns
+ * all of HBM after start-up (a serving process that partitions the device up
+ * front, or a host framework whose operator interface passes only input and
+ * output tensors) has no way to obtain the scratch gattn_fwd needs.  This
+ * entry point has no counterpart in the paper.
+ *
+ * Same computation and arguments as gattn_fwd minus `saved`: the forward's
+ * scratch lives in a device array of GATTN_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading this library holds until the process exits.  Problems whose
+ * gattn_saved_bytes(desc) exceeds that size are rejected with
+ * GATTN_ERR_WORKSPACE before any launch.  The call itself allocates nothing
+ * (no cudaMalloc / cudaFree or allocating library routine).
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (no call depends on them: everything read is written
+ * first in the same call).  Calls whose work overlaps on the GPU -- on
+ * different streams, or from different host threads -- race on the array:
+ * serialise them.  The result cannot be passed to gattn_bwd (the saved state
+ * is not the caller's).
+ */
+#define GATTN_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+gattn_status gattn_fwd_noalloc(const gattn_desc *desc, const void *q, const void *k, const void *v,
+                               void *out, gattn_stream_t stream);
+
 /* Synchronises `stream`, then returns (and clears) the device status word of
  * this library on the current device: GATTN_OK, GATTN_ERR_TIMEOUT or
  * GATTN_ERR_DEVICE_BOUNDS; GATTN_ERR_CUDA if the stream reported an error. */

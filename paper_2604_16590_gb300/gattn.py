@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gattn_fwd": ([D, P, P, P, P, P, S, P], ctypes.c_int),
         "gattn_bwd": ([D, P, P, P, P, P, P, S, P, P, P, P, S, P], ctypes.c_int),
         "gattn_stream_status": ([P], ctypes.c_int),
+        "gattn_fwd_noalloc": ([D, P, P, P, P, P], ctypes.c_int),
         "gattn_profile_enable": ([ctypes.c_int32], ctypes.c_int),
         "gattn_profile_read": ([ctypes.POINTER(gattn_kernel_stat), ctypes.c_int32], ctypes.c_int32),
     }
@@ -179,6 +180,15 @@ def gattn_bwd(desc, q, k, v, out, dout, saved, dq, dk, dv, ws, saved_bytes=None,
         ctypes.byref(desc), _ptr(q), _ptr(k), _ptr(v), _ptr(out), _ptr(dout), _ptr(saved), _nbytes(saved, saved_bytes),
         _ptr(dq), _ptr(dk), _ptr(dv), _ptr(ws), _nbytes(ws, ws_bytes), _stream(stream),
     )
+
+
+GATTN_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def gattn_fwd_noalloc(desc, q, k, v, out, stream=None) -> int:
+    """Forward whose scratch is the library's own device array (no allocation);
+    see include/gattn.h for the size limit and the sharing rules."""
+    return load_library().gattn_fwd_noalloc(ctypes.byref(desc), _ptr(q), _ptr(k), _ptr(v), _ptr(out), _stream(stream))
 
 
 def gattn_stream_status(stream=None) -> int:
