@@ -30,8 +30,8 @@ inline SavedLayout saved_layout(const Geom& g) {
 }
 
 // Backward workspace.
-//   lse2c : float[S]      log2-domain LSE minus log2(w_t / sum w) (folds dO_t scaling into P)
-//   dd    : float[S]      D = dOut . O_t per slot
+//   lse2c : float[S]      -(log2-domain LSE - log2(w_t / sum w)) (folds the dO_t scaling into P), negated
+//   dd    : float[S]      -D, D = dOut . O_t per slot, negated
 //   dq_s, dk_s, dv_s : float[S * d]  per-tile gradients of multiply-covered rows
 struct BwdLayout {
   size_t S, lse_off, dd_off, dq_off, dk_off, dv_off, bytes;

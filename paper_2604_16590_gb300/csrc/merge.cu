@@ -84,11 +84,14 @@ __global__ void __launch_bounds__(kThreads) merge_fwd_kernel(Geom g, const float
 }
 
 // Per (batch*head, tile, row) slot: fold the merge weight c = w_t / sum w into
-// the log-sum-exp (lse2c = lse2 - log2 c, so exp2(s - lse2c) = c P) and form
+// the log-sum-exp (lse' = lse2 - log2 c, so exp2(s - lse') = c P) and form
 // D = dOut . O_t.  O_t is the output itself for single-cover rows, else the
-// FP32 per-tile value saved by the forward.  Slots of a box that fall outside
-// the tile get lse2c = +inf and D = 0, so the tensor-core backward can run
-// whole boxes without masking queries.  One lane group of d/4 lanes per slot.
+// FP32 per-tile value saved by the forward.  Both are stored negated
+// (-lse', -D) so that the backward kernels form exp2(s log2e + (-lse')) and
+// dP + (-D) with single fused/packed instructions.  Slots of a box that fall
+// outside the tile get -lse' = -inf and -D = 0, so the tensor-core backward
+// can run whole boxes without masking queries.  One lane group of d/4 lanes
+// per slot.
 template <typename OutT, typename InT>
 __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* __restrict__ out,
                                                             const InT* __restrict__ dout,
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* 
     for (int o = 1; o < F4; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if (in && !valid && f == 0) {
       // padding slot of a box that sticks out of the tile: probability 0
-      lse2c[slot] = INFINITY;
+      lse2c[slot] = -INFINITY;
       dd[slot] = 0.f;
     }
     if (valid && f == 0) {
@@ -148,8 +151,8 @@ __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* 
             for (k[2] = c.k0[2]; k[2] <= c.k1[2]; ++k[2]) ws += tile_weight(g, p, k);
         lc -= log2f(wt / ws);
       }
-      lse2c[slot] = lc;
-      dd[slot] = part;
+      lse2c[slot] = -lc;
+      dd[slot] = -part;
     }
   }
 }

@@ -173,8 +173,9 @@ __global__ void __launch_bounds__(kThreads) simt_fwd_kernel(Geom g, const float*
 }
 
 // ---------------------------------------------------------------- backward: dQ
-// P = exp2(s q.k log2e - lse2c) already carries the merge weight w_t / sum w,
-// so dS = P (dOut.v - D) and dQ_t = s sum_j dS k_j.
+// P = exp2(s q.k log2e - lse') already carries the merge weight w_t / sum w,
+// so dS = P (dOut.v - D) and dQ_t = s sum_j dS k_j (the workspace holds -lse'
+// and -D).
 template <int D, typename OutT>
 __global__ void __launch_bounds__(kThreads) simt_dq_kernel(Geom g, const float* __restrict__ Q,
                                                            const float* __restrict__ K,
@@ -208,8 +209,8 @@ __global__ void __launch_bounds__(kThreads) simt_dq_kernel(Geom g, const float* 
 #pragma unroll
     for (int e = 0; e < kDPT; ++e) q[e] = go[e] = 0.f;
   }
-  const float L2 = active ? lse2c[slot] : INFINITY;
-  const float Dr = active ? dd[slot] : 0.f;
+  const float nL = active ? lse2c[slot] : -INFINITY;  // -lse' (negated in the workspace)
+  const float nD = active ? dd[slot] : 0.f;           // -D
 #pragma unroll
   for (int e = 0; e < kDPT; ++e) acc[e] = 0.f;
 
@@ -225,8 +226,8 @@ __global__ void __launch_bounds__(kThreads) simt_dq_kernel(Geom g, const float* 
       float dp = dot_group<D>(go, Vs + jj * D, grp);
       sk = group_sum<TPR>(sk);
       dp = group_sum<TPR>(dp);
-      float p = (j0 + jj < tb.L) ? exp2f(sk * g.scale_log2 - L2) : 0.f;
-      float ds = p * (dp - Dr);
+      float p = (j0 + jj < tb.L) ? exp2f(fmaf(sk, g.scale_log2, nL)) : 0.f;
+      float ds = p * (dp + nD);
       axpy_group<D>(accc, ds, Ks + jj * D, grp);
     }
 #pragma unroll
@@ -285,8 +286,8 @@ __global__ void __launch_bounds__(kThreads) simt_dkdv_kernel(Geom g, const float
       int li[3];
       tile_local(tb, i < tb.L ? i : 0, li);
       int64_t s = slot_of(g, bh, tile, tb.e, li);
-      Ls[threadIdx.x] = i < tb.L ? lse2c[s] : INFINITY;
-      Ds[threadIdx.x] = i < tb.L ? dd[s] : 0.f;
+      Ls[threadIdx.x] = i < tb.L ? lse2c[s] : -INFINITY;  // -lse'
+      Ds[threadIdx.x] = i < tb.L ? dd[s] : 0.f;           // -D
     }
     __syncthreads();
 #pragma unroll
@@ -297,8 +298,8 @@ __global__ void __launch_bounds__(kThreads) simt_dkdv_kernel(Geom g, const float
       float dp = dot_group<D>(vr, Os + ii * D, grp);
       sk = group_sum<TPR>(sk);
       dp = group_sum<TPR>(dp);
-      float p = exp2f(sk * g.scale_log2 - Ls[ii]);
-      float ds = p * (dp - Ds[ii]);
+      float p = exp2f(fmaf(sk, g.scale_log2, Ls[ii]));
+      float ds = p * (dp + Ds[ii]);
       axpy_group<D>(cdv, p, Os + ii * D, grp);
       axpy_group<D>(cdk, ds, Qs + ii * D, grp);
     }

@@ -13,16 +13,18 @@
 //       dS = P' (dP - D) (keys outside the tile masked), dQ += dS K_j.
 //
 // The merge weight of the Hann-weighted overlap average (arXiv 2604.16590,
-// Sec. III-C) enters through the per-row statistics the prep pass writes:
-// lse' = lse - log2(w_t / sum w) makes P' = (w_t / sum w) P, i.e. the
-// probabilities of the per-tile gradient dO_t = (w_t / sum w) dOut, and
-// D = dOut . O_t.  P is recomputed from lse' (never stored).  Rows covered by
+// Sec. III-C) enters through the per-row statistics the prep pass writes
+// (negated, -lse' and -D, so each element costs one packed FMA for the exp2
+// argument and one packed add + multiply for dS): lse' = lse - log2(w_t/sum w)
+// makes P' = (w_t / sum w) P, the probabilities of the per-tile gradient
+// dO_t = (w_t / sum w) dOut, and D = dOut . O_t.  P is recomputed from lse' (never stored).  Rows covered by
 // one tile are written straight to dQ/dK/dV; multiply-covered rows go to FP32
 // per-tile slots that the merge kernel sums in fixed tile order.
 //
-// Warp roles as in the forward: warp 0 TMA producer, warp 1 TMEM allocator +
-// single-thread MMA issuer, warps 2..5 elementwise math + epilogue (one TMEM
-// lane = one block row per thread).
+// Warp roles: warp 0 TMA producer, warp 1 TMEM allocator + single-thread MMA
+// issuer, warps 2..9 elementwise math + epilogue: one TMEM lane = one block row,
+// two warps per lane quadrant, each taking half of the row's columns (eight
+// math warps keep two warps per SM sub-partition to hide TMEM and MUFU latency).
 #include "internal.cuh"
 #include "sm103_common.cuh"
 
@@ -58,25 +60,17 @@ __device__ __forceinline__ void decode_item(const Geom& g, int w, int& bh, int& 
 // byte offset of K-step ks (16 elements) in a 128-byte-swizzled K-major operand
 __device__ __forceinline__ uint32_t kmaj_off(int ks) { return (ks >> 2) * 16384 + (ks & 3) * 32; }
 
-// Write 64 BF16 values (32 packed words) as one 128-byte row of a 128B-swizzled
-// K-major operand buffer.
-__device__ __forceinline__ void store_row64(uint32_t buf, int row, const uint32_t (&pk)[32]) {
-#pragma unroll
-  for (int u = 0; u < 8; ++u)
-    st_shared_v4(buf + row * 128 + ((u ^ (row & 7)) << 4), pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
-}
-
 // Epilogue of one D-wide FP32 TMEM row (this thread's lane), scaled by `mul`:
 // to `out` (OutT) if the row is covered by one tile, else to the FP32 slot
 // `scr`; nothing if the row lies outside the tile.  The TMEM loads are
 // warp-synchronous (.sync.aligned), so every lane executes them and only the
 // global stores depend on the lane's row.
-template <int D, typename OutT>
+template <int NCOLS, typename OutT>
 __device__ __forceinline__ void tmem_row_epilogue(uint32_t taddr, float mul, bool valid, bool single, OutT* out,
                                                   float* scr) {
   uint32_t r[32];
 #pragma unroll
-  for (int c = 0; c < D / 32; ++c) {
+  for (int c = 0; c < NCOLS / 32; ++c) {
     tmem_ld32(taddr + c * 32, r);
     tmem_wait_ld(r);
     if (valid) {
@@ -92,6 +86,20 @@ __device__ __forceinline__ void tmem_row_epilogue(uint32_t taddr, float mul, boo
     }
   }
 }
+
+// Write 32 BF16 values (16 packed words) as half of one 128-byte row (16-byte
+// units 4*ch .. 4*ch+3) of a 128B-swizzled K-major operand buffer.
+__device__ __forceinline__ void store_row32(uint32_t buf, int row, int ch, const uint32_t (&pk)[16]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    st_shared_v4(buf + row * 128 + (((ch * 4 + u) ^ (row & 7)) << 4), pk[4 * u], pk[4 * u + 1], pk[4 * u + 2],
+                 pk[4 * u + 3]);
+}
+
+// Math warps: kMathWarps warps, two per TMEM lane quadrant; the two warps of a
+// quadrant share its 32 rows and split each row's columns in half.
+constexpr int kMathWarps = 8;
+constexpr int kThreads = 64 + 32 * kMathWarps;
 
 // =============================================================== dK / dV
 template <int D>
@@ -115,7 +123,7 @@ struct KvCfg {
 };
 
 template <int D, typename OutT>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     sm103_dkdv_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
                       const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tdo,
                       const BwdArgs a) {
@@ -147,12 +155,12 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(st_full + s, 1);
-      mbar_init(st_empty + s, 4);
-      mbar_init(p_full + s, 4);
+      mbar_init(st_empty + s, kMathWarps);
+      mbar_init(p_full + s, kMathWarps);
       mbar_init(p_empty + s, 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);
+    mbar_init(acc_empty, kMathWarps);
     mbar_init(drain, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -303,6 +311,7 @@ __global__ void __launch_bounds__(192, 1)
   } else {
     // ------------------------------------------------------------ elementwise + epilogue (row = key)
     const int quad = warp & 3;
+    const int ch = (warp - 2) >> 2;  // which 32 of the 64 query columns of a half block
     const int row = quad * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     const uint32_t sP = smem_u32(smem + C::kP);
@@ -324,49 +333,45 @@ __global__ void __launch_bounds__(192, 1)
           const uint32_t b = H & 1;
           if (!(ok = WAIT(st_full + b, (H >> 1) & 1))) break;
           tc_fence_after();
-          uint32_t s0[32], s1[32], d0[32], d1[32];
-          tmem_ld32(tl + C::kColST + b * 64, s0);
-          tmem_ld32(tl + C::kColST + b * 64 + 32, s1);
-          tmem_ld32(tl + C::kColDP + b * 64, d0);
-          tmem_ld32(tl + C::kColDP + b * 64 + 32, d1);
-          tmem_wait_ld(s0);
-          tmem_wait_ld(s1);
-          tmem_wait_ld(d0);
-          tmem_wait_ld(d1);
+          uint32_t sv[32], dv[32];
+          tmem_ld32(tl + C::kColST + b * 64 + ch * 32, sv);
+          tmem_ld32(tl + C::kColDP + b * 64 + ch * 32, dv);
+          tmem_wait_ld(sv);
+          tmem_wait_ld(dv);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(st_empty + b);
-          uint32_t pp[32], pd[32];
-          const float* L = sL + half * 64;
-          const float* Dq = sD + half * 64;
+          // P' = exp2(s S^T log2e - lse'), dS^T = P' (dP^T - D); the stage holds -lse', -D
+          uint32_t pp[16], pd[16];
+          const float4* nL4 = reinterpret_cast<const float4*>(sL + half * 64 + ch * 32);
+          const float4* nD4 = reinterpret_cast<const float4*>(sD + half * 64 + ch * 32);
+          const uint64_t s2 = f2pack(sl2, sl2);
 #pragma unroll
-          for (int c = 0; c < 32; c += 2) {
-            const float p0 = ex2(fmaf(__uint_as_float(s0[c]), sl2, -L[c]));
-            const float p1 = ex2(fmaf(__uint_as_float(s0[c + 1]), sl2, -L[c + 1]));
-            const float e0 = p0 * (__uint_as_float(d0[c]) - Dq[c]);
-            const float e1 = p1 * (__uint_as_float(d0[c + 1]) - Dq[c + 1]);
-            pp[c >> 1] = pack_bf16(p0, p1);
-            pd[c >> 1] = pack_bf16(e0, e1);
-          }
-#pragma unroll
-          for (int c = 0; c < 32; c += 2) {
-            const float p0 = ex2(fmaf(__uint_as_float(s1[c]), sl2, -L[32 + c]));
-            const float p1 = ex2(fmaf(__uint_as_float(s1[c + 1]), sl2, -L[32 + c + 1]));
-            const float e0 = p0 * (__uint_as_float(d1[c]) - Dq[32 + c]);
-            const float e1 = p1 * (__uint_as_float(d1[c + 1]) - Dq[32 + c + 1]);
-            pp[16 + (c >> 1)] = pack_bf16(p0, p1);
-            pd[16 + (c >> 1)] = pack_bf16(e0, e1);
+          for (int c4 = 0; c4 < 8; ++c4) {
+            const float4 l = nL4[c4], dn = nD4[c4];
+            const int c = 4 * c4;
+            float a0, a1, a2, a3;
+            f2unpack(ffma2(u2pack(sv[c], sv[c + 1]), s2, f2pack(l.x, l.y)), a0, a1);
+            f2unpack(ffma2(u2pack(sv[c + 2], sv[c + 3]), s2, f2pack(l.z, l.w)), a2, a3);
+            const float p0 = ex2(a0), p1 = ex2(a1), p2 = ex2(a2), p3 = ex2(a3);
+            float e0, e1, e2, e3;
+            f2unpack(fmul2(f2pack(p0, p1), fadd2(u2pack(dv[c], dv[c + 1]), f2pack(dn.x, dn.y))), e0, e1);
+            f2unpack(fmul2(f2pack(p2, p3), fadd2(u2pack(dv[c + 2], dv[c + 3]), f2pack(dn.z, dn.w))), e2, e3);
+            pp[2 * c4] = pack_bf16(p0, p1);
+            pp[2 * c4 + 1] = pack_bf16(p2, p3);
+            pd[2 * c4] = pack_bf16(e0, e1);
+            pd[2 * c4 + 1] = pack_bf16(e2, e3);
           }
           if (!(ok = WAIT(p_empty + b, ((H >> 1) & 1) ^ 1))) break;
-          store_row64(sP + b * 32768, row, pp);
-          store_row64(sP + b * 32768 + 16384, row, pd);
+          store_row32(sP + b * 32768, row, ch, pp);
+          store_row32(sP + b * 32768 + 16384, row, ch, pd);
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) mbar_arrive(p_full + b);
         }
       }
       if (!ok) break;
-      // ---- epilogue: this thread's key row of dK, dV
+      // ---- epilogue: this thread's key row of dK, dV (its half of the columns)
       if (!(ok = WAIT(acc_full, W & 1))) break;
       tc_fence_after();
       int ko[3], kl[3];
@@ -377,10 +382,13 @@ __global__ void __launch_bounds__(192, 1)
       const int64_t tok = kvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
       const bool single = kvalid && single_cover(g, p);
       const int64_t slot = tile_slot0(g, bh, tile) + kb * 128 + row;
-      tmem_row_epilogue<D, OutT>(tl + C::kColDK, g.scale, kvalid, single,
-                                 static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * D, a.dk_s + slot * D);
-      tmem_row_epilogue<D, OutT>(tl + C::kColDV, 1.f, kvalid, single,
-                                 static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * D, a.dv_s + slot * D);
+      const int c0 = ch * (D / 2);
+      tmem_row_epilogue<D / 2, OutT>(tl + C::kColDK + c0, g.scale, kvalid, single,
+                                     static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * D + c0,
+                                     a.dk_s + slot * D + c0);
+      tmem_row_epilogue<D / 2, OutT>(tl + C::kColDV + c0, 1.f, kvalid, single,
+                                     static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * D + c0,
+                                     a.dv_s + slot * D + c0);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
@@ -415,23 +423,29 @@ struct QCfg {
   static constexpr uint32_t kColS = 0, kColDP = 128, kColDQ = 256;
 };
 
+// dS = P' (dP - D) for 32 key columns of this thread's query row, packed to
+// BF16; nL = -lse', nD = -D of the row; keys outside the tile masked to 0.
 template <bool MASK>
 __device__ __forceinline__ void dq_half(const uint32_t (&s)[32], const uint32_t (&dp)[32], uint32_t mbits, float sl2,
-                                        float L, float Dr, uint32_t (&pk)[32], int base) {
+                                        float nL, float nD, uint32_t (&pk)[16]) {
+  const uint64_t s2 = f2pack(sl2, sl2), nl2 = f2pack(nL, nL), nd2 = f2pack(nD, nD);
 #pragma unroll
   for (int c = 0; c < 32; c += 2) {
-    float p0 = ex2(fmaf(__uint_as_float(s[c]), sl2, -L));
-    float p1 = ex2(fmaf(__uint_as_float(s[c + 1]), sl2, -L));
+    float a0, a1;
+    f2unpack(ffma2(u2pack(s[c], s[c + 1]), s2, nl2), a0, a1);
+    float p0 = ex2(a0), p1 = ex2(a1);
     if (MASK) {
       p0 = (mbits >> c) & 1u ? p0 : 0.f;
       p1 = (mbits >> (c + 1)) & 1u ? p1 : 0.f;
     }
-    pk[base + (c >> 1)] = pack_bf16(p0 * (__uint_as_float(dp[c]) - Dr), p1 * (__uint_as_float(dp[c + 1]) - Dr));
+    float e0, e1;
+    f2unpack(fmul2(f2pack(p0, p1), fadd2(u2pack(dp[c], dp[c + 1]), nd2)), e0, e1);
+    pk[c >> 1] = pack_bf16(e0, e1);
   }
 }
 
 template <int D, typename OutT>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     sm103_dq_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
                     const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tdo,
                     const BwdArgs a) {
@@ -463,12 +477,12 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(s_full + s, 1);
-      mbar_init(s_empty + s, 4);
-      mbar_init(ds_full + s, 4);
+      mbar_init(s_empty + s, kMathWarps);
+      mbar_init(ds_full + s, kMathWarps);
       mbar_init(ds_empty + s, 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);
+    mbar_init(acc_empty, kMathWarps);
     mbar_init(drain, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -597,6 +611,7 @@ __global__ void __launch_bounds__(192, 1)
   } else {
     // ------------------------------------------------------------ elementwise + epilogue (row = query)
     const int quad = warp & 3;
+    const int ch = (warp - 2) >> 2;  // which 32 of the 64 key columns of a half block
     const int row = quad * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     const uint32_t sDS = smem_u32(smem + C::kDS);
@@ -610,47 +625,40 @@ __global__ void __launch_bounds__(192, 1)
       tile_blocks(g, tile, tbk);
       if (qb >= tbk.NB) continue;
       const int64_t qslot = tile_slot0(g, bh, tile) + qb * 128 + row;
-      const float L = a.lse2c[qslot];
-      const float Dr = a.dd[qslot];
+      const float nL = a.lse2c[qslot];  // -lse' (-inf for padding rows)
+      const float nD = a.dd[qslot];     // -D
       for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
         int ko[3];
         block_origin(g, tbk, j, ko);
         const bool full = block_full(g, tbk, ko);
-        uint32_t kmask[4] = {~0u, ~0u, ~0u, ~0u};
+        uint32_t kmask[2] = {~0u, ~0u};
         if (!full) {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
+          for (int h2 = 0; h2 < 2; ++h2) {
             int kl[3];
-            block_row(g, ko, c * 32 + lane, kl);
-            kmask[c] = __ballot_sync(0xffffffffu, inside(tbk, kl));
+            block_row(g, ko, h2 * 64 + ch * 32 + lane, kl);
+            kmask[h2] = __ballot_sync(0xffffffffu, inside(tbk, kl));
           }
         }
         for (int half = 0; half < 2; ++half, ++H) {
           const uint32_t b = H & 1;
           if (!(ok = WAIT(s_full + b, (H >> 1) & 1))) break;
           tc_fence_after();
-          uint32_t s0[32], s1[32], d0[32], d1[32];
-          tmem_ld32(tl + C::kColS + b * 64, s0);
-          tmem_ld32(tl + C::kColS + b * 64 + 32, s1);
-          tmem_ld32(tl + C::kColDP + b * 64, d0);
-          tmem_ld32(tl + C::kColDP + b * 64 + 32, d1);
-          tmem_wait_ld(s0);
-          tmem_wait_ld(s1);
-          tmem_wait_ld(d0);
-          tmem_wait_ld(d1);
+          uint32_t sv[32], dv[32];
+          tmem_ld32(tl + C::kColS + b * 64 + ch * 32, sv);
+          tmem_ld32(tl + C::kColDP + b * 64 + ch * 32, dv);
+          tmem_wait_ld(sv);
+          tmem_wait_ld(dv);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(s_empty + b);
-          uint32_t pk[32];
-          if (full) {
-            dq_half<false>(s0, d0, 0u, sl2, L, Dr, pk, 0);
-            dq_half<false>(s1, d1, 0u, sl2, L, Dr, pk, 16);
-          } else {
-            dq_half<true>(s0, d0, kmask[2 * half], sl2, L, Dr, pk, 0);
-            dq_half<true>(s1, d1, kmask[2 * half + 1], sl2, L, Dr, pk, 16);
-          }
+          uint32_t pk[16];
+          if (full)
+            dq_half<false>(sv, dv, 0u, sl2, nL, nD, pk);
+          else
+            dq_half<true>(sv, dv, kmask[half], sl2, nL, nD, pk);
           if (!(ok = WAIT(ds_empty + b, ((H >> 1) & 1) ^ 1))) break;
-          store_row64(sDS + b * 16384, row, pk);
+          store_row32(sDS + b * 16384, row, ch, pk);
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) mbar_arrive(ds_full + b);
@@ -666,8 +674,10 @@ __global__ void __launch_bounds__(192, 1)
       const int p[3] = {tbk.tb.lo[0] + ql[0], tbk.tb.lo[1] + ql[1], tbk.tb.lo[2] + ql[2]};
       const int64_t tok = qvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
       const bool single = qvalid && single_cover(g, p);
-      tmem_row_epilogue<D, OutT>(tl + C::kColDQ, g.scale, qvalid, single,
-                                 static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * D, a.dq_s + qslot * D);
+      const int c0 = ch * (D / 2);
+      tmem_row_epilogue<D / 2, OutT>(tl + C::kColDQ + c0, g.scale, qvalid, single,
+                                     static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * D + c0,
+                                     a.dq_s + qslot * D + c0);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
@@ -711,14 +721,14 @@ cudaError_t run_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
   cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, KvCfg<D>::kSmem);
   if (e != cudaSuccess) return e;
   prof_begin(kKBwdDkdv, st);
-  k1<<<grid, 192, KvCfg<D>::kSmem, st>>>(mq, mk, mv, mdo, a);
+  k1<<<grid, kThreads, KvCfg<D>::kSmem, st>>>(mq, mk, mv, mdo, a);
   prof_end(kKBwdDkdv, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   auto k2 = sm103_dq_kernel<D, OutT>;
   e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, QCfg<D>::kSmem);
   if (e != cudaSuccess) return e;
   prof_begin(kKBwdDq, st);
-  k2<<<grid, 192, QCfg<D>::kSmem, st>>>(mq, mk, mv, mdo, a);
+  k2<<<grid, kThreads, QCfg<D>::kSmem, st>>>(mq, mk, mv, mdo, a);
   prof_end(kKBwdDq, st);
   return cudaGetLastError();
 }

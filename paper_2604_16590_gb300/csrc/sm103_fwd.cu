@@ -5,21 +5,27 @@
 // Per extended tile t (arXiv 2604.16590, Sec. III-C), for every 128-query block
 // of the tile the CTA streams the tile's 128-key blocks (flash-style online
 // softmax, the FlashAttention of Sec. III-D Level 5):
-//   S_j  = Q K_j^T                      tcgen05, BF16 x BF16 -> FP32 (TMEM)
+//   S_j  = Q K_j^T                      tcgen05, A = Q from TMEM, B = K from smem -> FP32 TMEM
 //   m_j  = max(m_{j-1}, rowmax(s S_j))  log2 domain
-//   P_j  = exp2(s S_j log2e - m_j)      -> BF16, shared memory (SW128, K-major)
-//   PV_j = P_j V_j                      tcgen05 -> FP32 (TMEM), V read MN-major
+//   P_j  = exp2(s S_j log2e - m_j)      -> BF16 pairs written into TMEM (tcgen05.st)
+//   PV_j = P_j V_j                      tcgen05, A = P from TMEM, B = V (MN-major) from smem
 //   O   <- O exp2(m_O - m_{j}) + PV_j   FP32 registers (no TMEM read-modify-write)
+// Keeping Q and P in tensor memory leaves shared memory with only the TMA'd K/V
+// blocks and the B-operand reads (about 64 KB per 128x128 block instead of
+// 144 KB): the 128 B/clk shared-memory read path otherwise limits the MMAs.
 // The epilogue writes O / l for rows covered by one tile straight to the output
 // and parks multiply-covered rows (FP32) for the deterministic Hann merge, and
 // stores the row log-sum-exp for the backward.
 //
-// Warp roles (192 threads, one CTA per SM, persistent over work items
+// Warp roles (320 threads, one CTA per SM, persistent over work items
 // (batch*head, tile, query block)):
 //   warp 0      TMA producer (Q once per item; K_j, V_j through a ring of stages)
 //   warp 1      TMEM allocator + single-thread tcgen05 MMA issuer
-//   warps 2..5  softmax + epilogue, one query row per thread (TMEM lane)
-// TMEM: columns [0,256) two S buffers, [256, 256+d) the P V block product.
+//   warps 2..9  softmax + epilogue: one query row per TMEM lane, two warps per
+//               lane quadrant splitting each row's keys and output columns
+//               (two math warps per SM sub-partition hide TMEM/MUFU latency)
+// TMEM: columns [0,256) two S buffers, [256, 256+d) the P V block product,
+// then 64 columns of P (BF16 pairs) and d/2 columns of Q (BF16 pairs).
 #include "internal.cuh"
 #include "sm103_common.cuh"
 
@@ -33,19 +39,23 @@ template <int D>
 struct FwdCfg {
   static constexpr int kHalves = D / 64;            // 128-byte column chunks of a row
   static constexpr int kBlock = 128 * D * 2;        // bytes of one Q/K/V block
-  static constexpr int kStages = D == 64 ? 3 : 2;   // K/V ring depth
-  static constexpr int kPBytes = 128 * 128 * 2;
+  static constexpr int kStages = D == 64 ? 4 : 2;   // K/V ring depth
   static constexpr int kQ = 0;
   static constexpr int kK = kQ + kBlock;
   static constexpr int kV = kK + kStages * kBlock;
-  static constexpr int kP = kV + kStages * kBlock;
-  static constexpr int kBar = kP + kPBytes;
-  // q_full, q_empty, k_full[S], k_empty[S], v_full[S], v_empty[S], s_full[2], s_empty[2], p_full, pv_done, drain
-  static constexpr int kNumBars = 2 + 4 * kStages + 4 + 3;
+  static constexpr int kBar = kV + kStages * kBlock;
+  // q_full, q_empty, qt_full, k_full[S], k_empty[S], v_full[S], v_empty[S], s_full[2], s_empty[2],
+  // p_full, pv_done[2], o_empty, drain
+  static constexpr int kNumBars = 3 + 4 * kStages + 4 + 5;
   static constexpr int kMisc = kBar + kNumBars * 8;
-  static constexpr int kSmem = kMisc + 16 + 1024;   // + slack for 1024-byte alignment
+  static constexpr int kRed = kMisc + 16;           // float [3 slots][2 half][128 rows]
+  static constexpr int kSmem = kRed + 3072 + 1024;  // + slack for 1024-byte alignment
   static constexpr uint32_t kTmemCols = 512;
-  static constexpr uint32_t kColO = 256;
+  static constexpr int kPBufs = D == 64 ? 2 : 1;    // P buffers in TMEM
+  static constexpr uint32_t kColO = 256;            // O accumulator, D columns
+  static constexpr uint32_t kColP = 256 + D;        // kPBufs x 64 columns: 128 keys as BF16 pairs
+  static constexpr uint32_t kColQ = 256 + D + 64 * kPBufs;  // D/2 columns: the query block as BF16 pairs
+  static_assert(kColQ + D / 2 <= kTmemCols, "TMEM budget");
 };
 
 struct FwdArgs {
@@ -65,41 +75,20 @@ __device__ __forceinline__ void decode_item(const FwdArgs& a, int w, int& bh, in
 
 __device__ void set_status_fwd(uint32_t c) { set_status(c); }
 
-// Fold block Gp's P V (TMEM, relative to max mprev) into the FP32 register
-// accumulator O (relative to max mO): O <- O exp2(mO - mprev) + PV.
-template <int D>
-__device__ __forceinline__ bool accumulate_pv(float (&O)[D], float& mO, float mprev, uint32_t Gp, uint32_t tO,
-                                              uint64_t* pv_done, volatile int* abort_flag) {
-  if (!sm103::mbar_wait<set_status_fwd>(pv_done, Gp & 1, abort_flag)) return false;
-  sm103::tc_fence_after();
-  const float sc = sm103::ex2(mO - mprev);
-  uint32_t r[32];
-#pragma unroll
-  for (int c = 0; c < D / 32; ++c) {
-    sm103::tmem_ld32(tO + c * 32, r);
-    sm103::tmem_wait_ld(r);
-#pragma unroll
-    for (int i = 0; i < 32; ++i) O[c * 32 + i] = fmaf(O[c * 32 + i], sc, __uint_as_float(r[i]));
-  }
-  mO = mprev;
-  return true;
-}
+// Math warps: two per TMEM lane quadrant; the two warps of a quadrant share
+// its 32 query rows, warp half `ch` owning keys [64 ch, 64 ch + 64) of every
+// block (one 64-key chunk of P) and output columns [ch D/2, (ch+1) D/2).
+constexpr int kMathWarps = 8;
+constexpr int kThreads = 64 + 32 * kMathWarps;
 
-
-// Online-softmax state of one query row.
-template <int D>
+// Online-softmax state of one query row, as held by one of its two threads.
+// P = exp2(s S log2e - m) is formed against a reference max m that only moves
+// when a row max exceeds it by more than kRescaleLog2 (then O in TMEM and l
+// are rescaled once); O itself accumulates in TMEM across the key blocks.
+constexpr float kRescaleLog2 = 8.f;
 struct RowState {
-  float O[D];  // sum of P V relative to max mO
-  float m;     // running row max (log2 domain, scaled)
-  float l;     // running row sum relative to m
-  float mO;    // max the register accumulator O is expressed against
-  __device__ __forceinline__ void init() {
-#pragma unroll
-    for (int e = 0; e < D; ++e) O[e] = 0.f;
-    m = -INFINITY;
-    l = 0.f;
-    mO = -INFINITY;
-  }
+  float m;  // reference max (log2 domain, scaled), same in both threads of the row
+  float l;  // this thread's half of the row sum, relative to m
 };
 
 template <int N>
@@ -119,109 +108,146 @@ __device__ __forceinline__ float tree_sum(float (&v)[N]) {
   return v[0];
 }
 
-// Exponentiate 32 scores of TMEM chunk c into BF16 P in shared memory
-// (128-byte swizzled, K-major: row = query, 64 keys per 128-byte line).
+// named barrier of the two warps that share a TMEM lane quadrant
+__device__ __forceinline__ void pair_sync(int quad) {
+  asm volatile("bar.sync %0, 64;" ::"r"(quad + 1) : "memory");
+}
+
+// Exchange a per-row partial value with the partner thread (same row, other
+// column half).  Slots 0/1 alternate between key blocks and slot 2 serves the
+// epilogue, so a fast thread never overwrites a value its partner has not
+// read yet (every reuse of a slot is separated by another pair barrier).
+__device__ __forceinline__ float pair_exchange(float* red, int parity, int ch, int row, int quad, float v) {
+  red[(parity * 2 + ch) * 128 + row] = v;
+  pair_sync(quad);
+  return red[(parity * 2 + (ch ^ 1)) * 128 + row];
+}
+
+// running max of 32 scores into 4 partial maxima (3-input max)
 template <bool MASK>
-__device__ __forceinline__ void exp_store_chunk(const uint32_t (&r)[32], int c, uint32_t mbits, float sl2, float mnew,
-                                                float (&acc)[8], uint32_t sP, int row) {
-  uint32_t pk[16];
+__device__ __forceinline__ void chunk_max(const uint32_t (&r)[32], uint32_t mbits, float (&mx)[4]) {
 #pragma unroll
   for (int i = 0; i < 32; i += 2) {
-    float p0 = sm103::ex2(fmaf(__uint_as_float(r[i]), sl2, -mnew));
-    float p1 = sm103::ex2(fmaf(__uint_as_float(r[i + 1]), sl2, -mnew));
+    float x0 = __uint_as_float(r[i]), x1 = __uint_as_float(r[i + 1]);
+    if (MASK) {
+      x0 = (mbits >> i) & 1u ? x0 : -INFINITY;
+      x1 = (mbits >> (i + 1)) & 1u ? x1 : -INFINITY;
+    }
+    mx[(i >> 1) & 3] = sm103::fmax3(mx[(i >> 1) & 3], x0, x1);
+  }
+}
+
+// exp2 of 32 scores -> 16 BF16 pairs (for TMEM), with the exp2 argument and the
+// row sum formed by packed FP32 pair instructions
+template <bool MASK>
+__device__ __forceinline__ void exp_chunk(const uint32_t (&r)[32], uint32_t mbits, uint64_t s2, uint64_t nm2,
+                                          uint64_t (&acc)[4], uint32_t* pk) {
+  using namespace sm103;
+#pragma unroll
+  for (int i = 0; i < 32; i += 2) {
+    float a0, a1;
+    f2unpack(ffma2(u2pack(r[i], r[i + 1]), s2, nm2), a0, a1);
+    float p0 = ex2(a0), p1 = ex2(a1);
     if (MASK) {
       p0 = (mbits >> i) & 1u ? p0 : 0.f;
       p1 = (mbits >> (i + 1)) & 1u ? p1 : 0.f;
     }
-    acc[(i >> 1) & 7] += p0 + p1;
-    pk[i >> 1] = sm103::pack_bf16(p0, p1);
-  }
-  const uint32_t base = sP + (c >> 1) * 16384 + row * 128;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const uint32_t unit = ((c & 1) * 4 + u) ^ (row & 7);
-    sm103::st_shared_v4(base + unit * 16, pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+    acc[(i >> 1) & 3] = fadd2(acc[(i >> 1) & 3], f2pack(p0, p1));
+    pk[i >> 1] = pack_bf16(p0, p1);
   }
 }
 
-template <bool MASK>
-__device__ __forceinline__ void chunk_max(const uint32_t (&r)[32], uint32_t mbits, float (&mx)[8]) {
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    float x = __uint_as_float(r[i]);
-    if (MASK) x = (mbits >> i) & 1u ? x : -INFINITY;
-    mx[i & 7] = fmaxf(mx[i & 7], x);
-  }
-}
-
-// One 128-key block of the online softmax for this thread's query row:
-// row max, fold of the previous block's P V (if any), P = exp2(...) to shared
-// memory, row-sum update.  For d = 64 the whole 128-column score row is kept
-// in registers; for d = 128 (larger accumulator) the scores are read from
-// TMEM twice, 64 columns at a time.
-template <int D, bool MASK>
-__device__ __forceinline__ bool softmax_block(RowState<D>& rs, uint32_t tS, uint32_t tO, uint32_t sP, int row,
-                                              const uint32_t (&kmask)[4], float sl2, bool has_prev, uint32_t G,
-                                              uint64_t* pv_done, volatile int* abort_flag) {
+// One 128-key block of the online softmax for this thread's half of a query
+// row: partial row max (exchanged with the partner), fold of the previous
+// block's P V into O, exp2 of its 64 scores into P (shared memory), row-sum.
+// Rescale this thread's half (D/2 columns) of the O accumulator in TMEM by
+// `f` (1 for rows that keep their reference max).  Warp-synchronous.
+template <int D>
+__device__ __forceinline__ void rescale_o(uint32_t tO, float f) {
   using namespace sm103;
-  float mx[8], acc[8];
+  const uint64_t f2 = f2pack(f, f);
+  uint32_t r[32];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int c = 0; c < D / 64; ++c) {
+    tmem_ld32(tO + c * 32, r);
+    tmem_wait_ld(r);
+#pragma unroll
+    for (int i = 0; i < 32; i += 2) {
+      float x, y;
+      f2unpack(fmul2(u2pack(r[i], r[i + 1]), f2), x, y);
+      r[i] = __float_as_uint(x);
+      r[i + 1] = __float_as_uint(y);
+    }
+    tmem_st32(tO + c * 32, r);
+  }
+  tmem_wait_st();
+}
+
+// One 128-key block of the online softmax for this thread's half of a query
+// row: partial row max (exchanged with the partner thread), lazy rescale of
+// the reference max (and of O in TMEM, after the previous P V completed),
+// exp2 of the 64 scores into BF16 P in TMEM, row-sum update.
+template <int D, bool MASK>
+__device__ __forceinline__ bool softmax_block(RowState& rs, uint32_t tS, uint32_t tO, uint32_t tP, int row, int ch,
+                                              int quad, float* red, int parity, const uint32_t (&kmask)[2], float sl2,
+                                              bool first,
+                                              uint64_t* pv_last, uint32_t pv_last_par, uint64_t* p_free,
+                                              uint32_t p_free_par, volatile int* abort_flag) {
+  using namespace sm103;
+  float mx[4];
+  uint64_t acc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
     mx[i] = -INFINITY;
-    acc[i] = 0.f;
+    acc[i] = f2pack(0.f, 0.f);
   }
   uint32_t r0[32], r1[32];
-  if constexpr (D == 64) {
-    uint32_t r2[32], r3[32];
-    tmem_ld32(tS, r0);
-    tmem_ld32(tS + 32, r1);
-    tmem_ld32(tS + 64, r2);
-    tmem_ld32(tS + 96, r3);
-    tmem_wait_ld(r0);
-    tmem_wait_ld(r1);
-    tmem_wait_ld(r2);
-    tmem_wait_ld(r3);
-    chunk_max<MASK>(r0, kmask[0], mx);
-    chunk_max<MASK>(r1, kmask[1], mx);
-    chunk_max<MASK>(r2, kmask[2], mx);
-    chunk_max<MASK>(r3, kmask[3], mx);
-    const float mnew = fmaxf(rs.m, tree_max(mx) * sl2);
-    if (has_prev && !accumulate_pv<D>(rs.O, rs.mO, rs.m, G - 1, tO, pv_done, abort_flag)) return false;
-    exp_store_chunk<MASK>(r0, 0, kmask[0], sl2, mnew, acc, sP, row);
-    exp_store_chunk<MASK>(r1, 1, kmask[1], sl2, mnew, acc, sP, row);
-    exp_store_chunk<MASK>(r2, 2, kmask[2], sl2, mnew, acc, sP, row);
-    exp_store_chunk<MASK>(r3, 3, kmask[3], sl2, mnew, acc, sP, row);
-    rs.l = rs.l * ex2(rs.m - mnew) + tree_sum(acc);
-    rs.m = mnew;
+  tmem_ld32(tS, r0);
+  tmem_ld32(tS + 32, r1);
+  tmem_wait_ld(r0);
+  tmem_wait_ld(r1);
+  chunk_max<MASK>(r0, kmask[0], mx);
+  chunk_max<MASK>(r1, kmask[1], mx);
+  const float mine = fmaxf(fmaxf(mx[0], mx[1]), fmaxf(mx[2], mx[3]));
+  const float other = pair_exchange(red, parity, ch, row, quad, mine);
+  const float mblk = fmaxf(mine, other) * sl2;
+  if (first) {
+    rs.m = mblk;  // O is written fresh by this block's P V
   } else {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      tmem_ld32(tS + 64 * h, r0);
-      tmem_ld32(tS + 64 * h + 32, r1);
-      tmem_wait_ld(r0);
-      tmem_wait_ld(r1);
-      chunk_max<MASK>(r0, kmask[2 * h], mx);
-      chunk_max<MASK>(r1, kmask[2 * h + 1], mx);
+    const bool grow = mblk > rs.m + kRescaleLog2;
+    if (__any_sync(0xffffffffu, grow)) {
+      // O must not be in flight: wait for the previous block's P V
+      if (!mbar_wait<set_status_fwd>(pv_last, pv_last_par, abort_flag)) return false;
+      tc_fence_after();
+      const float f = grow ? ex2(rs.m - mblk) : 1.f;
+      rescale_o<D>(tO, f);
+      rs.l *= f;
+      if (grow) rs.m = mblk;
     }
-    const float mnew = fmaxf(rs.m, tree_max(mx) * sl2);
-    if (has_prev && !accumulate_pv<D>(rs.O, rs.mO, rs.m, G - 1, tO, pv_done, abort_flag)) return false;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      tmem_ld32(tS + 64 * h, r0);
-      tmem_ld32(tS + 64 * h + 32, r1);
-      tmem_wait_ld(r0);
-      tmem_wait_ld(r1);
-      exp_store_chunk<MASK>(r0, 2 * h, kmask[2 * h], sl2, mnew, acc, sP, row);
-      exp_store_chunk<MASK>(r1, 2 * h + 1, kmask[2 * h + 1], sl2, mnew, acc, sP, row);
-    }
-    rs.l = rs.l * ex2(rs.m - mnew) + tree_sum(acc);
-    rs.m = mnew;
   }
+  const uint64_t s2 = f2pack(sl2, sl2), nm2 = f2pack(-rs.m, -rs.m);
+  uint32_t pk0[16], pk1[16];
+  exp_chunk<MASK>(r0, kmask[0], s2, nm2, acc, pk0);
+  exp_chunk<MASK>(r1, kmask[1], s2, nm2, acc, pk1);
+  // this P buffer is free once the P V product that last read it completed
+  if (!mbar_wait<set_status_fwd>(p_free, p_free_par, abort_flag)) return false;
+  tc_fence_after();
+  tmem_st16(tP, pk0);  // keys [64 ch, 64 ch + 64) -> P columns [32 ch, 32 ch + 32)
+  tmem_st16(tP + 16, pk1);
+  float lsum = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float x, y;
+    f2unpack(acc[i], x, y);
+    lsum += x + y;
+  }
+  rs.l += lsum;
+  tmem_wait_st();
   return true;
 }
 
 template <int D, typename OutT>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     sm103_fwd_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
                      const __grid_constant__ CUtensorMap tv, const FwdArgs a) {
   using C = FwdCfg<D>;
@@ -230,22 +256,25 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kBar);
   uint64_t* q_full = bars + 0;
   uint64_t* q_empty = bars + 1;
-  uint64_t* k_full = bars + 2;
+  uint64_t* qt_full = bars + 2;
+  uint64_t* k_full = bars + 3;
   uint64_t* k_empty = k_full + C::kStages;
   uint64_t* v_full = k_empty + C::kStages;
   uint64_t* v_empty = v_full + C::kStages;
   uint64_t* s_full = v_empty + C::kStages;
   uint64_t* s_empty = s_full + 2;
   uint64_t* p_full = s_empty + 2;
-  uint64_t* pv_done = p_full + 1;
-  uint64_t* drain = pv_done + 1;
+  uint64_t* pv_done = p_full + 1;  // [2], one per P buffer
+  uint64_t* o_empty = pv_done + 2;
+  uint64_t* drain = o_empty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(q_full, 1);
-    mbar_init(q_empty, 1);
+    mbar_init(q_empty, kMathWarps);
+    mbar_init(qt_full, kMathWarps);
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(k_full + s, 1);
       mbar_init(k_empty + s, 1);
@@ -254,10 +283,12 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(s_full + s, 1);
-      mbar_init(s_empty + s, 4);
+      mbar_init(s_empty + s, kMathWarps);
     }
-    mbar_init(p_full, 4);
+    mbar_init(p_full, kMathWarps);
     mbar_init(pv_done, 1);
+    mbar_init(pv_done + 1, 1);
+    mbar_init(o_empty, kMathWarps);
     mbar_init(drain, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -331,22 +362,21 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       constexpr uint32_t idS = idesc_bf16(128, 128, 0);
       constexpr uint32_t idO = idesc_bf16(128, D, 1);
-      const uint32_t sQ = smem_u32(smem + C::kQ), sK = smem_u32(smem + C::kK), sV = smem_u32(smem + C::kV),
-                     sP = smem_u32(smem + C::kP);
+      const uint32_t sK = smem_u32(smem + C::kK), sV = smem_u32(smem + C::kV);
       uint32_t G = 0, W = 0;
       bool ok = true;
-      auto issue_pv = [&](uint32_t Gp) -> bool {
-        const uint32_t st = Gp % C::kStages;
+      // P V of global block Gp (first block of its item: fresh accumulator)
+      auto issue_pv = [&](uint32_t Gp, bool first) -> bool {
+        const uint32_t st = Gp % C::kStages, pb = Gp % C::kPBufs;
         if (!mbar_wait<set_status_fwd>(v_full + st, (Gp / C::kStages) & 1, abort_flag)) return false;
         if (!mbar_wait<set_status_fwd>(p_full, Gp & 1, abort_flag)) return false;
+        if (first && !mbar_wait<set_status_fwd>(o_empty, (W & 1) ^ 1, abort_flag)) return false;
         tc_fence_after();
 #pragma unroll
-        for (int ks = 0; ks < 8; ++ks) {
-          const uint64_t ad = sw128_desc(sP + (ks >> 2) * 16384 + (ks & 3) * 32, 16, 1024);
-          const uint64_t bd = sw128_desc(sV + st * C::kBlock + ks * 2048, 16384, 1024);
-          umma_bf16(tmem + C::kColO, ad, bd, idO, ks > 0);
-        }
-        umma_commit(pv_done);
+        for (int ks = 0; ks < 8; ++ks)
+          umma_bf16_ts(tmem + C::kColO, tmem + C::kColP + pb * 64 + ks * 8,
+                       sw128_desc(sV + st * C::kBlock + ks * 2048, 16384, 1024), idO, (!first || ks > 0) ? 1u : 0u);
+        umma_commit(pv_done + pb);
         umma_commit(v_empty + st);
         return true;
       };
@@ -356,8 +386,9 @@ __global__ void __launch_bounds__(192, 1)
         TileBlocks tbk;
         tile_blocks(g, tile, tbk);
         if (qb >= tbk.NB) continue;
-        if (!(ok = mbar_wait<set_status_fwd>(q_full, W & 1, abort_flag))) break;
+        if (!(ok = mbar_wait<set_status_fwd>(qt_full, W & 1, abort_flag))) break;  // Q in TMEM
         tc_fence_after();
+        const uint32_t G0 = G;
         for (int j = 0; j < tbk.NB; ++j, ++G) {
           const uint32_t st = G % C::kStages, sb = G & 1;
           if (!(ok = mbar_wait<set_status_fwd>(k_full + st, (G / C::kStages) & 1, abort_flag))) break;
@@ -366,16 +397,15 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
           for (int ks = 0; ks < D / 16; ++ks) {
             const uint32_t off = (ks >> 2) * 16384 + (ks & 3) * 32;
-            umma_bf16(tmem + sb * 128, sw128_desc(sQ + off, 16, 1024), sw128_desc(sK + st * C::kBlock + off, 16, 1024),
-                      idS, ks > 0);
+            umma_bf16_ts(tmem + sb * 128, tmem + C::kColQ + ks * 8, sw128_desc(sK + st * C::kBlock + off, 16, 1024),
+                         idS, ks > 0);
           }
           umma_commit(s_full + sb);
           umma_commit(k_empty + st);
-          if (j == tbk.NB - 1) umma_commit(q_empty);
-          if (j > 0 && !(ok = issue_pv(G - 1))) break;
+          if (j > 0 && !(ok = issue_pv(G - 1, G - 1 == G0))) break;
         }
         if (!ok) break;
-        if (!(ok = issue_pv(G - 1))) break;
+        if (!(ok = issue_pv(G - 1, G - 1 == G0))) break;
         ++W;
       }
       // all issued MMAs complete before TMEM is released
@@ -385,10 +415,12 @@ __global__ void __launch_bounds__(192, 1)
   } else {
     // ------------------------------------------------------------ softmax + epilogue
     const int quad = warp & 3;
+    const int ch = (warp - 2) >> 2;    // key half of every block / output-column half
     const int row = quad * 32 + lane;  // TMEM lane = block row
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
-    const uint32_t sP = smem_u32(smem + C::kP);
-    uint32_t G = 0;
+    const uint32_t tO = tl + C::kColO + ch * (D / 2);
+    float* red = reinterpret_cast<float*>(smem + C::kRed);
+    uint32_t G = 0, W = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
       int bh, tile, qb;
@@ -401,59 +433,112 @@ __global__ void __launch_bounds__(192, 1)
       block_row(g, qo, row, ql);
       const bool qvalid = inside(tbk, ql);
 
-      RowState<D> rs;
-      rs.init();
+      // the query block: shared memory (TMA) -> registers -> TMEM (A operand of S = Q K^T)
+      if (!(ok = mbar_wait<set_status_fwd>(q_full, W & 1, abort_flag))) break;
+      {
+        const uint32_t sQ = smem_u32(smem + C::kQ);
+        if constexpr (D == 64) {
+          uint32_t qr[16];
+          ld_swizzled_row<4>(sQ, row, 4 * ch, qr);  // elements [32 ch, 32 ch + 32)
+          tmem_st16(tl + C::kColQ + 16 * ch, qr);
+        } else {
+          uint32_t qr[32];
+          ld_swizzled_row<8>(sQ + ch * 16384, row, 0, qr);  // elements [64 ch, 64 ch + 64)
+          tmem_st32(tl + C::kColQ + 32 * ch, qr);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(q_empty);
+          mbar_arrive(qt_full);
+        }
+      }
+
+      RowState rs;
+      rs.m = -INFINITY;
+      rs.l = 0.f;
+      // key-block coordinates stepped incrementally (no divisions in the loop)
+      int jt = 0, jy = 0, jx = 0;
       for (int j = 0; j < tbk.NB; ++j, ++G) {
-        const uint32_t sb = G & 1;
-        int ko[3];
-        block_origin(g, tbk, j, ko);
-        // key validity of the block's 128 columns, one ballot per 32 columns
-        uint32_t kmask[4];
+        const uint32_t sb = G & 1, pb = G % C::kPBufs;
+        const int ko[3] = {jt << g.lt, jy << g.ly, jx << g.lx};
+        if (++jx == tbk.nb[2]) {
+          jx = 0;
+          if (++jy == tbk.nb[1]) {
+            jy = 0;
+            ++jt;
+          }
+        }
+        // validity of this thread's 64 key columns, one ballot per 32
+        uint32_t kmask[2] = {~0u, ~0u};
         const bool full = block_full(g, tbk, ko);
         if (!full) {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
+          for (int c = 0; c < 2; ++c) {
             int kl[3];
-            block_row(g, ko, c * 32 + lane, kl);
+            block_row(g, ko, ch * 64 + c * 32 + lane, kl);
             kmask[c] = __ballot_sync(0xffffffffu, inside(tbk, kl));
           }
         }
         if (!(ok = mbar_wait<set_status_fwd>(s_full + sb, (G >> 1) & 1, abort_flag))) break;
         tc_fence_after();
+        const uint32_t tS = tl + sb * 128 + ch * 64;
+        const uint32_t tP = tl + C::kColP + pb * 64 + ch * 32;
+        // previous block's P V (for a rescale of O) and the P V that last read this P buffer
+        uint64_t* pv_last = pv_done + (G - 1) % C::kPBufs;
+        const uint32_t pv_last_par = ((G - 1) / C::kPBufs) & 1;
+        const uint32_t p_free_par = ((G / C::kPBufs) & 1) ^ 1;
         if (full)
-          ok = softmax_block<D, false>(rs, tl + sb * 128, tl + C::kColO, sP, row, kmask, g.scale_log2, j > 0, G, pv_done, abort_flag);
+          ok = softmax_block<D, false>(rs, tS, tO, tP, row, ch, quad, red, sb, kmask, g.scale_log2, j == 0, pv_last,
+                                       pv_last_par, pv_done + pb, p_free_par, abort_flag);
         else
-          ok = softmax_block<D, true>(rs, tl + sb * 128, tl + C::kColO, sP, row, kmask, g.scale_log2, j > 0, G, pv_done, abort_flag);
+          ok = softmax_block<D, true>(rs, tS, tO, tP, row, ch, quad, red, sb, kmask, g.scale_log2, j == 0, pv_last,
+                                      pv_last_par, pv_done + pb, p_free_par, abort_flag);
         if (!ok) break;
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(s_empty + sb);
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(p_full);
-      }
-      if (!ok) break;
-      if (!(ok = accumulate_pv<D>(rs.O, rs.mO, rs.m, G - 1, tl + C::kColO, pv_done, abort_flag))) break;
-      tc_fence_before();
-      // ---- epilogue
-      if (qvalid) {
-        const int64_t slot = tile_slot0(g, bh, tile) + qb * 128 + row;
-        a.lse2[slot] = rs.m + __log2f(rs.l);
-        const int p[3] = {tbk.tb.lo[0] + ql[0], tbk.tb.lo[1] + ql[1], tbk.tb.lo[2] + ql[2]};
-        const int64_t tok = ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2];
-        const float inv = 1.f / rs.l;
-        if (single_cover(g, p)) {
-          OutT* dst = static_cast<OutT*>(a.out) + ((int64_t)bh * g.N + tok) * D;
-#pragma unroll
-          for (int e = 0; e < D; e += 4)
-            store4<OutT>(dst + e, make_float4(rs.O[e] * inv, rs.O[e + 1] * inv, rs.O[e + 2] * inv, rs.O[e + 3] * inv));
-        } else {
-          float* dst = a.ot + slot * D;
-#pragma unroll
-          for (int e = 0; e < D; e += 4)
-            store4<float>(dst + e, make_float4(rs.O[e] * inv, rs.O[e + 1] * inv, rs.O[e + 2] * inv, rs.O[e + 3] * inv));
+        if (lane == 0) {
+          mbar_arrive(s_empty + sb);
+          mbar_arrive(p_full);
         }
       }
+      if (!ok) break;
+      // ---- epilogue: wait for the last P V, full row sum from the two halves, O / l
+      if (!(ok = mbar_wait<set_status_fwd>(pv_done + (G - 1) % C::kPBufs, ((G - 1) / C::kPBufs) & 1, abort_flag)))
+        break;
+      tc_fence_after();
+      const float l = rs.l + pair_exchange(red, 2, ch, row, quad, rs.l);  // slot 2: epilogue only
+      const float inv = 1.f / l;
+      const int64_t slot = tile_slot0(g, bh, tile) + qb * 128 + row;
+      if (qvalid && ch == 0) a.lse2[slot] = rs.m + __log2f(l);
+      const int p[3] = {tbk.tb.lo[0] + ql[0], tbk.tb.lo[1] + ql[1], tbk.tb.lo[2] + ql[2]};
+      const int64_t tok = qvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
+      const bool single = qvalid && single_cover(g, p);
+      const int c0 = ch * (D / 2);
+      OutT* dst_out = static_cast<OutT*>(a.out) + ((int64_t)bh * g.N + tok) * D + c0;
+      float* dst_scr = a.ot + slot * D + c0;
+      uint32_t r[32];
+#pragma unroll
+      for (int c = 0; c < D / 64; ++c) {
+        tmem_ld32(tO + c * 32, r);
+        tmem_wait_ld(r);
+        if (qvalid) {
+#pragma unroll
+          for (int e = 0; e < 32; e += 4) {
+            const float4 v4 = make_float4(__uint_as_float(r[e]) * inv, __uint_as_float(r[e + 1]) * inv,
+                                          __uint_as_float(r[e + 2]) * inv, __uint_as_float(r[e + 3]) * inv);
+            if (single)
+              store4<OutT>(dst_out + c * 32 + e, v4);
+            else
+              store4<float>(dst_scr + c * 32 + e, v4);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(o_empty);
+      ++W;
     }
   }
   tc_fence_before();
@@ -486,7 +571,7 @@ cudaError_t run_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
   if (e != cudaSuccess) return e;
   const int grid = (int)(a.items < num_sms() ? a.items : num_sms());
-  kern<<<grid, 192, C::kSmem, st>>>(mq, mk, mv, a);
+  kern<<<grid, kThreads, C::kSmem, st>>>(mq, mk, mv, a);
   return cudaGetLastError();
 }
 
