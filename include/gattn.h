@@ -156,6 +156,82 @@ gattn_status gattn_bwd(const gattn_desc *desc, const void *q, const void *k, con
                        gattn_stream_t stream);
 
 /*
+ * Serving: continuous batching of diffusion posterior-sampling requests.
+ *
+ * Every request carries a token state z ([nh, N, d] BF16 on a (T, Y, X) grid,
+ * N = T*Y*X) and runs `steps` denoising steps
+ *     z <- z + c * (GPA(z, z, z) - z)
+ * (a one-layer synthetic denoiser whose output is the GPA attention of its
+ * state; the per-step Hann-weighted merge is the propagation step of
+ * Sec. III-C, which the paper runs once per diffusion step without extra
+ * iterations).  The server keeps each active request's state on the device
+ * across its steps.  An engine iteration (gattn_serve_step) admits waiting
+ * requests in arrival order while the slot limit and the HBM budget allow,
+ * then runs one step of every active request in one persistent ragged
+ * attention launch (per-request descriptors and item offsets) followed by one
+ * merge-and-update launch, both captured in a CUDA graph that is replayed
+ * every iteration; requests that finish are retired, their result copied to
+ * host memory and their device memory released.  Results do not depend on
+ * which other requests share an iteration (deterministic kernels).
+ * The server owns its device memory (within hbm_budget) and one internal
+ * device buffer per slot of descriptors; calls on one server must not overlap.
+ */
+typedef struct gattn_server gattn_server;
+
+typedef struct {
+  int32_t d;                /* head dim: 64 or 128 */
+  int32_t Y, X;             /* spatial grid shared by every request; T varies */
+  int32_t core[3];          /* tile core (t, y, x) */
+  int32_t halo[3];          /* tile halo (t, y, x) */
+  int32_t window;           /* gattn_window */
+  int32_t steps;            /* denoising steps per request, >= 1 */
+  float c;                  /* step size of the state update */
+  int32_t max_active;       /* slot limit, 1..4096 */
+  int32_t use_graph;        /* 1: capture the iteration's two launches in a CUDA graph */
+  size_t hbm_budget;        /* bytes of device memory the server may hold for request state */
+} gattn_serve_cfg;
+
+typedef struct {
+  int32_t T;                /* frames: N = T * Y * X */
+  int32_t nh;               /* heads */
+  const void *z0;           /* initial state [nh, N, d] BF16 */
+  int32_t z0_on_device;     /* 1: device pointer, read at admission (keep it valid until then);
+                               0: host pointer, copied at submit */
+} gattn_request;
+
+typedef struct {
+  int64_t submitted, admitted, completed, rejected, active, waiting;
+  int64_t iterations;       /* engine iterations that ran GPU work */
+  double p50_latency_s, p99_latency_s, mean_latency_s, max_latency_s;  /* submit -> result on host */
+  double token_steps;       /* sum over completed requests of nh * N * steps */
+  double gpu_busy_s;        /* device time of the engine iterations */
+  double wall_s;            /* host time from the first submit to the last completion */
+  size_t hbm_in_use, hbm_peak;
+} gattn_serve_stats_t;
+
+/* Device memory one request holds while active (state, attention output,
+ * merge scratch); 0 on an invalid request. */
+size_t gattn_serve_request_bytes(const gattn_serve_cfg *cfg, int32_t T, int32_t nh);
+
+/* `stream`: the stream engine iterations run on; NULL makes the server create
+ * (and destroy) its own blocking stream (a graph cannot be captured on the
+ * legacy default stream). */
+gattn_status gattn_serve_create(const gattn_serve_cfg *cfg, gattn_stream_t stream, gattn_server **out);
+/* Queues a request.  GATTN_ERR_OOM if it can never fit the budget,
+ * GATTN_ERR_INVALID_ARG on a bad shape. */
+gattn_status gattn_serve_submit(gattn_server *s, const gattn_request *req, uint64_t *id);
+/* One engine iteration (admission, one step of every active request,
+ * retirement); synchronises the server's stream.  *n_active receives the
+ * number of active requests after the iteration, *n_waiting the queue length. */
+gattn_status gattn_serve_step(gattn_server *s, int32_t *n_active, int32_t *n_waiting);
+/* *done = 1 once the request finished; then copies its final state into
+ * result_host ([nh, N, d] BF16, may be NULL) and reports its latency.
+ * GATTN_ERR_NOT_FOUND for an unknown id. */
+gattn_status gattn_serve_poll(gattn_server *s, uint64_t id, int32_t *done, double *latency_s, void *result_host);
+gattn_status gattn_serve_stats(gattn_server *s, gattn_serve_stats_t *out);
+void gattn_serve_destroy(gattn_server *s);
+
+/*
  * Forward without a caller-provided saved buffer, for callers that cannot
  * allocate device memory: code that runs under a memory manager which owns
  * all of HBM after start-up (a serving process that partitions the device up

@@ -325,7 +325,8 @@ int32_t gattn_profile_read(gattn_kernel_stat* out, int32_t max) {
 
 gattn_status gattn_stream_status(gattn_stream_t stream) {
   if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return GATTN_ERR_CUDA;
-  uint32_t words[] = {fetch_status_simt(), fetch_status_merge(), fetch_status_sm103_fwd(), fetch_status_sm103_bwd()};
+  uint32_t words[] = {fetch_status_simt(), fetch_status_merge(), fetch_status_sm103_fwd(), fetch_status_sm103_bwd(),
+                      fetch_status_serve()};
   for (uint32_t w : words)
     if (w == ~0u) return GATTN_ERR_CUDA;
   for (uint32_t w : words)

@@ -2,6 +2,7 @@
 // shared by the translation units of libgattn.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -72,6 +73,7 @@ uint32_t fetch_status_simt();
 uint32_t fetch_status_merge();
 uint32_t fetch_status_sm103_fwd();
 uint32_t fetch_status_sm103_bwd();
+uint32_t fetch_status_serve();
 
 // ---- per-kernel device timing (gattn_profile_*); no-ops unless enabled
 enum KernelId : int { kKFwdTiles = 0, kKMergeFwd, kKBwdPrep, kKBwdDkdv, kKBwdDq, kKMergeBwd, kKCount };
@@ -98,6 +100,26 @@ cudaError_t launch_sm103_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_b
                              const __nv_bfloat16* v, const __nv_bfloat16* dout, const float* lse2c,
                              const float* dd, void* dq, void* dk, void* dv, int out_dtype, float* dq_s,
                              float* dk_s, float* dv_s, uint32_t flags, cudaStream_t st);
+
+// ---- ragged (multi-request) forward, used by the serving engine.
+// One descriptor per active request, in device memory, sorted by item0: the
+// request's token state z ([nh, N, d] BF16, Q = K = V = z), its geometry
+// (B = 1) and TMA tensor map, its attention output and per-slot scratch.
+struct alignas(128) ReqDesc {
+  CUtensorMap tmap;      // over z, box of the geometry's block shape
+  Geom g;
+  __nv_bfloat16* z;      // state (read by the attention, updated by the step kernel)
+  void* out;             // GPA(z) for rows covered by one tile (BF16)
+  float* ot;             // per-slot FP32 outputs of multiply-covered rows
+  int64_t tok0;          // first global (head, token) row of this request (step kernel)
+  int item0;             // first global attention work item of this request
+  int items;             // nh * ntiles * nbmax_tot
+};
+// counts[0] = number of requests, counts[1] = total attention work items,
+// counts[2] = total (head, token) rows; read on the device so that one
+// captured launch serves any active set.
+cudaError_t launch_sm103_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, int d, cudaStream_t st);
+cudaError_t launch_serve_update(const ReqDesc* reqs, const int64_t* counts, int d, float c, cudaStream_t st);
 
 // ---- small device helpers
 #ifdef __CUDACC__

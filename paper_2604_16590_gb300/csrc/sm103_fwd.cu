@@ -26,6 +26,8 @@
 //               (two math warps per SM sub-partition hide TMEM/MUFU latency)
 // TMEM: columns [0,256) two S buffers, [256, 256+d) the P V block product,
 // then 64 columns of P (BF16 pairs) and d/2 columns of Q (BF16 pairs).
+#include <string.h>
+
 #include "internal.cuh"
 #include "sm103_common.cuh"
 
@@ -64,13 +66,78 @@ struct FwdArgs {
   float* lse2;
   float* ot;
   int items;  // B*nh * ntiles * nbmax_tot
+  // ragged mode (serving): per-request descriptors and device-side counts
+  const ReqDesc* reqs;
+  const int64_t* counts;
 };
 
-__device__ __forceinline__ void decode_item(const FwdArgs& a, int w, int& bh, int& tile, int& qb) {
-  qb = w % a.g.nbmax_tot;
-  const int r = w / a.g.nbmax_tot;
-  tile = r % a.g.ntiles;
-  bh = r / a.g.ntiles;
+// One work item (batch*head, tile, 128-row block) resolved to its problem.
+struct Item {
+  const Geom* g;
+  const CUtensorMap* tq;
+  const CUtensorMap* tk;
+  const CUtensorMap* tv;
+  void* out;
+  float* lse2;  // may be null (no backward)
+  float* ot;
+  int bh, tile, blk;
+  int req;  // request index (ragged mode), else -1
+};
+
+// Returns false (after recording GATTN_ERR_DEVICE_BOUNDS) if a ragged work
+// item does not decode to a valid (request, head, tile, block); every role
+// decodes the same item identically, so all of them skip it together.
+template <bool RAGGED>
+__device__ __forceinline__ bool resolve(const FwdArgs& a, const CUtensorMap* tq, const CUtensorMap* tk,
+                                        const CUtensorMap* tv, int w, Item& it) {
+  int req = -1;
+  if constexpr (RAGGED) {
+    // requests are sorted by item0: binary search for the last item0 <= w
+    const int nreq = (int)a.counts[0];
+    int lo = 0, hi = nreq - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.reqs[mid].item0 <= w) lo = mid;
+      else hi = mid - 1;
+    }
+    if (nreq < 1 || w < a.reqs[lo].item0 || w >= a.reqs[lo].item0 + a.reqs[lo].items) {
+      set_status(kStatusBounds);
+      return false;
+    }
+    req = lo;
+    const ReqDesc& r = a.reqs[lo];
+    it.g = &r.g;
+    it.tq = it.tk = it.tv = &r.tmap;
+    it.out = r.out;
+    it.lse2 = nullptr;
+    it.ot = r.ot;
+    w -= r.item0;
+  } else {
+    it.g = &a.g;
+    it.tq = tq;
+    it.tk = tk;
+    it.tv = tv;
+    it.out = a.out;
+    it.lse2 = a.lse2;
+    it.ot = a.ot;
+  }
+  const Geom& g = *it.g;
+  it.blk = w % g.nbmax_tot;
+  const int r = w / g.nbmax_tot;
+  it.tile = r % g.ntiles;
+  it.bh = r / g.ntiles;
+  it.req = req;
+  if (RAGGED && it.bh >= g.B * g.nh) {
+    set_status(kStatusBounds);
+    return false;
+  }
+  return true;
+}
+
+template <bool RAGGED>
+__device__ __forceinline__ int total_items(const FwdArgs& a) {
+  if constexpr (RAGGED) return (int)a.counts[1];
+  else return a.items;
 }
 
 __device__ void set_status_fwd(uint32_t c) { set_status(c); }
@@ -246,7 +313,7 @@ __device__ __forceinline__ bool softmax_block(RowState& rs, uint32_t tS, uint32_
   return true;
 }
 
-template <int D, typename OutT>
+template <int D, typename OutT, bool RAGGED>
 __global__ void __launch_bounds__(kThreads, 1)
     sm103_fwd_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
                      const __grid_constant__ CUtensorMap tv, const FwdArgs a) {
@@ -292,9 +359,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(drain, 1);
     *abort_flag = 0;
     fence_mbar_init();
-    prefetch_tmap(&tq);
-    prefetch_tmap(&tk);
-    prefetch_tmap(&tv);
+    if (!RAGGED) {
+      prefetch_tmap(&tq);
+      prefetch_tmap(&tk);
+      prefetch_tmap(&tv);
+    }
   }
   if (warp == 1) {
     tmem_alloc(tmem_slot, C::kTmemCols);
@@ -304,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const Geom& g = a.g;
+  const int n_items = total_items<RAGGED>(a);
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -313,13 +382,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       // arming record for the abort drain: bit s of k_arm/v_arm = stage s armed at
       // least once, bit s of k_par/v_par = parity of its latest arming
       uint32_t k_arm = 0, v_arm = 0, k_par = 0, v_par = 0, q_arm = 0, q_par = 0;
+      int last_req = -1;
       bool ok = true;
-      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-        int bh, tile, qb;
-        decode_item(a, w, bh, tile, qb);
+      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+        Item it;
+        if (!resolve<RAGGED>(a, &tq, &tk, &tv, w, it)) continue;
+        const Geom& g = *it.g;
+        const int bh = it.bh, tile = it.tile, qb = it.blk;
         TileBlocks tbk;
         tile_blocks(g, tile, tbk);
         if (qb >= tbk.NB) continue;
+        if (RAGGED && it.req != last_req) {
+          tmap_acquire(it.tq);  // this launch's descriptor table may hold a new map here
+          last_req = it.req;
+        }
         int o[3];
         block_origin(g, tbk, qb, o);
         if (!(ok = mbar_wait<set_status_fwd>(q_empty, (W & 1) ^ 1, abort_flag))) break;
@@ -327,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         q_arm = 1;
         q_par = W & 1;
         for (int h = 0; h < C::kHalves; ++h)
-          tma_load_5d(smem + C::kQ + h * 16384, &tq, q_full, 64 * h, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
+          tma_load_5d(smem + C::kQ + h * 16384, it.tq, q_full, 64 * h, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
                       tbk.tb.lo[0] + o[0], bh);
         for (int j = 0; j < tbk.NB; ++j, ++G) {
           const uint32_t st = G % C::kStages, n = G / C::kStages;
@@ -338,13 +414,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           k_arm |= 1u << st;
           k_par = (k_par & ~(1u << st)) | ((n & 1) << st);
           for (int h = 0; h < C::kHalves; ++h)
-            tma_load_5d(smem + C::kK + st * C::kBlock + h * 16384, &tk, k_full + st, 64 * h, c1, c2, c3, bh);
+            tma_load_5d(smem + C::kK + st * C::kBlock + h * 16384, it.tk, k_full + st, 64 * h, c1, c2, c3, bh);
           if (!(ok = mbar_wait<set_status_fwd>(v_empty + st, (n & 1) ^ 1, abort_flag))) break;
           mbar_arrive_expect_tx(v_full + st, C::kBlock);
           v_arm |= 1u << st;
           v_par = (v_par & ~(1u << st)) | ((n & 1) << st);
           for (int h = 0; h < C::kHalves; ++h)
-            tma_load_5d(smem + C::kV + st * C::kBlock + h * 16384, &tv, v_full + st, 64 * h, c1, c2, c3, bh);
+            tma_load_5d(smem + C::kV + st * C::kBlock + h * 16384, it.tv, v_full + st, 64 * h, c1, c2, c3, bh);
         }
         ++W;
       }
@@ -380,12 +456,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         umma_commit(v_empty + st);
         return true;
       };
-      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-        int bh, tile, qb;
-        decode_item(a, w, bh, tile, qb);
+      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+        Item it;
+        if (!resolve<RAGGED>(a, &tq, &tk, &tv, w, it)) continue;
         TileBlocks tbk;
-        tile_blocks(g, tile, tbk);
-        if (qb >= tbk.NB) continue;
+        tile_blocks(*it.g, it.tile, tbk);
+        if (it.blk >= tbk.NB) continue;
         if (!(ok = mbar_wait<set_status_fwd>(qt_full, W & 1, abort_flag))) break;  // Q in TMEM
         tc_fence_after();
         const uint32_t G0 = G;
@@ -422,9 +498,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* red = reinterpret_cast<float*>(smem + C::kRed);
     uint32_t G = 0, W = 0;
     bool ok = true;
-    for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-      int bh, tile, qb;
-      decode_item(a, w, bh, tile, qb);
+    for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+      Item it;
+      if (!resolve<RAGGED>(a, &tq, &tk, &tv, w, it)) continue;
+      const Geom& g = *it.g;
+      const int bh = it.bh, tile = it.tile, qb = it.blk;
       TileBlocks tbk;
       tile_blocks(g, tile, tbk);
       if (qb >= tbk.NB) continue;
@@ -511,13 +589,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float l = rs.l + pair_exchange(red, 2, ch, row, quad, rs.l);  // slot 2: epilogue only
       const float inv = 1.f / l;
       const int64_t slot = tile_slot0(g, bh, tile) + qb * 128 + row;
-      if (qvalid && ch == 0) a.lse2[slot] = rs.m + __log2f(l);
+      if (qvalid && ch == 0 && it.lse2) it.lse2[slot] = rs.m + __log2f(l);
       const int p[3] = {tbk.tb.lo[0] + ql[0], tbk.tb.lo[1] + ql[1], tbk.tb.lo[2] + ql[2]};
       const int64_t tok = qvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
       const bool single = qvalid && single_cover(g, p);
       const int c0 = ch * (D / 2);
-      OutT* dst_out = static_cast<OutT*>(a.out) + ((int64_t)bh * g.N + tok) * D + c0;
-      float* dst_scr = a.ot + slot * D + c0;
+      OutT* dst_out = static_cast<OutT*>(it.out) + ((int64_t)bh * g.N + tok) * D + c0;
+      float* dst_scr = it.ot + slot * D + c0;
       uint32_t r[32];
 #pragma unroll
       for (int c = 0; c < D / 64; ++c) {
@@ -558,6 +636,8 @@ cudaError_t run_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
   a.out = out;
   a.lse2 = lse2;
   a.ot = ot;
+  a.reqs = nullptr;
+  a.counts = nullptr;
   const int64_t items = (int64_t)g.B * g.nh * g.ntiles * g.nbmax_tot;
   if (items >= (1LL << 31)) return cudaErrorNotSupported;
   a.items = (int)items;
@@ -567,7 +647,7 @@ cudaError_t run_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
       !make_tmap_5d(&mk, k, D, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
       !make_tmap_5d(&mv, v, D, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt))
     return cudaErrorInvalidValue;
-  auto kern = sm103_fwd_kernel<D, OutT>;
+  auto kern = sm103_fwd_kernel<D, OutT, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
   if (e != cudaSuccess) return e;
   const int grid = (int)(a.items < num_sms() ? a.items : num_sms());
@@ -575,7 +655,29 @@ cudaError_t run_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
   return cudaGetLastError();
 }
 
+template <int D>
+cudaError_t run_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, cudaStream_t st) {
+  using C = FwdCfg<D>;
+  FwdArgs a;
+  memset(&a, 0, sizeof(a));
+  a.reqs = reqs;
+  a.counts = counts;
+  CUtensorMap dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  auto kern = sm103_fwd_kernel<D, __nv_bfloat16, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+  if (e != cudaSuccess) return e;
+  kern<<<num_sms(), kThreads, C::kSmem, st>>>(dummy, dummy, dummy, a);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_sm103_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, int d, cudaStream_t st) {
+  if (d == 64) return run_fwd_ragged<64>(reqs, counts, st);
+  if (d == 128) return run_fwd_ragged<128>(reqs, counts, st);
+  return cudaErrorNotSupported;
+}
 
 cudaError_t launch_sm103_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v,
                              void* out, int out_dtype, float* lse2, float* ot, uint32_t, cudaStream_t st) {

@@ -51,6 +51,47 @@ class gattn_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+class gattn_serve_cfg(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int32),
+        ("Y", ctypes.c_int32),
+        ("X", ctypes.c_int32),
+        ("core", ctypes.c_int32 * 3),
+        ("halo", ctypes.c_int32 * 3),
+        ("window", ctypes.c_int32),
+        ("steps", ctypes.c_int32),
+        ("c", ctypes.c_float),
+        ("max_active", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+        ("hbm_budget", ctypes.c_size_t),
+    ]
+
+
+class gattn_request(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("nh", ctypes.c_int32), ("z0", ctypes.c_void_p), ("z0_on_device", ctypes.c_int32)]
+
+
+class gattn_serve_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64),
+        ("admitted", ctypes.c_int64),
+        ("completed", ctypes.c_int64),
+        ("rejected", ctypes.c_int64),
+        ("active", ctypes.c_int64),
+        ("waiting", ctypes.c_int64),
+        ("iterations", ctypes.c_int64),
+        ("p50_latency_s", ctypes.c_double),
+        ("p99_latency_s", ctypes.c_double),
+        ("mean_latency_s", ctypes.c_double),
+        ("max_latency_s", ctypes.c_double),
+        ("token_steps", ctypes.c_double),
+        ("gpu_busy_s", ctypes.c_double),
+        ("wall_s", ctypes.c_double),
+        ("hbm_in_use", ctypes.c_size_t),
+        ("hbm_peak", ctypes.c_size_t),
+    ]
+
+
 class gattn_desc(ctypes.Structure):
     _fields_ = [
         ("B", ctypes.c_int32),
@@ -95,6 +136,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gattn_bwd": ([D, P, P, P, P, P, P, S, P, P, P, P, S, P], ctypes.c_int),
         "gattn_stream_status": ([P], ctypes.c_int),
         "gattn_fwd_noalloc": ([D, P, P, P, P, P], ctypes.c_int),
+        "gattn_serve_request_bytes": ([ctypes.POINTER(gattn_serve_cfg), ctypes.c_int32, ctypes.c_int32], S),
+        "gattn_serve_create": ([ctypes.POINTER(gattn_serve_cfg), P, ctypes.POINTER(P)], ctypes.c_int),
+        "gattn_serve_submit": ([P, ctypes.POINTER(gattn_request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "gattn_serve_step": ([P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "gattn_serve_poll": (
+            [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), P],
+            ctypes.c_int,
+        ),
+        "gattn_serve_stats": ([P, ctypes.POINTER(gattn_serve_stats_t)], ctypes.c_int),
+        "gattn_serve_destroy": ([P], None),
         "gattn_profile_enable": ([ctypes.c_int32], ctypes.c_int),
         "gattn_profile_read": ([ctypes.POINTER(gattn_kernel_stat), ctypes.c_int32], ctypes.c_int32),
     }
@@ -206,6 +257,121 @@ def gattn_profile_read() -> dict:
     if n < 0:
         raise GattnError(-n, "gattn_profile_read")
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n, 16))}
+
+
+# ---------------------------------------------------------------- serving ABI, one to one
+def gattn_serve_request_bytes(cfg, T, nh) -> int:
+    return load_library().gattn_serve_request_bytes(ctypes.byref(cfg), int(T), int(nh))
+
+
+def gattn_serve_create(cfg, stream=None):
+    """Returns (status, server handle); stream None lets the server own a stream."""
+    h = ctypes.c_void_p()
+    st = load_library().gattn_serve_create(ctypes.byref(cfg), None if stream is None else _stream(stream), ctypes.byref(h))
+    return st, h
+
+
+def gattn_serve_submit(server, req):
+    """Returns (status, request id)."""
+    rid = ctypes.c_uint64()
+    st = load_library().gattn_serve_submit(server, ctypes.byref(req), ctypes.byref(rid))
+    return st, rid.value
+
+
+def gattn_serve_step(server):
+    """Returns (status, n_active, n_waiting)."""
+    a, w = ctypes.c_int32(), ctypes.c_int32()
+    st = load_library().gattn_serve_step(server, ctypes.byref(a), ctypes.byref(w))
+    return st, a.value, w.value
+
+
+def gattn_serve_poll(server, rid, result_host=None):
+    """Returns (status, done, latency_s)."""
+    done, lat = ctypes.c_int32(), ctypes.c_double()
+    st = load_library().gattn_serve_poll(server, ctypes.c_uint64(rid), ctypes.byref(done), ctypes.byref(lat), _ptr(result_host))
+    return st, bool(done.value), lat.value
+
+
+def gattn_serve_stats(server) -> gattn_serve_stats_t:
+    out = gattn_serve_stats_t()
+    check(load_library().gattn_serve_stats(server, ctypes.byref(out)), "gattn_serve_stats")
+    return out
+
+
+def gattn_serve_destroy(server) -> None:
+    load_library().gattn_serve_destroy(server)
+
+
+def serve_cfg(d=64, Y=32, X=64, core=(1, 16, 16), halo=(0, 4, 4), window="hann", steps=20, c=0.5, max_active=256,
+              use_graph=True, hbm_budget=150 * 10**9):
+    cfg = gattn_serve_cfg()
+    cfg.d, cfg.Y, cfg.X = int(d), int(Y), int(X)
+    for a in range(3):
+        cfg.core[a] = int(core[a])
+        cfg.halo[a] = int(halo[a])
+    cfg.window = GATTN_WINDOW_HANN if window == "hann" else GATTN_WINDOW_FLAT
+    cfg.steps, cfg.c, cfg.max_active = int(steps), float(c), int(max_active)
+    cfg.use_graph = 1 if use_graph else 0
+    cfg.hbm_budget = int(hbm_budget)
+    return cfg
+
+
+class Server:
+    """Owns a gattn_server; submit BF16 states (CPU or CUDA tensors [nh, N, d])."""
+
+    def __init__(self, cfg, stream=None):
+        self.cfg = cfg
+        st, self.h = gattn_serve_create(cfg, stream)
+        check(st, "gattn_serve_create")
+        self._keep = {}
+
+    def submit(self, z0: torch.Tensor) -> int:
+        nh, N, d = z0.shape
+        if z0.dtype != torch.bfloat16 or d != self.cfg.d or N % (self.cfg.Y * self.cfg.X):
+            raise ValueError("z0 must be BF16 [nh, T*Y*X, d]")
+        z0 = z0.contiguous()
+        req = gattn_request()
+        req.T, req.nh, req.z0 = N // (self.cfg.Y * self.cfg.X), nh, z0.data_ptr()
+        req.z0_on_device = 1 if z0.is_cuda else 0
+        st, rid = gattn_serve_submit(self.h, req)
+        check(st, "gattn_serve_submit")
+        if z0.is_cuda:
+            self._keep[rid] = z0  # read at admission
+        return rid
+
+    def step(self):
+        st, a, w = gattn_serve_step(self.h)
+        check(st, "gattn_serve_step")
+        return a, w
+
+    def result(self, rid, shape):
+        out = torch.empty(shape, dtype=torch.bfloat16)
+        st, done, lat = gattn_serve_poll(self.h, rid, out)
+        check(st, "gattn_serve_poll")
+        if done:
+            self._keep.pop(rid, None)
+        return (out, lat) if done else (None, None)
+
+    def done(self, rid) -> bool:
+        st, done, _ = gattn_serve_poll(self.h, rid, None)
+        check(st, "gattn_serve_poll")
+        if done:
+            self._keep.pop(rid, None)
+        return done
+
+    def stats(self):
+        return gattn_serve_stats(self.h)
+
+    def close(self):
+        if self.h:
+            gattn_serve_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def check(status: int, what: str = "gattn") -> None:

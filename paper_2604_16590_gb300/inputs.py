@@ -92,3 +92,38 @@ def workload_inputs(w: Workload, device="cpu", with_grad: bool = True):
     if not with_grad:
         return q, k, v
     return q, k, v, upstream_grad(w.shape, w.seed, w.dtype, device)
+
+
+@dataclass(frozen=True)
+class ServeRequestSpec:
+    """One synthetic posterior-sampling request of the serving workload."""
+
+    arrival_s: float
+    T: int  # frames; N = T * Y * X
+    nh: int
+    seed: int
+
+
+def poisson_requests(n=256, rate=40.0, n_min=16384, n_max=2097152, frame=2048, heads=(8, 16), seed=20265):
+    """Serving workload: n requests, Poisson arrivals at `rate` per second
+    (seeded exponential gaps), token count N log-uniform in [n_min, n_max]
+    rounded to a multiple of `frame` (one 32 x 64 frame of patch tokens),
+    heads uniform over `heads`."""
+    import math
+    import random
+
+    rng = random.Random(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.expovariate(rate)
+        N = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
+        T = max(1, int(round(N / frame)))
+        out.append(ServeRequestSpec(t, T, rng.choice(heads), seed * 1000 + i))
+    return out
+
+
+def request_state(spec: ServeRequestSpec, Y=32, X=64, d=64, std=0.5, device="cpu"):
+    """Initial state z0 [nh, T*Y*X, d] BF16 of a request, iid N(0, std^2)."""
+    (z,) = qkv((spec.nh, spec.T * Y * X, d), spec.seed, std, "bf16", device, n=1)
+    return z

@@ -79,3 +79,13 @@ def test_fwd_rejects_bad_pointers_without_touching_the_gpu(lib):
     # too-small saved buffer
     assert gattn.gattn_fwd(d, 16, 16, 16, 16, 16, saved_bytes=16, stream=0) == 3
     assert gattn.gattn_bwd(d, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, saved_bytes=1 << 40, ws_bytes=16, stream=0) == 3
+
+
+def test_serve_request_bytes_on_host(lib):
+    cfg = gattn.serve_cfg(d=64, Y=32, X=64, core=(1, 16, 16), halo=(0, 4, 4))
+    T, nh = 4, 8
+    b = gattn.gattn_serve_request_bytes(cfg, T, nh)
+    N = T * 32 * 64
+    assert b >= 2 * nh * N * 64 * 2  # state + attention output (BF16)
+    assert gattn.gattn_serve_request_bytes(cfg, 0, nh) == 0
+    assert gattn.gattn_serve_request_bytes(cfg, 2 * T, nh) > b

@@ -1,0 +1,108 @@
+"""Serving engine (continuous batching of posterior-sampling requests).
+
+Each request runs `steps` denoising steps z <- z + c (GPA(z) - z) with its
+state kept on the device; engine iterations batch all active requests into one
+ragged attention launch and one merge-update launch (CUDA graph).  Checked:
+one step against the FP64 oracle, bitwise identity of a request's result alone
+and in a mix, admission under the HBM budget and the slot limit, statistics.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2604_16590_gb300 import build, gattn, serving
+from paper_2604_16590_gb300.inputs import ServeRequestSpec, request_state
+from tests._parity import assert_close
+
+pytestmark = pytest.mark.gpu
+
+Y, X, D = 32, 64, 64
+CORE, HALO = (1, 16, 16), (0, 4, 4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    gattn.load_library()
+
+
+def _cfg(**kw):
+    base = dict(d=D, Y=Y, X=X, core=CORE, halo=HALO, steps=1, c=0.5, max_active=16, hbm_budget=8 * 10**9)
+    base.update(kw)
+    return gattn.serve_cfg(**base)
+
+
+def test_one_step_matches_oracle():
+    spec = ServeRequestSpec(0.0, 2, 2, 77)
+    z0 = request_state(spec, Y, X, D)
+    with gattn.Server(_cfg(steps=1)) as srv:
+        rid = srv.submit(z0)
+        srv.step()
+        z1, lat = srv.result(rid, z0.shape)
+    assert z1 is not None and lat >= 0
+    T = spec.T
+    geo = oracle.Geometry(1, spec.nh, D, T, Y, X, CORE, HALO)
+    z = z0.double().numpy()[None]
+    att = oracle.forward(geo, z, z, z)[0]
+    ref = z[0] + 0.5 * (att - z[0])
+    assert_close("serve/z1", z1.double().numpy()[None], ref[None], 2e-2, 3e-3)
+
+
+@pytest.mark.parametrize("use_graph", [True, False], ids=["graph", "direct"])
+def test_result_is_identical_alone_and_in_a_mix(use_graph):
+    a = ServeRequestSpec(0.0, 3, 2, 101)
+    others = [ServeRequestSpec(0.0, 1 + i, 8 if i % 2 else 4, 200 + i) for i in range(4)]
+    za = request_state(a, Y, X, D)
+    with gattn.Server(_cfg(steps=3, use_graph=use_graph)) as srv:
+        rid = srv.submit(za)
+        while not srv.done(rid):
+            srv.step()
+        alone, _ = srv.result(rid, za.shape)
+    with gattn.Server(_cfg(steps=3, use_graph=use_graph)) as srv:
+        ids = [srv.submit(request_state(o, Y, X, D)) for o in others[:2]]
+        srv.step()  # the mix is already one step in when the request arrives
+        rid = srv.submit(za)
+        ids += [srv.submit(request_state(o, Y, X, D, device="cuda")) for o in others[2:]]
+        while not srv.done(rid):
+            srv.step()
+        mixed, _ = srv.result(rid, za.shape)
+        while srv.stats().active + srv.stats().waiting > 0:
+            srv.step()
+        st = srv.stats()
+    assert torch.equal(alone, mixed)
+    assert st.completed == 5
+
+
+def test_admission_respects_hbm_budget_and_slots():
+    cfg = _cfg(steps=2, max_active=8)
+    per = gattn.gattn_serve_request_bytes(cfg, 2, 4)
+    cfg.hbm_budget = 2 * per + per // 2  # room for two such requests at a time
+    specs = [ServeRequestSpec(0.0, 2, 4, 300 + i) for i in range(5)]
+    with gattn.Server(cfg) as srv:
+        ids = [srv.submit(request_state(s, Y, X, D)) for s in specs]
+        seen = 0
+        while not all(srv.done(r) for r in ids):
+            active, waiting = srv.step()
+            seen = max(seen, active)
+            assert srv.stats().hbm_in_use <= cfg.hbm_budget
+        st = srv.stats()
+        # a request larger than the whole budget is refused
+        big = request_state(ServeRequestSpec(0.0, 64, 16, 9), Y, X, D)
+        with pytest.raises(gattn.GattnError) as e:
+            srv.submit(big)
+        assert e.value.status == 6
+    assert seen <= 2
+    assert st.completed == 5 and st.hbm_peak <= cfg.hbm_budget
+    assert 0 < st.p50_latency_s <= st.p99_latency_s <= st.max_latency_s
+
+
+def test_request_loop_reports_latency_percentiles():
+    specs = [ServeRequestSpec(0.002 * i, 1 + (i % 3), 8, 400 + i) for i in range(6)]
+    with gattn.Server(_cfg(steps=4, max_active=4)) as srv:
+        lat = serving.run(srv, specs, Y, X, D, device="cuda", realtime=True)
+        st = srv.stats()
+    assert len(lat) == 6 and all(v > 0 for v in lat.values())
+    assert st.completed == 6 and st.iterations >= 4
+    assert st.p50_latency_s <= st.p99_latency_s
+    assert st.token_steps == sum(8 * s.T * Y * X * 4 for s in specs)
