@@ -164,6 +164,36 @@ def oracle_sample(w, q, k, v, go, target_s=12.0):
     return gtok, oracle.threads(), desc, tR
 
 
+def run_serving(n_requests, rank=0):
+    """Serving workload: n posterior-sampling requests with Poisson arrivals at
+    40 req/s, N log-uniform in [16384, 2097152] (multiples of one 32 x 64
+    frame), 8 or 16 heads, d = 64, BF16 states N(0, 0.5), 20 denoising steps
+    each, small tiles (core 1x16x16, halo 0/4/4), 150 GB HBM budget."""
+    import torch
+
+    from paper_2604_16590_gb300 import gattn, serving
+    from paper_2604_16590_gb300.inputs import poisson_requests, state_pool
+
+    specs = poisson_requests(n=n_requests, seed=20265 + 1000 * rank)
+    pool = state_pool(seed=20265 + 1000 * rank)
+    cfg = gattn.serve_cfg(d=64, Y=32, X=64, core=(1, 16, 16), halo=(0, 4, 4), steps=20, c=0.5, max_active=256,
+                          use_graph=True, hbm_budget=150 * 10**9)
+    with gattn.Server(cfg) as srv:
+        lat = serving.run(srv, specs, 32, 64, 64, device="cuda", realtime=True, pool=pool)
+        st = srv.stats()
+    del pool
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"{n_requests} requests, Poisson 40/s, N log-uniform [16384, 2097152], heads 8|16, d=64, "
+                    "20 steps, core 1x16x16 halo 0/4/4, 150 GB budget",
+        "requests": int(st.completed), "rejected": int(st.rejected), "iterations": int(st.iterations),
+        "p50_latency_s": st.p50_latency_s, "p99_latency_s": st.p99_latency_s, "mean_latency_s": st.mean_latency_s,
+        "max_latency_s": st.max_latency_s, "token_steps": st.token_steps, "wall_s": st.wall_s,
+        "gpu_busy_s": st.gpu_busy_s, "token_steps_per_s": st.token_steps / st.wall_s if st.wall_s > 0 else None,
+        "hbm_peak_gb": st.hbm_peak / 1e9, "graph": True, "n_latencies": len(lat),
+    }
+
+
 def run_reference(args, w):
     import torch
 
@@ -205,6 +235,8 @@ def main():
     ap.add_argument("--workload", default="c2_262k_p")
     ap.add_argument("--fp32-steps", type=int, default=1, help="timed steps of the plain FP32 form (0 = skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--serve-requests", type=int, default=256,
+                    help="requests of the serving run (Poisson 40/s, 20 steps; 0 = skip)")
     args = ap.parse_args()
 
     from paper_2604_16590_gb300.inputs import WORKLOADS
@@ -235,6 +267,18 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    # ---------------------------------------------------------------- serving: continuous batching (rank-local),
+    # run first so that its HBM budget does not compete with the step buffers
+    serve = None
+    if args.serve_requests > 0:
+        serve = run_serving(args.serve_requests, rank)
+        if world > 1:
+            t_srv = torch.tensor([serve["wall_s"]], device=dev)
+            tok = torch.tensor([serve["token_steps"]], device=dev)
+            dist.all_reduce(t_srv, op=dist.ReduceOp.MAX)
+            dist.all_reduce(tok)
+            serve["token_steps_per_s_all_ranks"] = float(tok.item()) / float(t_srv.item())
 
     # ---------------------------------------------------------------- inputs (per rank)
     q, k, v = qkv(w.shape, w.seed + 1000 * rank, w.std, "bf16", device=dev)
@@ -392,6 +436,7 @@ def main():
             "hbm": hbm,
             "kernels": kernels,
             "fp32_form": fp32,
+            "serve": serve,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

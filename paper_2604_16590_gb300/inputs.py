@@ -127,3 +127,24 @@ def request_state(spec: ServeRequestSpec, Y=32, X=64, d=64, std=0.5, device="cpu
     """Initial state z0 [nh, T*Y*X, d] BF16 of a request, iid N(0, std^2)."""
     (z,) = qkv((spec.nh, spec.T * Y * X, d), spec.seed, std, "bf16", device, n=1)
     return z
+
+
+def state_pool(elems=2 * 16 * 2097152 * 64 // 2 + 1024, seed=20265, std=0.5, device="cuda"):
+    """One shared buffer of iid N(0, std^2) BF16 values; request states are
+    seeded slices of it (see pooled_state), so a long serving run draws its
+    inputs without one allocation per request.  Default size covers the
+    largest serving request (16 heads x 2,097,152 tokens x d = 64)."""
+    (z,) = qkv((elems,), seed, std, "bf16", device, n=1)
+    return z
+
+
+def pooled_state(spec: ServeRequestSpec, pool, Y=32, X=64, d=64):
+    """View [nh, T*Y*X, d] of the pool at an offset drawn from the request's seed."""
+    import random
+
+    n = spec.nh * spec.T * Y * X * d
+    if n > pool.numel():
+        raise ValueError("state pool too small for this request")
+    off = random.Random(spec.seed).randrange(0, pool.numel() - n + 1)
+    off -= off % 8  # 16-byte aligned
+    return pool[off : off + n].view(spec.nh, spec.T * Y * X, d)

@@ -9,15 +9,16 @@ import time
 import torch
 
 from . import gattn
-from .inputs import request_state
+from .inputs import pooled_state, request_state
 
 
-def run(server: gattn.Server, specs, Y=32, X=64, d=64, device="cuda", realtime=True, on_done=None):
+def run(server: gattn.Server, specs, Y=32, X=64, d=64, device="cuda", realtime=True, on_done=None, pool=None):
     """Serve `specs` (inputs.ServeRequestSpec); returns {request index: latency_s}.
 
     With realtime=True a request is submitted once the wall clock passes its
     arrival time (engine iterations keep running meanwhile), otherwise all
-    requests are submitted up front in arrival order."""
+    requests are submitted up front in arrival order.  With `pool` (see
+    inputs.state_pool) the initial states are views into that device buffer."""
     pending = sorted(range(len(specs)), key=lambda i: specs[i].arrival_s)
     ids = {}
     lat = {}
@@ -27,7 +28,10 @@ def run(server: gattn.Server, specs, Y=32, X=64, d=64, device="cuda", realtime=T
         now = time.perf_counter() - t0
         while k < len(pending) and (not realtime or specs[pending[k]].arrival_s <= now):
             i = pending[k]
-            z0 = request_state(specs[i], Y, X, d, device=device)
+            if pool is not None:
+                z0 = pooled_state(specs[i], pool, Y, X, d)
+            else:
+                z0 = request_state(specs[i], Y, X, d, device=device)
             ids[i] = server.submit(z0)
             k += 1
         active, waiting = server.step()
