@@ -174,8 +174,10 @@ def run_serving(n_requests, rank=0):
     from paper_2604_16590_gb300 import gattn, serving
     from paper_2604_16590_gb300.inputs import poisson_requests, state_pool
 
-    specs = poisson_requests(n=n_requests, seed=20265 + 1000 * rank)
-    pool = state_pool(seed=20265 + 1000 * rank)
+    from paper_2604_16590_gb300.replicas import replica_seed
+
+    specs = poisson_requests(n=n_requests, seed=replica_seed(20265, rank))
+    pool = state_pool(seed=replica_seed(20265, rank))
     cfg = gattn.serve_cfg(d=64, Y=32, X=64, core=(1, 16, 16), halo=(0, 4, 4), steps=20, c=0.5, max_active=256,
                           use_graph=True, hbm_budget=150 * 10**9)
     with gattn.Server(cfg) as srv:
@@ -249,7 +251,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2604_16590_gb300 import build, gattn
+    from paper_2604_16590_gb300 import build, gattn, replicas
     from paper_2604_16590_gb300.inputs import qkv, upstream_grad
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -274,15 +276,12 @@ def main():
     if args.serve_requests > 0:
         serve = run_serving(args.serve_requests, rank)
         if world > 1:
-            t_srv = torch.tensor([serve["wall_s"]], device=dev)
-            tok = torch.tensor([serve["token_steps"]], device=dev)
-            dist.all_reduce(t_srv, op=dist.ReduceOp.MAX)
-            dist.all_reduce(tok)
-            serve["token_steps_per_s_all_ranks"] = float(tok.item()) / float(t_srv.item())
+            t_srv = replicas.max_over_ranks(serve["wall_s"], device=dev)
+            serve["token_steps_per_s_all_ranks"] = replicas.sum_over_ranks(serve["token_steps"], device=dev) / t_srv
 
     # ---------------------------------------------------------------- inputs (per rank)
-    q, k, v = qkv(w.shape, w.seed + 1000 * rank, w.std, "bf16", device=dev)
-    go = upstream_grad(w.shape, w.seed + 1000 * rank, "bf16", device=dev)
+    q, k, v = qkv(w.shape, replicas.replica_seed(w.seed, rank), w.std, "bf16", device=dev)
+    go = upstream_grad(w.shape, replicas.replica_seed(w.seed, rank), "bf16", device=dev)
     tiling = gattn.Tiling(w.grid, w.core, w.halo)
     desc = gattn.desc_for(q, tiling, torch.bfloat16)
     out = torch.empty_like(q)
@@ -321,13 +320,9 @@ def main():
     st = gattn.gattn_stream_status(stream)
     if st != 0:
         raise RuntimeError(f"device status after timed steps: {gattn.STATUS.get(st, st)}")
-    ms = e0.elapsed_time(e1) / args.steps
-    t_max = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms = float(t_max.item())
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
     tokens_per_step = w.B * w.N * world
-    value = tokens_per_step / (ms * 1e-3) / 1e9
+    value = replicas.weak_scaling_value(w.B * w.N, world, ms * 1e-3) / 1e9
     launches = sum(n for n, _ in kstats.values())
 
     # ---------------------------------------------------------------- roofline of the dominant kernel
@@ -377,11 +372,7 @@ def main():
         e2e_step()
     e3.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e2.elapsed_time(e3) / e2e_steps
-    t_e2e = torch.tensor([e2e_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t_e2e.item())
+    e2e_ms = replicas.max_over_ranks(e2.elapsed_time(e3) / e2e_steps, device=dev)
     bytes_io = 4 * q.numel() * q.element_size()
     del dq_in, dk_in, dv_in, dgo_in, host_in, host_out
 

@@ -71,6 +71,13 @@ typedef enum { GATTN_WINDOW_HANN = 0, GATTN_WINDOW_FLAT = 1 } gattn_window;
 
 /* flags */
 #define GATTN_FLAG_DEBUG_BOUNDS 0x1u /* device-side index checks on global accesses */
+/* Test hook for failure detection (BF16 forward only): the MMA-issuing thread
+ * of every CTA first waits on an mbarrier that nothing arrives on.  The
+ * bounded wait gives up after ~20 ms, the CTA raises its abort flag, drains
+ * the loads it issued, frees its tensor memory and exits; the call returns
+ * GATTN_OK and gattn_stream_status() then reports GATTN_ERR_TIMEOUT.  The
+ * output is not computed.  The context stays usable. */
+#define GATTN_FLAG_TEST_STALL 0x2u
 
 /*
  * Problem descriptor.

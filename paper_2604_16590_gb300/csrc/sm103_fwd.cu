@@ -47,8 +47,8 @@ struct FwdCfg {
   static constexpr int kV = kK + kStages * kBlock;
   static constexpr int kBar = kV + kStages * kBlock;
   // q_full, q_empty, qt_full, k_full[S], k_empty[S], v_full[S], v_empty[S], s_full[2], s_empty[2],
-  // p_full, pv_done[2], o_empty, drain
-  static constexpr int kNumBars = 3 + 4 * kStages + 4 + 5;
+  // p_full, pv_done[2], o_empty, drain, never (test hook: nothing arrives on it)
+  static constexpr int kNumBars = 3 + 4 * kStages + 4 + 6;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kRed = kMisc + 16;           // float [3 slots][2 half][128 rows]
   static constexpr int kSmem = kRed + 3072 + 1024;  // + slack for 1024-byte alignment
@@ -66,6 +66,7 @@ struct FwdArgs {
   float* lse2;
   float* ot;
   int items;  // B*nh * ntiles * nbmax_tot
+  uint32_t flags;  // GATTN_FLAG_*
   // ragged mode (serving): per-request descriptors and device-side counts
   const ReqDesc* reqs;
   const int64_t* counts;
@@ -334,6 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* pv_done = p_full + 1;  // [2], one per P buffer
   uint64_t* o_empty = pv_done + 2;
   uint64_t* drain = o_empty + 1;
+  uint64_t* never = drain + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
 
@@ -357,6 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(pv_done + 1, 1);
     mbar_init(o_empty, kMathWarps);
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     fence_mbar_init();
     if (!RAGGED) {
@@ -441,6 +444,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t sK = smem_u32(smem + C::kK), sV = smem_u32(smem + C::kV);
       uint32_t G = 0, W = 0;
       bool ok = true;
+      if (a.flags & GATTN_FLAG_TEST_STALL)  // failure-detection hook: a wait that cannot complete
+        ok = mbar_wait<set_status_fwd>(never, 0, abort_flag, true, 20000000ull);
       // P V of global block Gp (first block of its item: fresh accumulator)
       auto issue_pv = [&](uint32_t Gp, bool first) -> bool {
         const uint32_t st = Gp % C::kStages, pb = Gp % C::kPBufs;
@@ -629,7 +634,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int D, typename OutT>
 cudaError_t run_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v, void* out,
-                    float* lse2, float* ot, cudaStream_t st) {
+                    float* lse2, float* ot, uint32_t flags, cudaStream_t st) {
   using C = FwdCfg<D>;
   FwdArgs a;
   a.g = g;
@@ -638,6 +643,7 @@ cudaError_t run_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
   a.ot = ot;
   a.reqs = nullptr;
   a.counts = nullptr;
+  a.flags = flags;
   const int64_t items = (int64_t)g.B * g.nh * g.ntiles * g.nbmax_tot;
   if (items >= (1LL << 31)) return cudaErrorNotSupported;
   a.items = (int)items;
@@ -680,13 +686,14 @@ cudaError_t launch_sm103_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, 
 }
 
 cudaError_t launch_sm103_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v,
-                             void* out, int out_dtype, float* lse2, float* ot, uint32_t, cudaStream_t st) {
+                             void* out, int out_dtype, float* lse2, float* ot, uint32_t flags, cudaStream_t st) {
   const bool bf = out_dtype == GATTN_BF16;
   if (g.d == 64)
-    return bf ? run_fwd<64, __nv_bfloat16>(g, q, k, v, out, lse2, ot, st) : run_fwd<64, float>(g, q, k, v, out, lse2, ot, st);
+    return bf ? run_fwd<64, __nv_bfloat16>(g, q, k, v, out, lse2, ot, flags, st)
+              : run_fwd<64, float>(g, q, k, v, out, lse2, ot, flags, st);
   if (g.d == 128)
-    return bf ? run_fwd<128, __nv_bfloat16>(g, q, k, v, out, lse2, ot, st)
-              : run_fwd<128, float>(g, q, k, v, out, lse2, ot, st);
+    return bf ? run_fwd<128, __nv_bfloat16>(g, q, k, v, out, lse2, ot, flags, st)
+              : run_fwd<128, float>(g, q, k, v, out, lse2, ot, flags, st);
   return cudaErrorNotSupported;
 }
 

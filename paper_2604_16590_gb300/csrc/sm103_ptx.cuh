@@ -71,14 +71,14 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t addr, uint32_t pari
 // time limit ends the wait.
 template <void (*SetStatus)(uint32_t)>
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          bool honor_abort = true) {
+                                          bool honor_abort = true, uint64_t timeout_ns = kWaitTimeoutNs) {
   const uint32_t a = smem_u32(bar);
   if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait_sleep(a, parity)) return true;
     if (honor_abort && *abort_flag) return false;
-    if (globaltimer() - t0 > kWaitTimeoutNs || it > (1u << 24)) {
+    if (globaltimer() - t0 > timeout_ns || it > (1u << 24)) {
       *abort_flag = 1;
       SetStatus(GATTN_ERR_TIMEOUT);
       return false;

@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_PKG, "libgattn.so")
 GATTN_BF16, GATTN_FP32 = 0, 1
 GATTN_WINDOW_HANN, GATTN_WINDOW_FLAT = 0, 1
 GATTN_FLAG_DEBUG_BOUNDS = 0x1
+GATTN_FLAG_TEST_STALL = 0x2
 
 STATUS = {
     0: "GATTN_OK",
