@@ -259,11 +259,13 @@ gattn_status gattn_bwd(const gattn_desc* desc, const void* q, const void* k, con
   char* w = static_cast<char*>(ws);
   float* lse2c = reinterpret_cast<float*>(w + bl.lse_off);
   float* dd = reinterpret_cast<float*>(w + bl.dd_off);
+  // the statistics rows are read only by the d = 64 tensor-core dK/dV kernel
+  void* ext = desc->in_dtype == GATTN_BF16 && g.d == 64 ? static_cast<void*>(w + bl.ext_off) : nullptr;
   float* dq_s = reinterpret_cast<float*>(w + bl.dq_off);
   float* dk_s = reinterpret_cast<float*>(w + bl.dk_off);
   float* dv_s = reinterpret_cast<float*>(w + bl.dv_off);
   prof_begin(kKBwdPrep, st);
-  cudaError_t e = launch_bwd_prep(g, out, desc->out_dtype, dout, desc->in_dtype, lse2, ot, lse2c, dd, st);
+  cudaError_t e = launch_bwd_prep(g, out, desc->out_dtype, dout, desc->in_dtype, lse2, ot, lse2c, dd, ext, st);
   prof_end(kKBwdPrep, st);
   if (e != cudaSuccess) return GATTN_ERR_CUDA;
   if (desc->in_dtype == GATTN_FP32)
@@ -271,7 +273,7 @@ gattn_status gattn_bwd(const gattn_desc* desc, const void* q, const void* k, con
                         dv, desc->out_dtype, dq_s, dk_s, dv_s, st);
   else
     e = launch_sm103_bwd(g, (const __nv_bfloat16*)q, (const __nv_bfloat16*)k, (const __nv_bfloat16*)v,
-                         (const __nv_bfloat16*)dout, lse2c, dd, dq, dk, dv, desc->out_dtype, dq_s, dk_s, dv_s,
+                         (const __nv_bfloat16*)dout, lse2c, dd, ext, dq, dk, dv, desc->out_dtype, dq_s, dk_s, dv_s,
                          desc->flags, st);
   if (e == cudaErrorNotSupported) return GATTN_ERR_UNSUPPORTED;
   if (e != cudaSuccess) return GATTN_ERR_CUDA;
@@ -326,6 +328,7 @@ int32_t gattn_profile_read(gattn_kernel_stat* out, int32_t max) {
 gattn_status gattn_stream_status(gattn_stream_t stream) {
   if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return GATTN_ERR_CUDA;
   uint32_t words[] = {fetch_status_simt(), fetch_status_merge(), fetch_status_sm103_fwd(), fetch_status_sm103_bwd(),
+                      fetch_status_sm103_bwd64(),
                       fetch_status_serve()};
   for (uint32_t w : words)
     if (w == ~0u) return GATTN_ERR_CUDA;

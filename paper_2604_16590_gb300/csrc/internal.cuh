@@ -34,8 +34,11 @@ inline SavedLayout saved_layout(const Geom& g) {
 //   lse2c : float[S]      -(log2-domain LSE - log2(w_t / sum w)) (folds the dO_t scaling into P), negated
 //   dd    : float[S]      -D, D = dOut . O_t per slot, negated
 //   dq_s, dk_s, dv_s : float[S * d]  per-tile gradients of multiply-covered rows
+//   ext   : 16 B[S]       BF16 row (x0, x1, x2, y0, y1, y2, 0, 0) per slot: x0 + x1 + x2 = -lse' / (scale
+//                          log2 e) and y0 + y1 + y2 = -D, each split into three BF16 terms; the d = 64
+//                          dK/dV kernel adds both to S^T and dP^T with one extra K = 16 MMA step each
 struct BwdLayout {
-  size_t S, lse_off, dd_off, dq_off, dk_off, dv_off, bytes;
+  size_t S, lse_off, dd_off, ext_off, dq_off, dk_off, dv_off, bytes;
 };
 inline BwdLayout bwd_layout(const Geom& g) {
   BwdLayout b;
@@ -44,7 +47,8 @@ inline BwdLayout bwd_layout(const Geom& g) {
   size_t mat = align_up(b.S * g.d * sizeof(float));
   b.lse_off = 0;
   b.dd_off = vec;
-  b.dq_off = 2 * vec;
+  b.ext_off = 2 * vec;
+  b.dq_off = 2 * vec + align_up(b.S * 16);
   b.dk_off = b.dq_off + mat;
   b.dv_off = b.dk_off + mat;
   b.bytes = b.dv_off + mat;
@@ -73,6 +77,7 @@ uint32_t fetch_status_simt();
 uint32_t fetch_status_merge();
 uint32_t fetch_status_sm103_fwd();
 uint32_t fetch_status_sm103_bwd();
+uint32_t fetch_status_sm103_bwd64();
 uint32_t fetch_status_serve();
 
 // ---- per-kernel device timing (gattn_profile_*); no-ops unless enabled
@@ -90,7 +95,7 @@ cudaError_t launch_simt_bwd(const Geom& g, const float* q, const float* k, const
 cudaError_t launch_merge_fwd(const Geom& g, const float* ot, void* out, int out_dtype, cudaStream_t st);
 cudaError_t launch_bwd_prep(const Geom& g, const void* out, int out_dtype, const void* dout,
                             int in_dtype, const float* lse2, const float* ot, float* lse2c, float* dd,
-                            cudaStream_t st);
+                            void* ext, cudaStream_t st);
 cudaError_t launch_merge_bwd(const Geom& g, const float* dq_s, const float* dk_s, const float* dv_s,
                              void* dq, void* dk, void* dv, int out_dtype, cudaStream_t st);
 cudaError_t launch_sm103_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k,
@@ -98,8 +103,12 @@ cudaError_t launch_sm103_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_b
                              uint32_t flags, cudaStream_t st);
 cudaError_t launch_sm103_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k,
                              const __nv_bfloat16* v, const __nv_bfloat16* dout, const float* lse2c,
-                             const float* dd, void* dq, void* dk, void* dv, int out_dtype, float* dq_s,
-                             float* dk_s, float* dv_s, uint32_t flags, cudaStream_t st);
+                             const float* dd, const void* ext, void* dq, void* dk, void* dv, int out_dtype,
+                             float* dq_s, float* dk_s, float* dv_s, uint32_t flags, cudaStream_t st);
+cudaError_t launch_sm103_bwd64(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k,
+                               const __nv_bfloat16* v, const __nv_bfloat16* dout, const float* lse2c,
+                               const float* dd, const void* ext, void* dq, void* dk, void* dv, int out_dtype,
+                               float* dq_s, float* dk_s, float* dv_s, cudaStream_t st);
 
 // ---- ragged (multi-request) forward, used by the serving engine.
 // One descriptor per active request, in device memory, sorted by item0: the

@@ -83,6 +83,31 @@ __global__ void __launch_bounds__(kThreads) merge_fwd_kernel(Geom g, const float
   }
 }
 
+// x as the sum of three BF16 terms (each the rounding of what the previous ones
+// leave), exact to about 2^-24 |x|.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r1);
+  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+
+// One 16-byte B-operand row (K = 8 BF16 values) of the d = 64 dK/dV kernel:
+// (x0, x1, x2, y0, y1, y2, 0, 0) with x0+x1+x2 = x and y0+y1+y2 = y.  With an
+// A operand of ones in K-columns 0..2 (resp. 3..5) one extra MMA step adds x
+// (resp. y) to every element of the row's S^T (resp. dP^T) column.
+__device__ __forceinline__ uint4 stat_row(float x, float y) {
+  __nv_bfloat16 v[8];
+  split3(x, v[0], v[1], v[2]);
+  split3(y, v[3], v[4], v[5]);
+  v[6] = v[7] = __float2bfloat16_rn(0.f);
+  uint4 r;
+  uint32_t* w = reinterpret_cast<uint32_t*>(&r);
+  for (int i = 0; i < 4; ++i)
+    w[i] = (uint32_t)__bfloat16_as_ushort(v[2 * i]) | ((uint32_t)__bfloat16_as_ushort(v[2 * i + 1]) << 16);
+  return r;
+}
+
 // Per (batch*head, tile, row) slot: fold the merge weight c = w_t / sum w into
 // the log-sum-exp (lse' = lse2 - log2 c, so exp2(s - lse') = c P) and form
 // D = dOut . O_t.  O_t is the output itself for single-cover rows, else the
@@ -97,7 +122,8 @@ __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* 
                                                             const InT* __restrict__ dout,
                                                             const float* __restrict__ lse2,
                                                             const float* __restrict__ ot,
-                                                            float* __restrict__ lse2c, float* __restrict__ dd) {
+                                                            float* __restrict__ lse2c, float* __restrict__ dd,
+                                                            uint4* __restrict__ ext) {
   const int F4 = g.d / 4;  // 8, 16 or 32 lanes per slot
   const int64_t S = (int64_t)g.B * g.nh * g.ntiles * g.per_tile;
   const int64_t total = S * F4;
@@ -133,6 +159,8 @@ __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* 
       // padding slot of a box that sticks out of the tile: probability 0
       lse2c[slot] = -INFINITY;
       dd[slot] = 0.f;
+      // finite (the extension MMA multiplies it by the other statistic's zero weights)
+      if (ext) ext[slot] = stat_row(-1e30f, 0.f);
     }
     if (valid && f == 0) {
       float lc = lse2[slot];
@@ -153,6 +181,7 @@ __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* 
       }
       lse2c[slot] = -lc;
       dd[slot] = -part;
+      if (ext) ext[slot] = stat_row(-lc / g.scale_log2, -part);
     }
   }
 }
@@ -211,18 +240,20 @@ cudaError_t launch_merge_fwd(const Geom& g, const float* ot, void* out, int out_
 }
 
 cudaError_t launch_bwd_prep(const Geom& g, const void* out, int out_dtype, const void* dout, int in_dtype,
-                            const float* lse2, const float* ot, float* lse2c, float* dd, cudaStream_t st) {
+                            const float* lse2, const float* ot, float* lse2c, float* dd, void* ext_,
+                            cudaStream_t st) {
+  uint4* ext = static_cast<uint4*>(ext_);
   const int64_t total = (int64_t)g.B * g.nh * g.ntiles * g.per_tile * (g.d / 4);
   const unsigned grid = grid_for(total);
   using bf = __nv_bfloat16;
   if (out_dtype == GATTN_BF16 && in_dtype == GATTN_BF16)
-    bwd_prep_kernel<bf, bf><<<grid, kThreads, 0, st>>>(g, (const bf*)out, (const bf*)dout, lse2, ot, lse2c, dd);
+    bwd_prep_kernel<bf, bf><<<grid, kThreads, 0, st>>>(g, (const bf*)out, (const bf*)dout, lse2, ot, lse2c, dd, ext);
   else if (out_dtype == GATTN_BF16)
-    bwd_prep_kernel<bf, float><<<grid, kThreads, 0, st>>>(g, (const bf*)out, (const float*)dout, lse2, ot, lse2c, dd);
+    bwd_prep_kernel<bf, float><<<grid, kThreads, 0, st>>>(g, (const bf*)out, (const float*)dout, lse2, ot, lse2c, dd, ext);
   else if (in_dtype == GATTN_BF16)
-    bwd_prep_kernel<float, bf><<<grid, kThreads, 0, st>>>(g, (const float*)out, (const bf*)dout, lse2, ot, lse2c, dd);
+    bwd_prep_kernel<float, bf><<<grid, kThreads, 0, st>>>(g, (const float*)out, (const bf*)dout, lse2, ot, lse2c, dd, ext);
   else
-    bwd_prep_kernel<float, float><<<grid, kThreads, 0, st>>>(g, (const float*)out, (const float*)dout, lse2, ot, lse2c, dd);
+    bwd_prep_kernel<float, float><<<grid, kThreads, 0, st>>>(g, (const float*)out, (const float*)dout, lse2, ot, lse2c, dd, ext);
   return cudaGetLastError();
 }
 

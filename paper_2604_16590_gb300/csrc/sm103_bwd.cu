@@ -1,5 +1,6 @@
 // sm103_bwd.cu -- BF16 tensor-core backward of STORM-GPA tile attention on
-// GB300 (sm_103a).  Two deterministic kernels (no atomics):
+// GB300 (sm_103a), general head size (d = 128; d = 64 runs the TMEM-operand
+// kernels of sm103_bwd64.cu).  Two deterministic kernels (no atomics):
 //
 //   dKdV kernel, one work item per (batch*head, tile, 128-key block kb):
 //     for every 64-query half-block i of the tile:
@@ -25,8 +26,7 @@
 // issuer, warps 2..9 elementwise math + epilogue: one TMEM lane = one block row,
 // two warps per lane quadrant, each taking half of the row's columns (eight
 // math warps keep two warps per SM sub-partition to hide TMEM and MUFU latency).
-#include "internal.cuh"
-#include "sm103_common.cuh"
+#include "sm103_bwd_common.cuh"
 
 GATTN_DEFINE_STATUS(sm103_bwd)
 
@@ -36,70 +36,6 @@ using namespace sm103;
 
 __device__ void set_status_bwd(uint32_t c) { set_status(c); }
 #define WAIT(bar, par) mbar_wait<set_status_bwd>((bar), (par), abort_flag)
-
-struct BwdArgs {
-  Geom g;
-  const float* lse2c;
-  const float* dd;
-  void* dq;
-  void* dk;
-  void* dv;
-  float* dq_s;
-  float* dk_s;
-  float* dv_s;
-  int items;  // B*nh * ntiles * nbmax_tot
-};
-
-__device__ __forceinline__ void decode_item(const Geom& g, int w, int& bh, int& tile, int& blk) {
-  blk = w % g.nbmax_tot;
-  const int r = w / g.nbmax_tot;
-  tile = r % g.ntiles;
-  bh = r / g.ntiles;
-}
-
-// byte offset of K-step ks (16 elements) in a 128-byte-swizzled K-major operand
-__device__ __forceinline__ uint32_t kmaj_off(int ks) { return (ks >> 2) * 16384 + (ks & 3) * 32; }
-
-// Epilogue of one D-wide FP32 TMEM row (this thread's lane), scaled by `mul`:
-// to `out` (OutT) if the row is covered by one tile, else to the FP32 slot
-// `scr`; nothing if the row lies outside the tile.  The TMEM loads are
-// warp-synchronous (.sync.aligned), so every lane executes them and only the
-// global stores depend on the lane's row.
-template <int NCOLS, typename OutT>
-__device__ __forceinline__ void tmem_row_epilogue(uint32_t taddr, float mul, bool valid, bool single, OutT* out,
-                                                  float* scr) {
-  uint32_t r[32];
-#pragma unroll
-  for (int c = 0; c < NCOLS / 32; ++c) {
-    tmem_ld32(taddr + c * 32, r);
-    tmem_wait_ld(r);
-    if (valid) {
-#pragma unroll
-      for (int e = 0; e < 32; e += 4) {
-        const float4 v = make_float4(__uint_as_float(r[e]) * mul, __uint_as_float(r[e + 1]) * mul,
-                                     __uint_as_float(r[e + 2]) * mul, __uint_as_float(r[e + 3]) * mul);
-        if (single)
-          store4<OutT>(out + c * 32 + e, v);
-        else
-          store4<float>(scr + c * 32 + e, v);
-      }
-    }
-  }
-}
-
-// Write 32 BF16 values (16 packed words) as half of one 128-byte row (16-byte
-// units 4*ch .. 4*ch+3) of a 128B-swizzled K-major operand buffer.
-__device__ __forceinline__ void store_row32(uint32_t buf, int row, int ch, const uint32_t (&pk)[16]) {
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-    st_shared_v4(buf + row * 128 + (((ch * 4 + u) ^ (row & 7)) << 4), pk[4 * u], pk[4 * u + 1], pk[4 * u + 2],
-                 pk[4 * u + 3]);
-}
-
-// Math warps: kMathWarps warps, two per TMEM lane quadrant; the two warps of a
-// quadrant share its 32 rows and split each row's columns in half.
-constexpr int kMathWarps = 8;
-constexpr int kThreads = 64 + 32 * kMathWarps;
 
 // =============================================================== dK / dV
 template <int D>
@@ -425,24 +361,6 @@ struct QCfg {
 
 // dS = P' (dP - D) for 32 key columns of this thread's query row, packed to
 // BF16; nL = -lse', nD = -D of the row; keys outside the tile masked to 0.
-template <bool MASK>
-__device__ __forceinline__ void dq_half(const uint32_t (&s)[32], const uint32_t (&dp)[32], uint32_t mbits, float sl2,
-                                        float nL, float nD, uint32_t (&pk)[16]) {
-  const uint64_t s2 = f2pack(sl2, sl2), nl2 = f2pack(nL, nL), nd2 = f2pack(nD, nD);
-#pragma unroll
-  for (int c = 0; c < 32; c += 2) {
-    float a0, a1;
-    f2unpack(ffma2(u2pack(s[c], s[c + 1]), s2, nl2), a0, a1);
-    float p0 = ex2(a0), p1 = ex2(a1);
-    if (MASK) {
-      p0 = (mbits >> c) & 1u ? p0 : 0.f;
-      p1 = (mbits >> (c + 1)) & 1u ? p1 : 0.f;
-    }
-    float e0, e1;
-    f2unpack(fmul2(f2pack(p0, p1), fadd2(u2pack(dp[c], dp[c + 1]), nd2)), e0, e1);
-    pk[c >> 1] = pack_bf16(e0, e1);
-  }
-}
 
 template <int D, typename OutT>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -692,599 +610,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// =============================================================== d = 64: operands in TMEM
-// Sᵀ/dPᵀ (and S/dP) are A-operand products of a TMEM-resident K/V (Q/dO)
-// block, and the softmax warps write P'ᵀ/dSᵀ (dS) back into the Sᵀ/dPᵀ (S)
-// columns they read, as BF16 pairs, for the accumulating MMAs to read as their
-// A operand.  Shared memory then only feeds B operands and receives TMA
-// blocks (its 128 B/clk read path otherwise bounds the N = 64 products).
-// A thread of column half ch owns the 32 query (key) columns [32 ch, 32 ch + 32)
-// of a 64-column half block and writes their 16 BF16-pair columns in place at
-// [32 ch, 32 ch + 16); K-step ks of the accumulating MMA therefore reads
-// columns 8 ks (ks < 2) or 32 + 8 (ks - 2).
-__device__ __forceinline__ uint32_t pair_col(int ks) { return ks < 2 ? ks * 8 : 32 + (ks - 2) * 8; }
-
-struct TmCfgKv {
-  static constexpr int D = 64;
-  static constexpr int kBlock = 128 * D * 2;
-  static constexpr int kStages = 3;               // (Q, dOut, -lse', -D) ring
-  static constexpr int kK = 0;
-  static constexpr int kV = kBlock;
-  static constexpr int kQ = 2 * kBlock;
-  static constexpr int kStat = kQ + kStages * 2 * kBlock;
-  static constexpr int kBar = kStat + kStages * 1024;
-  // kv_full, kv_empty, kt_full, qd_full[S], qd_empty[S], s_full[2], p_full[2], acc_full, acc_empty, drain
-  static constexpr int kNumBars = 3 + 2 * kStages + 4 + 3;
-  static constexpr int kMisc = kBar + kNumBars * 8;
-  static constexpr int kSmem = kMisc + 16 + 1024;
-  // TMEM: Sᵀ[2] 0/64, dPᵀ[2] 128/192, dV 256, dK 320, K 384, V 416
-  static constexpr uint32_t kColST = 0, kColDP = 128, kColDV = 256, kColDK = 320, kColK = 384, kColV = 416;
-};
-
-template <typename OutT>
-__global__ void __launch_bounds__(kThreads, 1)
-    sm103_dkdv_tm_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
-                         const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tdo,
-                         const BwdArgs a) {
-  using C = TmCfgKv;
-  constexpr int D = C::D;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kBar);
-  uint64_t* kv_full = bars;
-  uint64_t* kv_empty = bars + 1;
-  uint64_t* kt_full = bars + 2;
-  uint64_t* qd_full = bars + 3;
-  uint64_t* qd_empty = qd_full + C::kStages;
-  uint64_t* s_full = qd_empty + C::kStages;
-  uint64_t* p_full = s_full + 2;
-  uint64_t* acc_full = p_full + 2;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* drain = acc_empty + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    mbar_init(kv_full, 1);
-    mbar_init(kv_empty, kMathWarps);
-    mbar_init(kt_full, kMathWarps);
-    for (int s = 0; s < C::kStages; ++s) {
-      mbar_init(qd_full + s, 1);
-      mbar_init(qd_empty + s, 1);
-    }
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(s_full + s, 1);
-      mbar_init(p_full + s, kMathWarps);
-    }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kMathWarps);
-    mbar_init(drain, 1);
-    *abort_flag = 0;
-    fence_mbar_init();
-    prefetch_tmap(&tq);
-    prefetch_tmap(&tk);
-    prefetch_tmap(&tv);
-    prefetch_tmap(&tdo);
-  }
-  if (warp == 1) {
-    tmem_alloc(tmem_slot, 512);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const Geom& g = a.g;
-
-  if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      uint32_t G = 0, W = 0;
-      uint32_t kv_arm = 0, kv_par = 0, qd_arm = 0, qd_par = 0;
-      bool ok = true;
-      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-        int bh, tile, kb;
-        decode_item(g, w, bh, tile, kb);
-        TileBlocks tbk;
-        tile_blocks(g, tile, tbk);
-        if (kb >= tbk.NB) continue;
-        int o[3];
-        block_origin(g, tbk, kb, o);
-        if (!(ok = WAIT(kv_empty, (W & 1) ^ 1))) break;
-        mbar_arrive_expect_tx(kv_full, 2 * C::kBlock);
-        kv_arm = 1;
-        kv_par = W & 1;
-        tma_load_5d(smem + C::kK, &tk, kv_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
-        tma_load_5d(smem + C::kV, &tv, kv_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
-        const int64_t slot0 = tile_slot0(g, bh, tile);
-        int jt = 0, jy = 0, jx = 0;
-        for (int i = 0; i < tbk.NB; ++i, ++G) {
-          const uint32_t st = G % C::kStages, n = G / C::kStages;
-          const int c1 = tbk.tb.lo[2] + (jx << g.lx), c2 = tbk.tb.lo[1] + (jy << g.ly), c3 = tbk.tb.lo[0] + (jt << g.lt);
-          if (++jx == tbk.nb[2]) {
-            jx = 0;
-            if (++jy == tbk.nb[1]) {
-              jy = 0;
-              ++jt;
-            }
-          }
-          if (!(ok = WAIT(qd_empty + st, (n & 1) ^ 1))) break;
-          mbar_arrive_expect_tx(qd_full + st, 2 * C::kBlock + 1024);
-          qd_arm |= 1u << st;
-          qd_par = (qd_par & ~(1u << st)) | ((n & 1) << st);
-          uint8_t* sq = smem + C::kQ + st * 2 * C::kBlock;
-          tma_load_5d(sq, &tq, qd_full + st, 0, c1, c2, c3, bh);
-          tma_load_5d(sq + C::kBlock, &tdo, qd_full + st, 0, c1, c2, c3, bh);
-          bulk_load(smem + C::kStat + st * 1024, a.lse2c + slot0 + i * 128, 512, qd_full + st);
-          bulk_load(smem + C::kStat + st * 1024 + 512, a.dd + slot0 + i * 128, 512, qd_full + st);
-        }
-        ++W;
-      }
-      if (!ok) {
-        if (kv_arm) mbar_wait<set_status_bwd>(kv_full, kv_par, abort_flag, false);
-        for (int s = 0; s < C::kStages; ++s)
-          if (qd_arm & (1u << s)) mbar_wait<set_status_bwd>(qd_full + s, (qd_par >> s) & 1, abort_flag, false);
-      }
-    }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      constexpr uint32_t idS = idesc_bf16(128, 64, 0);
-      constexpr uint32_t idA = idesc_bf16(128, D, 1);
-      const uint32_t sQ = smem_u32(smem + C::kQ);
-      uint32_t G = 0, H = 0, W = 0;
-      bool ok = true;
-      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-        int bh, tile, kb;
-        decode_item(g, w, bh, tile, kb);
-        TileBlocks tbk;
-        tile_blocks(g, tile, tbk);
-        if (kb >= tbk.NB) continue;
-        if (!(ok = WAIT(kt_full, W & 1))) break;  // K, V in TMEM
-        tc_fence_after();
-        const uint32_t G0 = G, H0 = H;
-        // dV += P'ᵀ dOut_h, dK += dSᵀ Q_h for half block h (A operands from TMEM)
-        auto issue_acc = [&](uint32_t h) -> bool {
-          const uint32_t b = h & 1;
-          const uint32_t gbox = G0 + ((h - H0) >> 1), half = (h - H0) & 1, st = gbox % C::kStages;
-          if (!WAIT(p_full + b, (h >> 1) & 1)) return false;
-          if (h == H0 && !WAIT(acc_empty, (W & 1) ^ 1)) return false;
-          tc_fence_after();
-          const uint32_t sq = sQ + st * 2 * C::kBlock + half * 8192;
-          const uint32_t sdo = sq + C::kBlock;
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t acc = (h != H0 || ks > 0) ? 1u : 0u;
-            umma_bf16_ts(tmem + C::kColDV, tmem + C::kColST + b * 64 + pair_col(ks),
-                         sw128_desc(sdo + ks * 2048, 16384, 1024), idA, acc);
-            umma_bf16_ts(tmem + C::kColDK, tmem + C::kColDP + b * 64 + pair_col(ks),
-                         sw128_desc(sq + ks * 2048, 16384, 1024), idA, acc);
-          }
-          if (half == 1) umma_commit(qd_empty + st);
-          return true;
-        };
-        bool pending = false;
-        for (int i = 0; i < tbk.NB && ok; ++i, ++G) {
-          const uint32_t st = G % C::kStages;
-          if (!(ok = WAIT(qd_full + st, (G / C::kStages) & 1))) break;
-          for (int half = 0; half < 2; ++half, ++H) {
-            const uint32_t b = H & 1;
-            // buffer b was last read by the dV/dK products of half H-2, issued
-            // (after its p_full) before this point: in-order execution
-            const uint32_t sq = sQ + st * 2 * C::kBlock + half * 8192;
-            const uint32_t sdo = sq + C::kBlock;
-#pragma unroll
-            for (int ks = 0; ks < D / 16; ++ks) {
-              umma_bf16_ts(tmem + C::kColST + b * 64, tmem + C::kColK + ks * 8, sw128_desc(sq + kmaj_off(ks), 16, 1024),
-                           idS, ks > 0);
-              umma_bf16_ts(tmem + C::kColDP + b * 64, tmem + C::kColV + ks * 8,
-                           sw128_desc(sdo + kmaj_off(ks), 16, 1024), idS, ks > 0);
-            }
-            umma_commit(s_full + b);
-            if (pending && !(ok = issue_acc(H - 1))) break;
-            pending = true;
-          }
-        }
-        if (!ok) break;
-        if (pending && !(ok = issue_acc(H - 1))) break;
-        umma_commit(acc_full);
-        ++W;
-      }
-      umma_commit(drain);
-      mbar_wait<set_status_bwd>(drain, 0, abort_flag, false);
-    }
-  } else {
-    // ------------------------------------------------------------ elementwise + epilogue (row = key)
-    const int quad = warp & 3;
-    const int ch = (warp - 2) >> 2;
-    const int row = quad * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
-    const float sl2 = g.scale_log2;
-    const uint64_t s2 = f2pack(sl2, sl2);
-    uint32_t G = 0, H = 0, W = 0;
-    bool ok = true;
-    for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-      int bh, tile, kb;
-      decode_item(g, w, bh, tile, kb);
-      TileBlocks tbk;
-      tile_blocks(g, tile, tbk);
-      if (kb >= tbk.NB) continue;
-      // K and V of the key block: shared memory -> TMEM (A operands of Sᵀ, dPᵀ)
-      if (!(ok = WAIT(kv_full, W & 1))) break;
-      {
-        uint32_t r16[16];
-        ld_swizzled_row<4>(smem_u32(smem + C::kK), row, 4 * ch, r16);
-        tmem_st16(tl + C::kColK + 16 * ch, r16);
-        ld_swizzled_row<4>(smem_u32(smem + C::kV), row, 4 * ch, r16);
-        tmem_st16(tl + C::kColV + 16 * ch, r16);
-        tmem_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(kv_empty);
-          mbar_arrive(kt_full);
-        }
-      }
-      for (int i = 0; i < tbk.NB && ok; ++i, ++G) {
-        const uint32_t st = G % C::kStages;
-        if (!(ok = WAIT(qd_full + st, (G / C::kStages) & 1))) break;
-        const float* sL = reinterpret_cast<const float*>(smem + C::kStat + st * 1024);
-        const float* sD = sL + 128;
-        for (int half = 0; half < 2; ++half, ++H) {
-          const uint32_t b = H & 1;
-          if (!(ok = WAIT(s_full + b, (H >> 1) & 1))) break;
-          tc_fence_after();
-          const uint32_t tS = tl + C::kColST + b * 64 + ch * 32;
-          const uint32_t tD = tl + C::kColDP + b * 64 + ch * 32;
-          uint32_t sv[32], dv[32];
-          tmem_ld32(tS, sv);
-          tmem_ld32(tD, dv);
-          tmem_wait_ld(sv);
-          tmem_wait_ld(dv);
-          // P' = exp2(s Sᵀ log2e - lse'), dSᵀ = P' (dPᵀ - D); the stage holds -lse', -D
-          uint32_t pp[16], pd[16];
-          const float4* nL4 = reinterpret_cast<const float4*>(sL + half * 64 + ch * 32);
-          const float4* nD4 = reinterpret_cast<const float4*>(sD + half * 64 + ch * 32);
-#pragma unroll
-          for (int c4 = 0; c4 < 8; ++c4) {
-            const float4 l = nL4[c4], dn = nD4[c4];
-            const int c = 4 * c4;
-            float a0, a1, a2, a3;
-            f2unpack(ffma2(u2pack(sv[c], sv[c + 1]), s2, f2pack(l.x, l.y)), a0, a1);
-            f2unpack(ffma2(u2pack(sv[c + 2], sv[c + 3]), s2, f2pack(l.z, l.w)), a2, a3);
-            const float p0 = ex2(a0), p1 = ex2(a1), p2 = ex2(a2), p3 = ex2(a3);
-            float e0, e1, e2, e3;
-            f2unpack(fmul2(f2pack(p0, p1), fadd2(u2pack(dv[c], dv[c + 1]), f2pack(dn.x, dn.y))), e0, e1);
-            f2unpack(fmul2(f2pack(p2, p3), fadd2(u2pack(dv[c + 2], dv[c + 3]), f2pack(dn.z, dn.w))), e2, e3);
-            pp[2 * c4] = pack_bf16(p0, p1);
-            pp[2 * c4 + 1] = pack_bf16(p2, p3);
-            pd[2 * c4] = pack_bf16(e0, e1);
-            pd[2 * c4 + 1] = pack_bf16(e2, e3);
-          }
-          tmem_st16(tS, pp);  // in place: this thread's own columns
-          tmem_st16(tD, pd);
-          tmem_wait_st();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(p_full + b);
-        }
-      }
-      if (!ok) break;
-      // ---- epilogue: this thread's key row of dK, dV (its half of the columns)
-      if (!(ok = WAIT(acc_full, W & 1))) break;
-      tc_fence_after();
-      int ko[3], kl[3];
-      block_origin(g, tbk, kb, ko);
-      block_row(g, ko, row, kl);
-      const bool kvalid = inside(tbk, kl);
-      const int p[3] = {tbk.tb.lo[0] + kl[0], tbk.tb.lo[1] + kl[1], tbk.tb.lo[2] + kl[2]};
-      const int64_t tok = kvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
-      const bool single = kvalid && single_cover(g, p);
-      const int64_t slot = tile_slot0(g, bh, tile) + kb * 128 + row;
-      const int c0 = ch * (D / 2);
-      tmem_row_epilogue<D / 2, OutT>(tl + C::kColDK + c0, g.scale, kvalid, single,
-                                     static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * D + c0,
-                                     a.dk_s + slot * D + c0);
-      tmem_row_epilogue<D / 2, OutT>(tl + C::kColDV + c0, 1.f, kvalid, single,
-                                     static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * D + c0,
-                                     a.dv_s + slot * D + c0);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
-      ++W;
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    tmem_dealloc(tmem, 512);
-  }
-}
-
-struct TmCfgQ {
-  static constexpr int D = 64;
-  static constexpr int kBlock = 128 * D * 2;
-  static constexpr int kStages = 4;               // (K, V) ring
-  static constexpr int kQ = 0;
-  static constexpr int kDO = kBlock;
-  static constexpr int kK = 2 * kBlock;           // stage s: K at kK + s*2*kBlock, V after it
-  static constexpr int kBar = kK + kStages * 2 * kBlock;
-  // qd_full, qd_empty, qt_full, kv_full[S], kv_empty[S], s_full[2], p_full[2], acc_full, acc_empty, drain
-  static constexpr int kNumBars = 3 + 2 * kStages + 4 + 3;
-  static constexpr int kMisc = kBar + kNumBars * 8;
-  static constexpr int kSmem = kMisc + 16 + 1024;
-  // TMEM: S[2] 0/64, dP[2] 128/192, dQ 256, Q 320, dOut 352
-  static constexpr uint32_t kColS = 0, kColDP = 128, kColDQ = 256, kColQ = 320, kColDO = 352;
-};
-
-template <typename OutT>
-__global__ void __launch_bounds__(kThreads, 1)
-    sm103_dq_tm_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
-                       const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tdo,
-                       const BwdArgs a) {
-  using C = TmCfgQ;
-  constexpr int D = C::D;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kBar);
-  uint64_t* qd_full = bars;
-  uint64_t* qd_empty = bars + 1;
-  uint64_t* qt_full = bars + 2;
-  uint64_t* kv_full = bars + 3;
-  uint64_t* kv_empty = kv_full + C::kStages;
-  uint64_t* s_full = kv_empty + C::kStages;
-  uint64_t* p_full = s_full + 2;
-  uint64_t* acc_full = p_full + 2;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* drain = acc_empty + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    mbar_init(qd_full, 1);
-    mbar_init(qd_empty, kMathWarps);
-    mbar_init(qt_full, kMathWarps);
-    for (int s = 0; s < C::kStages; ++s) {
-      mbar_init(kv_full + s, 1);
-      mbar_init(kv_empty + s, 1);
-    }
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(s_full + s, 1);
-      mbar_init(p_full + s, kMathWarps);
-    }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kMathWarps);
-    mbar_init(drain, 1);
-    *abort_flag = 0;
-    fence_mbar_init();
-    prefetch_tmap(&tq);
-    prefetch_tmap(&tk);
-    prefetch_tmap(&tv);
-    prefetch_tmap(&tdo);
-  }
-  if (warp == 1) {
-    tmem_alloc(tmem_slot, 512);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const Geom& g = a.g;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      uint32_t G = 0, W = 0;
-      uint32_t qd_arm = 0, qd_par = 0, kv_arm = 0, kv_par = 0;
-      bool ok = true;
-      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-        int bh, tile, qb;
-        decode_item(g, w, bh, tile, qb);
-        TileBlocks tbk;
-        tile_blocks(g, tile, tbk);
-        if (qb >= tbk.NB) continue;
-        int o[3];
-        block_origin(g, tbk, qb, o);
-        if (!(ok = WAIT(qd_empty, (W & 1) ^ 1))) break;
-        mbar_arrive_expect_tx(qd_full, 2 * C::kBlock);
-        qd_arm = 1;
-        qd_par = W & 1;
-        tma_load_5d(smem + C::kQ, &tq, qd_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
-        tma_load_5d(smem + C::kDO, &tdo, qd_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0],
-                    bh);
-        int jt = 0, jy = 0, jx = 0;
-        for (int j = 0; j < tbk.NB; ++j, ++G) {
-          const uint32_t st = G % C::kStages, n = G / C::kStages;
-          const int c1 = tbk.tb.lo[2] + (jx << g.lx), c2 = tbk.tb.lo[1] + (jy << g.ly), c3 = tbk.tb.lo[0] + (jt << g.lt);
-          if (++jx == tbk.nb[2]) {
-            jx = 0;
-            if (++jy == tbk.nb[1]) {
-              jy = 0;
-              ++jt;
-            }
-          }
-          if (!(ok = WAIT(kv_empty + st, (n & 1) ^ 1))) break;
-          mbar_arrive_expect_tx(kv_full + st, 2 * C::kBlock);
-          kv_arm |= 1u << st;
-          kv_par = (kv_par & ~(1u << st)) | ((n & 1) << st);
-          uint8_t* sk = smem + C::kK + st * 2 * C::kBlock;
-          tma_load_5d(sk, &tk, kv_full + st, 0, c1, c2, c3, bh);
-          tma_load_5d(sk + C::kBlock, &tv, kv_full + st, 0, c1, c2, c3, bh);
-        }
-        ++W;
-      }
-      if (!ok) {
-        if (qd_arm) mbar_wait<set_status_bwd>(qd_full, qd_par, abort_flag, false);
-        for (int s = 0; s < C::kStages; ++s)
-          if (kv_arm & (1u << s)) mbar_wait<set_status_bwd>(kv_full + s, (kv_par >> s) & 1, abort_flag, false);
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idS = idesc_bf16(128, 64, 0);
-      constexpr uint32_t idA = idesc_bf16(128, D, 1);
-      const uint32_t sK = smem_u32(smem + C::kK);
-      uint32_t G = 0, H = 0, W = 0;
-      bool ok = true;
-      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-        int bh, tile, qb;
-        decode_item(g, w, bh, tile, qb);
-        TileBlocks tbk;
-        tile_blocks(g, tile, tbk);
-        if (qb >= tbk.NB) continue;
-        if (!(ok = WAIT(qt_full, W & 1))) break;  // Q, dOut in TMEM
-        tc_fence_after();
-        const uint32_t G0 = G, H0 = H;
-        // dQ += dS K_h for half block h (A = dS from TMEM, B = K half MN-major)
-        auto issue_dq = [&](uint32_t h) -> bool {
-          const uint32_t b = h & 1;
-          const uint32_t gbox = G0 + ((h - H0) >> 1), half = (h - H0) & 1, st = gbox % C::kStages;
-          if (!WAIT(p_full + b, (h >> 1) & 1)) return false;
-          if (h == H0 && !WAIT(acc_empty, (W & 1) ^ 1)) return false;
-          tc_fence_after();
-          const uint32_t sk = sK + st * 2 * C::kBlock + half * 8192;
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            umma_bf16_ts(tmem + C::kColDQ, tmem + C::kColS + b * 64 + pair_col(ks), sw128_desc(sk + ks * 2048, 16384, 1024),
-                         idA, (h != H0 || ks > 0) ? 1u : 0u);
-          if (half == 1) umma_commit(kv_empty + st);
-          return true;
-        };
-        bool pending = false;
-        for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
-          const uint32_t st = G % C::kStages;
-          if (!(ok = WAIT(kv_full + st, (G / C::kStages) & 1))) break;
-          for (int half = 0; half < 2; ++half, ++H) {
-            const uint32_t b = H & 1;
-            const uint32_t sk = sK + st * 2 * C::kBlock + half * 8192;
-            const uint32_t sv = sk + C::kBlock;
-#pragma unroll
-            for (int ks = 0; ks < D / 16; ++ks) {
-              umma_bf16_ts(tmem + C::kColS + b * 64, tmem + C::kColQ + ks * 8, sw128_desc(sk + kmaj_off(ks), 16, 1024),
-                           idS, ks > 0);
-              umma_bf16_ts(tmem + C::kColDP + b * 64, tmem + C::kColDO + ks * 8,
-                           sw128_desc(sv + kmaj_off(ks), 16, 1024), idS, ks > 0);
-            }
-            umma_commit(s_full + b);
-            if (pending && !(ok = issue_dq(H - 1))) break;
-            pending = true;
-          }
-        }
-        if (!ok) break;
-        if (pending && !(ok = issue_dq(H - 1))) break;
-        umma_commit(acc_full);
-        ++W;
-      }
-      umma_commit(drain);
-      mbar_wait<set_status_bwd>(drain, 0, abort_flag, false);
-    }
-  } else {
-    // ------------------------------------------------------------ elementwise + epilogue (row = query)
-    const int quad = warp & 3;
-    const int ch = (warp - 2) >> 2;
-    const int row = quad * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
-    const float sl2 = g.scale_log2;
-    uint32_t G = 0, H = 0, W = 0;
-    bool ok = true;
-    for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-      int bh, tile, qb;
-      decode_item(g, w, bh, tile, qb);
-      TileBlocks tbk;
-      tile_blocks(g, tile, tbk);
-      if (qb >= tbk.NB) continue;
-      const int64_t qslot = tile_slot0(g, bh, tile) + qb * 128 + row;
-      const float nL = a.lse2c[qslot];  // -lse' (-inf for padding rows)
-      const float nD = a.dd[qslot];     // -D
-      // Q and dOut of the query block: shared memory -> TMEM (A operands of S, dP)
-      if (!(ok = WAIT(qd_full, W & 1))) break;
-      {
-        uint32_t r16[16];
-        ld_swizzled_row<4>(smem_u32(smem + C::kQ), row, 4 * ch, r16);
-        tmem_st16(tl + C::kColQ + 16 * ch, r16);
-        ld_swizzled_row<4>(smem_u32(smem + C::kDO), row, 4 * ch, r16);
-        tmem_st16(tl + C::kColDO + 16 * ch, r16);
-        tmem_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(qd_empty);
-          mbar_arrive(qt_full);
-        }
-      }
-      int jt = 0, jy = 0, jx = 0;
-      for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
-        const int ko[3] = {jt << g.lt, jy << g.ly, jx << g.lx};
-        if (++jx == tbk.nb[2]) {
-          jx = 0;
-          if (++jy == tbk.nb[1]) {
-            jy = 0;
-            ++jt;
-          }
-        }
-        const bool full = block_full(g, tbk, ko);
-        uint32_t kmask[2] = {~0u, ~0u};
-        if (!full) {
-#pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2) {
-            int kl[3];
-            block_row(g, ko, h2 * 64 + ch * 32 + lane, kl);
-            kmask[h2] = __ballot_sync(0xffffffffu, inside(tbk, kl));
-          }
-        }
-        for (int half = 0; half < 2; ++half, ++H) {
-          const uint32_t b = H & 1;
-          if (!(ok = WAIT(s_full + b, (H >> 1) & 1))) break;
-          tc_fence_after();
-          const uint32_t tS = tl + C::kColS + b * 64 + ch * 32;
-          uint32_t sv[32], dv[32];
-          tmem_ld32(tS, sv);
-          tmem_ld32(tl + C::kColDP + b * 64 + ch * 32, dv);
-          tmem_wait_ld(sv);
-          tmem_wait_ld(dv);
-          uint32_t pk[16];
-          if (full)
-            dq_half<false>(sv, dv, 0u, sl2, nL, nD, pk);
-          else
-            dq_half<true>(sv, dv, kmask[half], sl2, nL, nD, pk);
-          tmem_st16(tS, pk);  // dS in place: this thread's own columns
-          tmem_wait_st();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(p_full + b);
-        }
-      }
-      if (!ok) break;
-      if (!(ok = WAIT(acc_full, W & 1))) break;
-      tc_fence_after();
-      int qo[3], ql[3];
-      block_origin(g, tbk, qb, qo);
-      block_row(g, qo, row, ql);
-      const bool qvalid = inside(tbk, ql);
-      const int p[3] = {tbk.tb.lo[0] + ql[0], tbk.tb.lo[1] + ql[1], tbk.tb.lo[2] + ql[2]};
-      const int64_t tok = qvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
-      const bool single = qvalid && single_cover(g, p);
-      const int c0 = ch * (D / 2);
-      tmem_row_epilogue<D / 2, OutT>(tl + C::kColDQ + c0, g.scale, qvalid, single,
-                                     static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * D + c0,
-                                     a.dq_s + qslot * D + c0);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
-      ++W;
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    tmem_dealloc(tmem, 512);
-  }
-}
-
 template <int D, typename OutT>
 cudaError_t run_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v,
                     const __nv_bfloat16* dout, const float* lse2c, const float* dd, void* dq, void* dk, void* dv,
@@ -1310,22 +635,6 @@ cudaError_t run_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
       !make_tmap_5d(&mdo, dout, D, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt))
     return cudaErrorInvalidValue;
   const int grid = (int)(a.items < num_sms() ? a.items : num_sms());
-  if constexpr (D == 64) {
-    auto k1 = sm103_dkdv_tm_kernel<OutT>;
-    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, TmCfgKv::kSmem);
-    if (e != cudaSuccess) return e;
-    prof_begin(kKBwdDkdv, st);
-    k1<<<grid, kThreads, TmCfgKv::kSmem, st>>>(mq, mk, mv, mdo, a);
-    prof_end(kKBwdDkdv, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    auto k2 = sm103_dq_tm_kernel<OutT>;
-    e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, TmCfgQ::kSmem);
-    if (e != cudaSuccess) return e;
-    prof_begin(kKBwdDq, st);
-    k2<<<grid, kThreads, TmCfgQ::kSmem, st>>>(mq, mk, mv, mdo, a);
-    prof_end(kKBwdDq, st);
-    return cudaGetLastError();
-  }
   auto k1 = sm103_dkdv_kernel<D, OutT>;
   cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, KvCfg<D>::kSmem);
   if (e != cudaSuccess) return e;
@@ -1345,14 +654,14 @@ cudaError_t run_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
 }  // namespace
 
 cudaError_t launch_sm103_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v,
-                             const __nv_bfloat16* dout, const float* lse2c, const float* dd, void* dq, void* dk,
+                             const __nv_bfloat16* dout, const float* lse2c, const float* dd, const void* ext,
+                             void* dq, void* dk,
                              void* dv, int out_dtype, float* dq_s, float* dk_s, float* dv_s, uint32_t,
                              cudaStream_t st) {
   const bool bf = out_dtype == GATTN_BF16;
   using bf16 = __nv_bfloat16;
   if (g.d == 64)
-    return bf ? run_bwd<64, bf16>(g, q, k, v, dout, lse2c, dd, dq, dk, dv, dq_s, dk_s, dv_s, st)
-              : run_bwd<64, float>(g, q, k, v, dout, lse2c, dd, dq, dk, dv, dq_s, dk_s, dv_s, st);
+    return launch_sm103_bwd64(g, q, k, v, dout, lse2c, dd, ext, dq, dk, dv, out_dtype, dq_s, dk_s, dv_s, st);
   if (g.d == 128)
     return bf ? run_bwd<128, bf16>(g, q, k, v, dout, lse2c, dd, dq, dk, dv, dq_s, dk_s, dv_s, st)
               : run_bwd<128, float>(g, q, k, v, dout, lse2c, dd, dq, dk, dv, dq_s, dk_s, dv_s, st);

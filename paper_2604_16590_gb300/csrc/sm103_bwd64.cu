@@ -1,0 +1,687 @@
+// sm103_bwd64.cu -- BF16 tensor-core backward of STORM-GPA tile attention for
+// head size d = 64 on GB300 (sm_103a).  Two deterministic kernels (no atomics):
+//
+//   dK/dV kernel, one work item per (batch*head, tile, 128-key box kb):
+//     for every 128-query box i of the tile:
+//       S'^T  = K Q_i^T  + 1 x_i^T,  x = -lse' / (scale log2 e)      M = N = 128, 4 + 1 K-steps
+//       dP'^T = V dO_i^T + 1 y_i^T,  y = -D                          M = N = 128, 4 + 1 K-steps
+//       P'^T = exp2(scale log2e S'^T),  dS^T = P'^T * dP'^T          math warps, BF16 pairs -> TMEM
+//       dV += P'^T dO_i,  dK += dS^T Q_i                             A from TMEM, FP32 in TMEM
+//   dQ kernel, one work item per (batch*head, tile, 128-query box qb):
+//     for every 128-key box j of the tile:
+//       S = Q K_j^T, dP = dO V_j^T (Q, dO copied once per item into TMEM),
+//       dS = P' (dP - D) (keys outside the tile masked), dQ += dS K_j.
+//
+// Why this shape on this part: a tcgen05 MMA step with N = 64 costs about 54
+// SM cycles against 64 for N = 128, so the score products run over whole
+// 128-token boxes; only the gradient products (N = d = 64) keep the narrow
+// shape.  The packed P'/dS operand has its own TMEM columns, so the next box's
+// score products start as soon as the math warps have read the current scores
+// (s_empty), while the gradient products of the current box wait only for
+// the packed values (p_full).  In the dK/dV kernel the per-query statistics
+// (-lse' and -D are per column there) enter through one extra K = 16 MMA step
+// against a constant A operand of ones, instead of a broadcast load per
+// element: the prep pass writes each slot's values as sums of three BF16 terms
+// (FP32-accurate), K-columns 0..2 for -lse' / (scale log2 e) and 3..5 for -D.
+//
+// The merge weight of the Hann-weighted overlap average (arXiv 2604.16590,
+// Sec. III-C) enters through lse' = lse - log2(w_t / sum w), which makes P'
+// the probabilities of the per-tile gradient dO_t = (w_t / sum w) dOut, and
+// D = dOut . O_t.  Rows covered by one tile are written straight to
+// dQ/dK/dV; multiply-covered rows go to FP32 per-tile slots that the merge
+// kernel sums in fixed tile order.
+//
+// Warp roles: warp 0 TMA producer, warp 1 TMEM allocator + single-thread MMA
+// issuer, warps 2..9 elementwise math + epilogue: one TMEM lane = one box
+// row, two warps per lane quadrant, each taking 64 of the row's 128 columns.
+#include "sm103_bwd_common.cuh"
+
+GATTN_DEFINE_STATUS(sm103_bwd64)
+
+namespace gattn {
+namespace {
+using namespace sm103;
+
+__device__ void set_status_bwd64(uint32_t c) { set_status(c); }
+#define WAIT(bar, par) mbar_wait<set_status_bwd64>((bar), (par), abort_flag)
+
+constexpr int kD = 64;
+constexpr int kBox = 128 * kD * 2;  // one 128-token box of one operand, BF16, 16 KB
+
+// =============================================================== dK / dV
+struct Kv64 {
+  static constexpr int kStages = 4;  // (Q, dOut, statistics rows) ring
+  static constexpr int kK = 0;
+  static constexpr int kV = kBox;
+  static constexpr int kQ = 2 * kBox;  // stage s: Q at kQ + s*2*kBox, dOut after it
+  static constexpr int kOnes = kQ + kStages * 2 * kBox;  // A of the extension step: ones in K 0..2, then 3..5
+  static constexpr int kExt = kOnes + 2 * 2048;            // stage s: 128 statistics rows (16 B) at kExt + s*2048
+  static constexpr int kZero = kExt + kStages * 2048;      // K-columns 8..15 of every extension operand
+  static constexpr int kBar = kZero + 2048;
+  // kv_full, kv_empty, qd_full[S], qd_empty[S], s_full, s_empty, p_full, p_empty, acc_full, acc_empty, drain
+  static constexpr int kNumBars = 2 + 2 * kStages + 7;
+  static constexpr int kMisc = kBar + kNumBars * 8;
+  static constexpr int kSmem = kMisc + 16 + 1024;
+  // TMEM: S'^T 0, dP'^T 128, P'^T (packed) 256, dS^T (packed) 320, dV 384, dK 448
+  static constexpr uint32_t kColST = 0, kColDP = 128, kColP = 256, kColDS = 320, kColDV = 384, kColDK = 448;
+};
+
+// P'^T and dS^T of 32 columns of this thread's key row (S'^T, dP'^T already
+// carry the statistics), packed as BF16 pairs.
+__device__ __forceinline__ void kv_chunk(const uint32_t (&s)[32], const uint32_t (&dp)[32], uint64_t s2,
+                                         uint32_t (&pp)[16], uint32_t (&pd)[16]) {
+#pragma unroll
+  for (int c = 0; c < 32; c += 2) {
+    float a0, a1;
+    f2unpack(fmul2(u2pack(s[c], s[c + 1]), s2), a0, a1);
+    const float p0 = ex2(a0), p1 = ex2(a1);
+    float e0, e1;
+    f2unpack(fmul2(f2pack(p0, p1), u2pack(dp[c], dp[c + 1])), e0, e1);
+    pp[c >> 1] = pack_bf16(p0, p1);
+    pd[c >> 1] = pack_bf16(e0, e1);
+  }
+}
+
+template <typename OutT>
+__global__ void __launch_bounds__(kThreads, 1)
+    dkdv64_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
+                  const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tdo,
+                  const BwdArgs a) {
+  using C = Kv64;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kBar);
+  uint64_t* kv_full = bars;
+  uint64_t* kv_empty = bars + 1;
+  uint64_t* qd_full = bars + 2;
+  uint64_t* qd_empty = qd_full + C::kStages;
+  uint64_t* s_full = qd_empty + C::kStages;
+  uint64_t* s_empty = s_full + 1;
+  uint64_t* p_full = s_empty + 1;
+  uint64_t* p_empty = p_full + 1;
+  uint64_t* acc_full = p_empty + 1;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain = acc_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // constant operands of the extension step: 128 rows of ones, and the zero
+  // core matrices (K 8..15) that every extension descriptor points at
+  for (int r = threadIdx.x; r < 128 * 3; r += kThreads) {
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r < 128) v = make_uint4(0x3F803F80u, 0x00003F80u, 0u, 0u);            // (1, 1, 1, 0, 0, 0, 0, 0)
+    else if (r < 256) v = make_uint4(0u, 0x3F800000u, 0x3F803F80u, 0u);       // (0, 0, 0, 1, 1, 1, 0, 0)
+    uint8_t* dst = r < 256 ? smem + C::kOnes + r * 16 : smem + C::kZero + (r - 256) * 16;
+    *reinterpret_cast<uint4*>(dst) = v;
+  }
+  fence_proxy_async_smem();
+  if (threadIdx.x == 0) {
+    mbar_init(kv_full, 1);
+    mbar_init(kv_empty, 1);
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(qd_full + s, 1);
+      mbar_init(qd_empty + s, 1);
+    }
+    mbar_init(s_full, 1);
+    mbar_init(s_empty, kMathWarps);
+    mbar_init(p_full, kMathWarps);
+    mbar_init(p_empty, 1);
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kMathWarps);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    prefetch_tmap(&tq);
+    prefetch_tmap(&tk);
+    prefetch_tmap(&tv);
+    prefetch_tmap(&tdo);
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const Geom& g = a.g;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t G = 0, W = 0;
+      uint32_t kv_arm = 0, kv_par = 0, qd_arm = 0, qd_par = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
+        int bh, tile, kb;
+        decode_item(g, w, bh, tile, kb);
+        TileBlocks tbk;
+        tile_blocks(g, tile, tbk);
+        if (kb >= tbk.NB) continue;
+        int o[3];
+        block_origin(g, tbk, kb, o);
+        if (!(ok = WAIT(kv_empty, (W & 1) ^ 1))) break;
+        mbar_arrive_expect_tx(kv_full, 2 * kBox);
+        kv_arm = 1;
+        kv_par = W & 1;
+        tma_load_5d(smem + C::kK, &tk, kv_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
+        tma_load_5d(smem + C::kV, &tv, kv_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
+        const int64_t slot0 = tile_slot0(g, bh, tile);
+        int jt = 0, jy = 0, jx = 0;
+        for (int i = 0; i < tbk.NB; ++i, ++G) {
+          const uint32_t st = G % C::kStages, n = G / C::kStages;
+          const int c1 = tbk.tb.lo[2] + (jx << g.lx), c2 = tbk.tb.lo[1] + (jy << g.ly), c3 = tbk.tb.lo[0] + (jt << g.lt);
+          if (++jx == tbk.nb[2]) {
+            jx = 0;
+            if (++jy == tbk.nb[1]) {
+              jy = 0;
+              ++jt;
+            }
+          }
+          if (!(ok = WAIT(qd_empty + st, (n & 1) ^ 1))) break;
+          mbar_arrive_expect_tx(qd_full + st, 2 * kBox + 2048);
+          qd_arm |= 1u << st;
+          qd_par = (qd_par & ~(1u << st)) | ((n & 1) << st);
+          uint8_t* sq = smem + C::kQ + st * 2 * kBox;
+          tma_load_5d(sq, &tq, qd_full + st, 0, c1, c2, c3, bh);
+          tma_load_5d(sq + kBox, &tdo, qd_full + st, 0, c1, c2, c3, bh);
+          bulk_load(smem + C::kExt + st * 2048, a.ext + slot0 + i * 128, 2048, qd_full + st);
+        }
+        ++W;
+      }
+      if (!ok) {
+        if (kv_arm) mbar_wait<set_status_bwd64>(kv_full, kv_par, abort_flag, false);
+        for (int s = 0; s < C::kStages; ++s)
+          if (qd_arm & (1u << s)) mbar_wait<set_status_bwd64>(qd_full + s, (qd_par >> s) & 1, abort_flag, false);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idS = idesc_bf16(128, 128, 0);
+      constexpr uint32_t idA = idesc_bf16(128, kD, 1);
+      const uint32_t sK = smem_u32(smem + C::kK), sV = smem_u32(smem + C::kV), sQ = smem_u32(smem + C::kQ);
+      const uint32_t sOnes = smem_u32(smem + C::kOnes), sExt = smem_u32(smem + C::kExt);
+      const uint64_t dOnesS = noswz_desc(sOnes, C::kZero - C::kOnes, 128);
+      const uint64_t dOnesD = noswz_desc(sOnes + 2048, C::kZero - C::kOnes - 2048, 128);
+      uint32_t G = 0, W = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
+        int bh, tile, kb;
+        decode_item(g, w, bh, tile, kb);
+        TileBlocks tbk;
+        tile_blocks(g, tile, tbk);
+        if (kb >= tbk.NB) continue;
+        if (!(ok = WAIT(kv_full, W & 1))) break;
+        const uint32_t G0 = G;
+        // dV += P'^T dOut_i, dK += dS^T Q_i for box counter gb (A operands from TMEM)
+        auto issue_acc = [&](uint32_t gb) -> bool {
+          const uint32_t st = gb % C::kStages;
+          if (!WAIT(p_full, gb & 1)) return false;
+          if (gb == G0 && !WAIT(acc_empty, (W & 1) ^ 1)) return false;
+          tc_fence_after();
+          const uint32_t sq = sQ + st * 2 * kBox, sdo = sq + kBox;
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks) {
+            const uint32_t acc = (gb != G0 || ks > 0) ? 1u : 0u;
+            umma_bf16_ts(tmem + C::kColDV, tmem + C::kColP + ks * 8, sw128_desc(sdo + ks * 2048, 16384, 1024), idA,
+                         acc);
+            umma_bf16_ts(tmem + C::kColDK, tmem + C::kColDS + ks * 8, sw128_desc(sq + ks * 2048, 16384, 1024), idA,
+                         acc);
+          }
+          umma_commit(p_empty);
+          umma_commit(qd_empty + st);
+          return true;
+        };
+        for (int i = 0; i < tbk.NB && ok; ++i, ++G) {
+          const uint32_t st = G % C::kStages;
+          if (!(ok = WAIT(qd_full + st, (G / C::kStages) & 1))) break;
+          if (G > 0 && !(ok = WAIT(s_empty, (G - 1) & 1))) break;  // scores of box G-1 read
+          tc_fence_after();
+          const uint32_t sq = sQ + st * 2 * kBox, sdo = sq + kBox;
+          const uint32_t ext = sExt + st * 2048, ext_lbo = C::kZero - C::kExt - st * 2048;
+#pragma unroll
+          for (int ks = 0; ks < kD / 16; ++ks)
+            umma_bf16(tmem + C::kColST, sw128_desc(sK + ks * 32, 16, 1024), sw128_desc(sq + ks * 32, 16, 1024), idS,
+                      ks > 0);
+          umma_bf16(tmem + C::kColST, dOnesS, noswz_desc(ext, ext_lbo, 128), idS, 1u);
+#pragma unroll
+          for (int ks = 0; ks < kD / 16; ++ks)
+            umma_bf16(tmem + C::kColDP, sw128_desc(sV + ks * 32, 16, 1024), sw128_desc(sdo + ks * 32, 16, 1024), idS,
+                      ks > 0);
+          umma_bf16(tmem + C::kColDP, dOnesD, noswz_desc(ext, ext_lbo, 128), idS, 1u);
+          umma_commit(s_full);
+          if (i == tbk.NB - 1) umma_commit(kv_empty);  // K, V of this item no longer read
+          if (i > 0 && !(ok = issue_acc(G - 1))) break;
+        }
+        if (!ok) break;
+        if (!(ok = issue_acc(G - 1))) break;
+        umma_commit(acc_full);
+        ++W;
+      }
+      umma_commit(drain);
+      mbar_wait<set_status_bwd64>(drain, 0, abort_flag, false);
+    }
+  } else {
+    // ------------------------------------------------------------ elementwise + epilogue (row = key)
+    const int quad = warp & 3;
+    const int ch = (warp - 2) >> 2;
+    const int row = quad * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+    const uint64_t s2 = f2pack(g.scale_log2, g.scale_log2);
+    uint32_t G = 0, W = 0;
+    bool ok = true;
+    for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
+      int bh, tile, kb;
+      decode_item(g, w, bh, tile, kb);
+      TileBlocks tbk;
+      tile_blocks(g, tile, tbk);
+      if (kb >= tbk.NB) continue;
+      for (int i = 0; i < tbk.NB && ok; ++i, ++G) {
+        if (!(ok = WAIT(s_full, G & 1))) break;
+        tc_fence_after();
+        const uint32_t tS = tl + C::kColST + ch * 64, tD = tl + C::kColDP + ch * 64;
+        uint32_t sv[32], dv[32], pp0[16], pd0[16], pp1[16], pd1[16];
+        tmem_ld32(tS, sv);
+        tmem_ld32(tD, dv);
+        tmem_wait_ld(sv);
+        tmem_wait_ld(dv);
+        kv_chunk(sv, dv, s2, pp0, pd0);
+        tmem_ld32(tS + 32, sv);
+        tmem_ld32(tD + 32, dv);
+        tmem_wait_ld(sv);
+        tmem_wait_ld(dv);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(s_empty);  // the next box's score products may overwrite S'^T, dP'^T
+        kv_chunk(sv, dv, s2, pp1, pd1);
+        if (G > 0 && !(ok = WAIT(p_empty, (G - 1) & 1))) break;  // gradient products of box G-1 done
+        tc_fence_after();
+        tmem_st16(tl + C::kColP + ch * 32, pp0);
+        tmem_st16(tl + C::kColP + ch * 32 + 16, pp1);
+        tmem_st16(tl + C::kColDS + ch * 32, pd0);
+        tmem_st16(tl + C::kColDS + ch * 32 + 16, pd1);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(p_full);
+      }
+      if (!ok) break;
+      // ---- epilogue: this thread's key row of dK, dV (its half of the columns)
+      if (!(ok = WAIT(acc_full, W & 1))) break;
+      tc_fence_after();
+      int ko[3], kl[3];
+      block_origin(g, tbk, kb, ko);
+      block_row(g, ko, row, kl);
+      const bool kvalid = inside(tbk, kl);
+      const int p[3] = {tbk.tb.lo[0] + kl[0], tbk.tb.lo[1] + kl[1], tbk.tb.lo[2] + kl[2]};
+      const int64_t tok = kvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
+      const bool single = kvalid && single_cover(g, p);
+      const int64_t slot = tile_slot0(g, bh, tile) + kb * 128 + row;
+      const int c0 = ch * (kD / 2);
+      tmem_row_epilogue<kD / 2, OutT>(tl + C::kColDK + c0, g.scale, kvalid, single,
+                                      static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * kD + c0,
+                                      a.dk_s + slot * kD + c0);
+      tmem_row_epilogue<kD / 2, OutT>(tl + C::kColDV + c0, 1.f, kvalid, single,
+                                      static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * kD + c0,
+                                      a.dv_s + slot * kD + c0);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+      ++W;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// =============================================================== dQ
+struct Q64 {
+  static constexpr int kStages = 4;  // (K, V) ring
+  static constexpr int kQ = 0;
+  static constexpr int kDO = kBox;
+  static constexpr int kK = 2 * kBox;  // stage s: K at kK + s*2*kBox, V after it
+  static constexpr int kBar = kK + kStages * 2 * kBox;
+  // qd_full, qd_empty, qt_full, kv_full[S], kv_empty[S], s_full, s_empty, p_full, p_empty, acc_full, acc_empty, drain
+  static constexpr int kNumBars = 3 + 2 * kStages + 7;
+  static constexpr int kMisc = kBar + kNumBars * 8;
+  static constexpr int kSmem = kMisc + 16 + 1024;
+  // TMEM: S 0, dP 128, dS (packed) 256, dQ 320, Q (packed) 384, dOut (packed) 416
+  static constexpr uint32_t kColS = 0, kColDP = 128, kColDS = 256, kColDQ = 320, kColQ = 384, kColDO = 416;
+};
+
+template <typename OutT>
+__global__ void __launch_bounds__(kThreads, 1)
+    dq64_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
+                const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tdo, const BwdArgs a) {
+  using C = Q64;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kBar);
+  uint64_t* qd_full = bars;
+  uint64_t* qd_empty = bars + 1;
+  uint64_t* qt_full = bars + 2;
+  uint64_t* kv_full = bars + 3;
+  uint64_t* kv_empty = kv_full + C::kStages;
+  uint64_t* s_full = kv_empty + C::kStages;
+  uint64_t* s_empty = s_full + 1;
+  uint64_t* p_full = s_empty + 1;
+  uint64_t* p_empty = p_full + 1;
+  uint64_t* acc_full = p_empty + 1;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain = acc_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(qd_full, 1);
+    mbar_init(qd_empty, kMathWarps);
+    mbar_init(qt_full, kMathWarps);
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(kv_full + s, 1);
+      mbar_init(kv_empty + s, 1);
+    }
+    mbar_init(s_full, 1);
+    mbar_init(s_empty, kMathWarps);
+    mbar_init(p_full, kMathWarps);
+    mbar_init(p_empty, 1);
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kMathWarps);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    prefetch_tmap(&tq);
+    prefetch_tmap(&tk);
+    prefetch_tmap(&tv);
+    prefetch_tmap(&tdo);
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const Geom& g = a.g;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t G = 0, W = 0;
+      uint32_t qd_arm = 0, qd_par = 0, kv_arm = 0, kv_par = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
+        int bh, tile, qb;
+        decode_item(g, w, bh, tile, qb);
+        TileBlocks tbk;
+        tile_blocks(g, tile, tbk);
+        if (qb >= tbk.NB) continue;
+        int o[3];
+        block_origin(g, tbk, qb, o);
+        if (!(ok = WAIT(qd_empty, (W & 1) ^ 1))) break;
+        mbar_arrive_expect_tx(qd_full, 2 * kBox);
+        qd_arm = 1;
+        qd_par = W & 1;
+        tma_load_5d(smem + C::kQ, &tq, qd_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
+        tma_load_5d(smem + C::kDO, &tdo, qd_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0],
+                    bh);
+        int jt = 0, jy = 0, jx = 0;
+        for (int j = 0; j < tbk.NB; ++j, ++G) {
+          const uint32_t st = G % C::kStages, n = G / C::kStages;
+          const int c1 = tbk.tb.lo[2] + (jx << g.lx), c2 = tbk.tb.lo[1] + (jy << g.ly), c3 = tbk.tb.lo[0] + (jt << g.lt);
+          if (++jx == tbk.nb[2]) {
+            jx = 0;
+            if (++jy == tbk.nb[1]) {
+              jy = 0;
+              ++jt;
+            }
+          }
+          if (!(ok = WAIT(kv_empty + st, (n & 1) ^ 1))) break;
+          mbar_arrive_expect_tx(kv_full + st, 2 * kBox);
+          kv_arm |= 1u << st;
+          kv_par = (kv_par & ~(1u << st)) | ((n & 1) << st);
+          uint8_t* sk = smem + C::kK + st * 2 * kBox;
+          tma_load_5d(sk, &tk, kv_full + st, 0, c1, c2, c3, bh);
+          tma_load_5d(sk + kBox, &tv, kv_full + st, 0, c1, c2, c3, bh);
+        }
+        ++W;
+      }
+      if (!ok) {
+        if (qd_arm) mbar_wait<set_status_bwd64>(qd_full, qd_par, abort_flag, false);
+        for (int s = 0; s < C::kStages; ++s)
+          if (kv_arm & (1u << s)) mbar_wait<set_status_bwd64>(kv_full + s, (kv_par >> s) & 1, abort_flag, false);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idS = idesc_bf16(128, 128, 0);
+      constexpr uint32_t idA = idesc_bf16(128, kD, 1);
+      const uint32_t sK = smem_u32(smem + C::kK);
+      uint32_t G = 0, W = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
+        int bh, tile, qb;
+        decode_item(g, w, bh, tile, qb);
+        TileBlocks tbk;
+        tile_blocks(g, tile, tbk);
+        if (qb >= tbk.NB) continue;
+        if (!(ok = WAIT(qt_full, W & 1))) break;  // Q, dOut in TMEM
+        tc_fence_after();
+        const uint32_t G0 = G;
+        // dQ += dS K_gb (A = dS from TMEM, B = the key box MN-major)
+        auto issue_dq = [&](uint32_t gb) -> bool {
+          const uint32_t st = gb % C::kStages;
+          if (!WAIT(p_full, gb & 1)) return false;
+          if (gb == G0 && !WAIT(acc_empty, (W & 1) ^ 1)) return false;
+          tc_fence_after();
+          const uint32_t sk = sK + st * 2 * kBox;
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks)
+            umma_bf16_ts(tmem + C::kColDQ, tmem + C::kColDS + ks * 8, sw128_desc(sk + ks * 2048, 16384, 1024), idA,
+                         (gb != G0 || ks > 0) ? 1u : 0u);
+          umma_commit(p_empty);
+          umma_commit(kv_empty + st);
+          return true;
+        };
+        for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
+          const uint32_t st = G % C::kStages;
+          if (!(ok = WAIT(kv_full + st, (G / C::kStages) & 1))) break;
+          if (G > 0 && !(ok = WAIT(s_empty, (G - 1) & 1))) break;  // scores of box G-1 read
+          tc_fence_after();
+          const uint32_t sk = sK + st * 2 * kBox, sv = sk + kBox;
+#pragma unroll
+          for (int ks = 0; ks < kD / 16; ++ks) {
+            umma_bf16_ts(tmem + C::kColS, tmem + C::kColQ + ks * 8, sw128_desc(sk + ks * 32, 16, 1024), idS, ks > 0);
+            umma_bf16_ts(tmem + C::kColDP, tmem + C::kColDO + ks * 8, sw128_desc(sv + ks * 32, 16, 1024), idS,
+                         ks > 0);
+          }
+          umma_commit(s_full);
+          if (j > 0 && !(ok = issue_dq(G - 1))) break;
+        }
+        if (!ok) break;
+        if (!(ok = issue_dq(G - 1))) break;
+        umma_commit(acc_full);
+        ++W;
+      }
+      umma_commit(drain);
+      mbar_wait<set_status_bwd64>(drain, 0, abort_flag, false);
+    }
+  } else {
+    // ------------------------------------------------------------ elementwise + epilogue (row = query)
+    const int quad = warp & 3;
+    const int ch = (warp - 2) >> 2;
+    const int row = quad * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+    const float sl2 = g.scale_log2;
+    uint32_t G = 0, W = 0;
+    bool ok = true;
+    for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
+      int bh, tile, qb;
+      decode_item(g, w, bh, tile, qb);
+      TileBlocks tbk;
+      tile_blocks(g, tile, tbk);
+      if (qb >= tbk.NB) continue;
+      const int64_t qslot = tile_slot0(g, bh, tile) + qb * 128 + row;
+      const float nL = a.lse2c[qslot];  // -lse' (-inf for padding rows)
+      const float nD = a.dd[qslot];     // -D
+      // Q and dOut of the query box: shared memory -> TMEM (A operands of S, dP).
+      // The previous item's products are complete (its acc_full was waited on).
+      if (!(ok = WAIT(qd_full, W & 1))) break;
+      {
+        uint32_t r16[16];
+        ld_swizzled_row<4>(smem_u32(smem + C::kQ), row, 4 * ch, r16);
+        tmem_st16(tl + C::kColQ + 16 * ch, r16);
+        ld_swizzled_row<4>(smem_u32(smem + C::kDO), row, 4 * ch, r16);
+        tmem_st16(tl + C::kColDO + 16 * ch, r16);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(qd_empty);
+          mbar_arrive(qt_full);
+        }
+      }
+      int jt = 0, jy = 0, jx = 0;
+      for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
+        const int ko[3] = {jt << g.lt, jy << g.ly, jx << g.lx};
+        if (++jx == tbk.nb[2]) {
+          jx = 0;
+          if (++jy == tbk.nb[1]) {
+            jy = 0;
+            ++jt;
+          }
+        }
+        const bool full = block_full(g, tbk, ko);
+        uint32_t kmask[2] = {~0u, ~0u};
+        if (!full) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            int kl[3];
+            block_row(g, ko, ch * 64 + c * 32 + lane, kl);
+            kmask[c] = __ballot_sync(0xffffffffu, inside(tbk, kl));
+          }
+        }
+        if (!(ok = WAIT(s_full, G & 1))) break;
+        tc_fence_after();
+        const uint32_t tS = tl + C::kColS + ch * 64, tD = tl + C::kColDP + ch * 64;
+        uint32_t sv[32], dv[32], pk0[16], pk1[16];
+        tmem_ld32(tS, sv);
+        tmem_ld32(tD, dv);
+        tmem_wait_ld(sv);
+        tmem_wait_ld(dv);
+        if (full)
+          dq_half<false>(sv, dv, 0u, sl2, nL, nD, pk0);
+        else
+          dq_half<true>(sv, dv, kmask[0], sl2, nL, nD, pk0);
+        tmem_ld32(tS + 32, sv);
+        tmem_ld32(tD + 32, dv);
+        tmem_wait_ld(sv);
+        tmem_wait_ld(dv);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(s_empty);  // the next box's score products may overwrite S, dP
+        if (full)
+          dq_half<false>(sv, dv, 0u, sl2, nL, nD, pk1);
+        else
+          dq_half<true>(sv, dv, kmask[1], sl2, nL, nD, pk1);
+        if (G > 0 && !(ok = WAIT(p_empty, (G - 1) & 1))) break;  // dQ products of box G-1 done
+        tc_fence_after();
+        tmem_st16(tl + C::kColDS + ch * 32, pk0);
+        tmem_st16(tl + C::kColDS + ch * 32 + 16, pk1);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(p_full);
+      }
+      if (!ok) break;
+      if (!(ok = WAIT(acc_full, W & 1))) break;
+      tc_fence_after();
+      int qo[3], ql[3];
+      block_origin(g, tbk, qb, qo);
+      block_row(g, qo, row, ql);
+      const bool qvalid = inside(tbk, ql);
+      const int p[3] = {tbk.tb.lo[0] + ql[0], tbk.tb.lo[1] + ql[1], tbk.tb.lo[2] + ql[2]};
+      const int64_t tok = qvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
+      const bool single = qvalid && single_cover(g, p);
+      const int c0 = ch * (kD / 2);
+      tmem_row_epilogue<kD / 2, OutT>(tl + C::kColDQ + c0, g.scale, qvalid, single,
+                                      static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * kD + c0,
+                                      a.dq_s + qslot * kD + c0);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+      ++W;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+template <typename OutT>
+cudaError_t run_bwd64(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v,
+                      const __nv_bfloat16* dout, const float* lse2c, const float* dd, const void* ext, void* dq,
+                      void* dk, void* dv, float* dq_s, float* dk_s, float* dv_s, cudaStream_t st) {
+  if (!ext || reinterpret_cast<uintptr_t>(ext) % 16) return cudaErrorInvalidValue;
+  BwdArgs a;
+  a.g = g;
+  a.lse2c = lse2c;
+  a.dd = dd;
+  a.ext = static_cast<const uint4*>(ext);
+  a.dq = dq;
+  a.dk = dk;
+  a.dv = dv;
+  a.dq_s = dq_s;
+  a.dk_s = dk_s;
+  a.dv_s = dv_s;
+  const int64_t items = (int64_t)g.B * g.nh * g.ntiles * g.nbmax_tot;
+  if (items >= (1LL << 31)) return cudaErrorNotSupported;
+  a.items = (int)items;
+  const int BH = g.B * g.nh;
+  CUtensorMap mq, mk, mv, mdo;
+  if (!make_tmap_5d(&mq, q, kD, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
+      !make_tmap_5d(&mk, k, kD, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
+      !make_tmap_5d(&mv, v, kD, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
+      !make_tmap_5d(&mdo, dout, kD, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt))
+    return cudaErrorInvalidValue;
+  const int grid = (int)(a.items < num_sms() ? a.items : num_sms());
+  auto k1 = dkdv64_kernel<OutT>;
+  cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, Kv64::kSmem);
+  if (e != cudaSuccess) return e;
+  prof_begin(kKBwdDkdv, st);
+  k1<<<grid, kThreads, Kv64::kSmem, st>>>(mq, mk, mv, mdo, a);
+  prof_end(kKBwdDkdv, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  auto k2 = dq64_kernel<OutT>;
+  e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, Q64::kSmem);
+  if (e != cudaSuccess) return e;
+  prof_begin(kKBwdDq, st);
+  k2<<<grid, kThreads, Q64::kSmem, st>>>(mq, mk, mv, mdo, a);
+  prof_end(kKBwdDq, st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sm103_bwd64(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v,
+                               const __nv_bfloat16* dout, const float* lse2c, const float* dd, const void* ext,
+                               void* dq, void* dk, void* dv, int out_dtype, float* dq_s, float* dk_s, float* dv_s,
+                               cudaStream_t st) {
+  if (g.d != kD) return cudaErrorNotSupported;
+  if (out_dtype == GATTN_BF16)
+    return run_bwd64<__nv_bfloat16>(g, q, k, v, dout, lse2c, dd, ext, dq, dk, dv, dq_s, dk_s, dv_s, st);
+  return run_bwd64<float>(g, q, k, v, dout, lse2c, dd, ext, dq, dk, dv, dq_s, dk_s, dv_s, st);
+}
+
+}  // namespace gattn

@@ -189,6 +189,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo, uin
   return d;
 }
 
+// Shared-memory matrix descriptor without swizzle, K-major: core matrices of
+// 8 rows x 16 bytes (rows 16 B apart); lbo = byte distance between the two
+// core matrices of a K = 16 step, sbo = byte distance between 8-row groups.
+__device__ __forceinline__ uint64_t noswz_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05; layout bits 61..63 = 0 (no swizzle)
+  return d;
+}
+
 // 32 lanes x 32 consecutive 32-bit columns: thread i of the warp gets the 32
 // columns of TMEM lane (warp quadrant * 32 + i) starting at `taddr`'s column.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
