@@ -57,10 +57,6 @@ constexpr int kBox = 128 * kD * 2;  // one 128-token box of one operand, BF16, 1
 constexpr int kThreads64 = kThreads + 32;  // + warp 10, the second MMA issuer
 constexpr int kIssuerA = kThreads / 32;    // warp index of the gradient-product issuer
 
-// Descriptor of the operand `bytes` further on: the start address occupies the
-// low 14 bits (16-byte units) and every shared-memory offset used here keeps
-// it below 2^14, so the move is one add.
-__device__ __forceinline__ uint64_t dmove(uint64_t desc, uint32_t bytes) { return desc + (bytes >> 4); }
 
 // =============================================================== dK / dV
 struct Kv64 {

@@ -20,10 +20,16 @@
 // Warp roles (320 threads, one CTA per SM, persistent over work items
 // (batch*head, tile, query block)):
 //   warp 0      TMA producer (Q once per item; K_j, V_j through a ring of stages)
-//   warp 1      TMEM allocator + single-thread tcgen05 MMA issuer
+//   warp 1      TMEM allocator + issuer of the S = Q K^T products
 //   warps 2..9  softmax + epilogue: one query row per TMEM lane, two warps per
 //               lane quadrant splitting each row's keys and output columns
 //               (two math warps per SM sub-partition hide TMEM/MUFU latency)
+//   warp 10     issuer of the P V products
+// Two issuing threads, because a thread's shared-memory accesses (an mbarrier
+// wait included) are held until the tcgen05.mma it issued before them have
+// drained from the tensor pipe: with one issuer every wait between the S and
+// the P V products emptied the pipe; with two, one thread's waits overlap the
+// other's MMAs.  The barriers order every TMEM region and stage they share.
 // TMEM: columns [0,256) two S buffers, [256, 256+d) the P V block product,
 // then 64 columns of P (BF16 pairs) and d/2 columns of Q (BF16 pairs).
 #include <string.h>
@@ -47,8 +53,8 @@ struct FwdCfg {
   static constexpr int kV = kK + kStages * kBlock;
   static constexpr int kBar = kV + kStages * kBlock;
   // q_full, q_empty, qt_full, k_full[S], k_empty[S], v_full[S], v_empty[S], s_full[2], s_empty[2],
-  // p_full, pv_done[2], o_empty, drain, never (test hook: nothing arrives on it)
-  static constexpr int kNumBars = 3 + 4 * kStages + 4 + 6;
+  // p_full, pv_done[2], o_empty, drain[2], never (test hook: nothing arrives on it)
+  static constexpr int kNumBars = 3 + 4 * kStages + 4 + 7;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kRed = kMisc + 16;           // float [3 slots][2 half][128 rows]
   static constexpr int kSmem = kRed + 3072 + 1024;  // + slack for 1024-byte alignment
@@ -147,7 +153,8 @@ __device__ void set_status_fwd(uint32_t c) { set_status(c); }
 // its 32 query rows, warp half `ch` owning keys [64 ch, 64 ch + 64) of every
 // block (one 64-key chunk of P) and output columns [ch D/2, (ch+1) D/2).
 constexpr int kMathWarps = 8;
-constexpr int kThreads = 64 + 32 * kMathWarps;
+constexpr int kThreads = 64 + 32 * kMathWarps + 32;
+constexpr int kIssuerPV = 2 + kMathWarps;  // warp index of the P V issuer
 
 // Online-softmax state of one query row, as held by one of its two threads.
 // P = exp2(s S log2e - m) is formed against a reference max m that only moves
@@ -334,8 +341,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* p_full = s_empty + 2;
   uint64_t* pv_done = p_full + 1;  // [2], one per P buffer
   uint64_t* o_empty = pv_done + 2;
-  uint64_t* drain = o_empty + 1;
-  uint64_t* never = drain + 1;
+  uint64_t* drain = o_empty + 1;  // [2]: one per issuing thread
+  uint64_t* never = drain + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
 
@@ -359,6 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(pv_done + 1, 1);
     mbar_init(o_empty, kMathWarps);
     mbar_init(drain, 1);
+    mbar_init(drain + 1, 1);
     mbar_init(never, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -437,30 +445,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
+    // ------------------------------------------------------------ issuer of S = Q K^T
     if (lane == 0) {
       constexpr uint32_t idS = idesc_bf16(128, 128, 0);
-      constexpr uint32_t idO = idesc_bf16(128, D, 1);
-      const uint32_t sK = smem_u32(smem + C::kK), sV = smem_u32(smem + C::kV);
+      const uint64_t dK0 = sw128_desc(smem_u32(smem + C::kK), 16, 1024);
       uint32_t G = 0, W = 0;
       bool ok = true;
       if (a.flags & GATTN_FLAG_TEST_STALL)  // failure-detection hook: a wait that cannot complete
         ok = mbar_wait<set_status_fwd>(never, 0, abort_flag, true, 20000000ull);
-      // P V of global block Gp (first block of its item: fresh accumulator)
-      auto issue_pv = [&](uint32_t Gp, bool first) -> bool {
-        const uint32_t st = Gp % C::kStages, pb = Gp % C::kPBufs;
-        if (!mbar_wait<set_status_fwd>(v_full + st, (Gp / C::kStages) & 1, abort_flag)) return false;
-        if (!mbar_wait<set_status_fwd>(p_full, Gp & 1, abort_flag)) return false;
-        if (first && !mbar_wait<set_status_fwd>(o_empty, (W & 1) ^ 1, abort_flag)) return false;
-        tc_fence_after();
-#pragma unroll
-        for (int ks = 0; ks < 8; ++ks)
-          umma_bf16_ts(tmem + C::kColO, tmem + C::kColP + pb * 64 + ks * 8,
-                       sw128_desc(sV + st * C::kBlock + ks * 2048, 16384, 1024), idO, (!first || ks > 0) ? 1u : 0u);
-        umma_commit(pv_done + pb);
-        umma_commit(v_empty + st);
-        return true;
-      };
       for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
         Item it;
         if (!resolve<RAGGED>(a, &tq, &tk, &tv, w, it)) continue;
@@ -468,30 +460,57 @@ __global__ void __launch_bounds__(kThreads, 1)
         tile_blocks(*it.g, it.tile, tbk);
         if (it.blk >= tbk.NB) continue;
         if (!(ok = mbar_wait<set_status_fwd>(qt_full, W & 1, abort_flag))) break;  // Q in TMEM
-        tc_fence_after();
-        const uint32_t G0 = G;
         for (int j = 0; j < tbk.NB; ++j, ++G) {
           const uint32_t st = G % C::kStages, sb = G & 1;
           if (!(ok = mbar_wait<set_status_fwd>(k_full + st, (G / C::kStages) & 1, abort_flag))) break;
           if (!(ok = mbar_wait<set_status_fwd>(s_empty + sb, ((G >> 1) & 1) ^ 1, abort_flag))) break;
           tc_fence_after();
+          const uint64_t dk = dmove(dK0, st * C::kBlock);
 #pragma unroll
-          for (int ks = 0; ks < D / 16; ++ks) {
-            const uint32_t off = (ks >> 2) * 16384 + (ks & 3) * 32;
-            umma_bf16_ts(tmem + sb * 128, tmem + C::kColQ + ks * 8, sw128_desc(sK + st * C::kBlock + off, 16, 1024),
+          for (int ks = 0; ks < D / 16; ++ks)
+            umma_bf16_ts(tmem + sb * 128, tmem + C::kColQ + ks * 8, dmove(dk, (ks >> 2) * 16384 + (ks & 3) * 32),
                          idS, ks > 0);
-          }
           umma_commit(s_full + sb);
           umma_commit(k_empty + st);
-          if (j > 0 && !(ok = issue_pv(G - 1, G - 1 == G0))) break;
         }
-        if (!ok) break;
-        if (!(ok = issue_pv(G - 1, G - 1 == G0))) break;
         ++W;
       }
       // all issued MMAs complete before TMEM is released
       umma_commit(drain);
       mbar_wait<set_status_fwd>(drain, 0, abort_flag, false);
+    }
+  } else if (warp == kIssuerPV) {
+    // ------------------------------------------------------------ issuer of O += P V
+    if (lane == 0) {
+      constexpr uint32_t idO = idesc_bf16(128, D, 1);
+      const uint64_t dV0 = sw128_desc(smem_u32(smem + C::kV), 16384, 1024);  // MN-major (K = keys)
+      uint32_t G = 0, W = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+        Item it;
+        if (!resolve<RAGGED>(a, &tq, &tk, &tv, w, it)) continue;
+        TileBlocks tbk;
+        tile_blocks(*it.g, it.tile, tbk);
+        if (it.blk >= tbk.NB) continue;
+        for (int j = 0; j < tbk.NB; ++j, ++G) {
+          const uint32_t st = G % C::kStages, pb = G % C::kPBufs;
+          if (!(ok = mbar_wait<set_status_fwd>(v_full + st, (G / C::kStages) & 1, abort_flag))) break;
+          if (!(ok = mbar_wait<set_status_fwd>(p_full, G & 1, abort_flag))) break;
+          if (j == 0 && !(ok = mbar_wait<set_status_fwd>(o_empty, (W & 1) ^ 1, abort_flag))) break;
+          tc_fence_after();
+          const uint64_t dv = dmove(dV0, st * C::kBlock);
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks)
+            umma_bf16_ts(tmem + C::kColO, tmem + C::kColP + pb * 64 + ks * 8, dmove(dv, ks * 2048), idO,
+                         (j > 0 || ks > 0) ? 1u : 0u);
+          umma_commit(pv_done + pb);
+          umma_commit(v_empty + st);
+        }
+        if (!ok) break;
+        ++W;
+      }
+      umma_commit(drain + 1);
+      mbar_wait<set_status_fwd>(drain + 1, 0, abort_flag, false);
     }
   } else {
     // ------------------------------------------------------------ softmax + epilogue

@@ -201,6 +201,11 @@ __device__ __forceinline__ uint64_t noswz_desc(uint32_t saddr, uint32_t lbo, uin
   return d;
 }
 
+// Descriptor of the operand `bytes` further on: the start address occupies the
+// low 14 bits (16-byte units); every shared-memory offset in these kernels
+// keeps it below 2^14, so the move is one add.
+__device__ __forceinline__ uint64_t dmove(uint64_t desc, uint32_t bytes) { return desc + (bytes >> 4); }
+
 // 32 lanes x 32 consecutive 32-bit columns: thread i of the warp gets the 32
 // columns of TMEM lane (warp quadrant * 32 + i) starting at `taddr`'s column.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
