@@ -32,9 +32,11 @@
 // kernel sums in fixed tile order.
 //
 // Warp roles: warp 0 TMA producer, warp 1 TMEM allocator + issuer of the
-// score products, warp 10 issuer of the gradient products, warps 2..9
-// elementwise math + epilogue: one TMEM lane = one box row, two warps per lane
-// quadrant, each taking 64 of the row's 128 columns.  Two issuing threads,
+// score products, warp 2 issuer of the gradient products, warps 3..18
+// elementwise math + epilogue: one TMEM lane = one box row, four warps per
+// lane quadrant, each taking 32 of the row's 128 columns (a warp reads its
+// scores with one load per operand and releases them at once; four warps per
+// SM sub-partition hide the TMEM and MUFU latencies).  Two issuing threads,
 // because a thread's shared-memory accesses (an mbarrier wait included) are
 // held until the tcgen05.mma it issued before them have drained from the
 // tensor pipe: with one issuer every wait between the two product groups
@@ -54,8 +56,32 @@ __device__ void set_status_bwd64(uint32_t c) { set_status(c); }
 
 constexpr int kD = 64;
 constexpr int kBox = 128 * kD * 2;  // one 128-token box of one operand, BF16, 16 KB
-constexpr int kThreads64 = kThreads + 32;  // + warp 10, the second MMA issuer
-constexpr int kIssuerA = kThreads / 32;    // warp index of the gradient-product issuer
+constexpr int kMath64 = 16;                 // math warps: 4 per TMEM lane quadrant
+constexpr int kMath0 = 3;                   // first math warp
+constexpr int kIssuerA = 2;                 // warp index of the gradient-product issuer
+constexpr int kThreads64 = 32 * (kMath0 + kMath64);
+
+// Epilogue of 16 FP32 TMEM columns of this thread's row, scaled by `mul`: to
+// `out` (OutT) if the row is covered by one tile, else to the FP32 slot `scr`,
+// nothing if the row lies outside the tile.  Every lane executes the TMEM load.
+template <typename OutT>
+__device__ __forceinline__ void row_epilogue16(uint32_t taddr, float mul, bool valid, bool single, OutT* out,
+                                               float* scr) {
+  uint32_t r[16];
+  tmem_ld16(taddr, r);
+  tmem_wait_ld(r);
+  if (valid) {
+#pragma unroll
+    for (int e = 0; e < 16; e += 4) {
+      const float4 v = make_float4(__uint_as_float(r[e]) * mul, __uint_as_float(r[e + 1]) * mul,
+                                   __uint_as_float(r[e + 2]) * mul, __uint_as_float(r[e + 3]) * mul);
+      if (single)
+        store4<OutT>(out + e, v);
+      else
+        store4<float>(scr + e, v);
+    }
+  }
+}
 
 
 // =============================================================== dK / dV
@@ -142,11 +168,11 @@ __global__ void __launch_bounds__(kThreads64, 1)
       mbar_init(qd_empty + s, 1);
     }
     mbar_init(s_full, 1);
-    mbar_init(s_empty, kMathWarps);
-    mbar_init(p_full, kMathWarps);
+    mbar_init(s_empty, kMath64);
+    mbar_init(p_full, kMath64);
     mbar_init(p_empty, 1);
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kMathWarps);
+    mbar_init(acc_empty, kMath64);
     mbar_init(drain, 1);
     mbar_init(drain + 1, 1);
     *abort_flag = 0;
@@ -296,7 +322,7 @@ __global__ void __launch_bounds__(kThreads64, 1)
   } else {
     // ------------------------------------------------------------ elementwise + epilogue (row = key)
     const int quad = warp & 3;
-    const int ch = (warp - 2) >> 2;
+    const int c4 = (warp - kMath0) >> 2;  // query columns [32 c4, 32 c4 + 32)
     const int row = quad * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     const uint64_t s2 = f2pack(g.scale_log2, g.scale_log2);
@@ -311,34 +337,26 @@ __global__ void __launch_bounds__(kThreads64, 1)
       for (int i = 0; i < tbk.NB && ok; ++i, ++G) {
         if (!(ok = WAIT(s_full, G & 1))) break;
         tc_fence_after();
-        const uint32_t tS = tl + C::kColST + ch * 64, tD = tl + C::kColDP + ch * 64;
-        uint32_t sv[32], dv[32], pp0[16], pd0[16], pp1[16], pd1[16];
-        tmem_ld32(tS, sv);
-        tmem_ld32(tD, dv);
-        tmem_wait_ld(sv);
-        tmem_wait_ld(dv);
-        kv_chunk(sv, dv, s2, pp0, pd0);
-        tmem_ld32(tS + 32, sv);
-        tmem_ld32(tD + 32, dv);
+        uint32_t sv[32], dv[32], pp[16], pd[16];
+        tmem_ld32(tl + C::kColST + c4 * 32, sv);
+        tmem_ld32(tl + C::kColDP + c4 * 32, dv);
         tmem_wait_ld(sv);
         tmem_wait_ld(dv);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(s_empty);  // the next box's score products may overwrite S'^T, dP'^T
-        kv_chunk(sv, dv, s2, pp1, pd1);
+        kv_chunk(sv, dv, s2, pp, pd);
         if (G > 0 && !(ok = WAIT(p_empty, (G - 1) & 1))) break;  // gradient products of box G-1 done
         tc_fence_after();
-        tmem_st16(tl + C::kColP + ch * 32, pp0);
-        tmem_st16(tl + C::kColP + ch * 32 + 16, pp1);
-        tmem_st16(tl + C::kColDS + ch * 32, pd0);
-        tmem_st16(tl + C::kColDS + ch * 32 + 16, pd1);
+        tmem_st16(tl + C::kColP + c4 * 16, pp);
+        tmem_st16(tl + C::kColDS + c4 * 16, pd);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(p_full);
       }
       if (!ok) break;
-      // ---- epilogue: this thread's key row of dK, dV (its half of the columns)
+      // ---- epilogue: this thread's key row of dK, dV (columns [16 c4, 16 c4 + 16))
       if (!(ok = WAIT(acc_full, W & 1))) break;
       tc_fence_after();
       int ko[3], kl[3];
@@ -349,13 +367,11 @@ __global__ void __launch_bounds__(kThreads64, 1)
       const int64_t tok = kvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
       const bool single = kvalid && single_cover(g, p);
       const int64_t slot = tile_slot0(g, bh, tile) + kb * 128 + row;
-      const int c0 = ch * (kD / 2);
-      tmem_row_epilogue<kD / 2, OutT>(tl + C::kColDK + c0, g.scale, kvalid, single,
-                                      static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * kD + c0,
-                                      a.dk_s + slot * kD + c0);
-      tmem_row_epilogue<kD / 2, OutT>(tl + C::kColDV + c0, 1.f, kvalid, single,
-                                      static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * kD + c0,
-                                      a.dv_s + slot * kD + c0);
+      const int c0 = c4 * 16;
+      row_epilogue16<OutT>(tl + C::kColDK + c0, g.scale, kvalid, single,
+                           static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * kD + c0, a.dk_s + slot * kD + c0);
+      row_epilogue16<OutT>(tl + C::kColDV + c0, 1.f, kvalid, single,
+                           static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * kD + c0, a.dv_s + slot * kD + c0);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
@@ -412,18 +428,18 @@ __global__ void __launch_bounds__(kThreads64, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(qd_full, 1);
-    mbar_init(qd_empty, kMathWarps);
-    mbar_init(qt_full, kMathWarps);
+    mbar_init(qd_empty, kMath64);
+    mbar_init(qt_full, kMath64);
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(kv_full + s, 1);
       mbar_init(kv_empty + s, 1);
     }
     mbar_init(s_full, 1);
-    mbar_init(s_empty, kMathWarps);
-    mbar_init(p_full, kMathWarps);
+    mbar_init(s_empty, kMath64);
+    mbar_init(p_full, kMath64);
     mbar_init(p_empty, 1);
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kMathWarps);
+    mbar_init(acc_empty, kMath64);
     mbar_init(drain, 1);
     mbar_init(drain + 1, 1);
     *abort_flag = 0;
@@ -562,7 +578,7 @@ __global__ void __launch_bounds__(kThreads64, 1)
   } else {
     // ------------------------------------------------------------ elementwise + epilogue (row = query)
     const int quad = warp & 3;
-    const int ch = (warp - 2) >> 2;
+    const int c4 = (warp - kMath0) >> 2;  // key columns [32 c4, 32 c4 + 32)
     const int row = quad * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     const float sl2 = g.scale_log2;
@@ -577,15 +593,16 @@ __global__ void __launch_bounds__(kThreads64, 1)
       const int64_t qslot = tile_slot0(g, bh, tile) + qb * 128 + row;
       const float nL = a.lse2c[qslot];  // -lse' (-inf for padding rows)
       const float nD = a.dd[qslot];     // -D
-      // Q and dOut of the query box: shared memory -> TMEM (A operands of S, dP).
-      // The previous item's products are complete (its acc_full was waited on).
+      // Q and dOut of the query box: shared memory -> TMEM (A operands of S, dP),
+      // elements [16 c4, 16 c4 + 16) of the row.  The previous item's products
+      // are complete (its acc_full was waited on).
       if (!(ok = WAIT(qd_full, W & 1))) break;
       {
-        uint32_t r16[16];
-        ld_swizzled_row<4>(smem_u32(smem + C::kQ), row, 4 * ch, r16);
-        tmem_st16(tl + C::kColQ + 16 * ch, r16);
-        ld_swizzled_row<4>(smem_u32(smem + C::kDO), row, 4 * ch, r16);
-        tmem_st16(tl + C::kColDO + 16 * ch, r16);
+        uint32_t r8[8];
+        ld_swizzled_row<2>(smem_u32(smem + C::kQ), row, 2 * c4, r8);
+        tmem_st8(tl + C::kColQ + 8 * c4, r8);
+        ld_swizzled_row<2>(smem_u32(smem + C::kDO), row, 2 * c4, r8);
+        tmem_st8(tl + C::kColDO + 8 * c4, r8);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
@@ -605,42 +622,29 @@ __global__ void __launch_bounds__(kThreads64, 1)
           }
         }
         const bool full = block_full(g, tbk, ko);
-        uint32_t kmask[2] = {~0u, ~0u};
+        uint32_t kmask = ~0u;
         if (!full) {
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            int kl[3];
-            block_row(g, ko, ch * 64 + c * 32 + lane, kl);
-            kmask[c] = __ballot_sync(0xffffffffu, inside(tbk, kl));
-          }
+          int kl[3];
+          block_row(g, ko, c4 * 32 + lane, kl);
+          kmask = __ballot_sync(0xffffffffu, inside(tbk, kl));
         }
         if (!(ok = WAIT(s_full, G & 1))) break;
         tc_fence_after();
-        const uint32_t tS = tl + C::kColS + ch * 64, tD = tl + C::kColDP + ch * 64;
-        uint32_t sv[32], dv[32], pk0[16], pk1[16];
-        tmem_ld32(tS, sv);
-        tmem_ld32(tD, dv);
-        tmem_wait_ld(sv);
-        tmem_wait_ld(dv);
-        if (full)
-          dq_half<false>(sv, dv, 0u, sl2, nL, nD, pk0);
-        else
-          dq_half<true>(sv, dv, kmask[0], sl2, nL, nD, pk0);
-        tmem_ld32(tS + 32, sv);
-        tmem_ld32(tD + 32, dv);
+        uint32_t sv[32], dv[32], pk[16];
+        tmem_ld32(tl + C::kColS + c4 * 32, sv);
+        tmem_ld32(tl + C::kColDP + c4 * 32, dv);
         tmem_wait_ld(sv);
         tmem_wait_ld(dv);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(s_empty);  // the next box's score products may overwrite S, dP
         if (full)
-          dq_half<false>(sv, dv, 0u, sl2, nL, nD, pk1);
+          dq_half<false>(sv, dv, 0u, sl2, nL, nD, pk);
         else
-          dq_half<true>(sv, dv, kmask[1], sl2, nL, nD, pk1);
+          dq_half<true>(sv, dv, kmask, sl2, nL, nD, pk);
         if (G > 0 && !(ok = WAIT(p_empty, (G - 1) & 1))) break;  // dQ products of box G-1 done
         tc_fence_after();
-        tmem_st16(tl + C::kColDS + ch * 32, pk0);
-        tmem_st16(tl + C::kColDS + ch * 32 + 16, pk1);
+        tmem_st16(tl + C::kColDS + c4 * 16, pk);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
@@ -656,10 +660,9 @@ __global__ void __launch_bounds__(kThreads64, 1)
       const int p[3] = {tbk.tb.lo[0] + ql[0], tbk.tb.lo[1] + ql[1], tbk.tb.lo[2] + ql[2]};
       const int64_t tok = qvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
       const bool single = qvalid && single_cover(g, p);
-      const int c0 = ch * (kD / 2);
-      tmem_row_epilogue<kD / 2, OutT>(tl + C::kColDQ + c0, g.scale, qvalid, single,
-                                      static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * kD + c0,
-                                      a.dq_s + qslot * kD + c0);
+      const int c0 = c4 * 16;
+      row_epilogue16<OutT>(tl + C::kColDQ + c0, g.scale, qvalid, single,
+                           static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * kD + c0, a.dq_s + qslot * kD + c0);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
