@@ -18,7 +18,12 @@
 // shape.  The packed P'/dS operand has its own TMEM columns, so the next box's
 // score products start as soon as the math warps have read the current scores
 // (s_empty), while the gradient products of the current box wait only for
-// the packed values (p_full).  In the dK/dV kernel the per-query statistics
+// the packed values (p_full).  The packed operand and its gradient products
+// come in two halves (K-steps 0..3 and 4..7, written by the warps of column
+// groups 0-1 and 2-3) with a ready and a free barrier each: a half of box G can
+// be written while the other half of box G-1 is still being read, so the
+// barrier round trips between the math warps and the gradient-product issuer
+// overlap tensor work instead of stalling it.  In the dK/dV kernel the per-query statistics
 // (-lse' and -D are per column there) enter through one extra K = 16 MMA step
 // against a constant A operand of ones, instead of a broadcast load per
 // element: the prep pass writes each slot's values as sums of three BF16 terms
@@ -95,8 +100,9 @@ struct Kv64 {
   static constexpr int kOnes = kQ + kStages * 2 * kBox;  // A: ones in K 0..2 at kOnes, ones in K 3..5 at kOnes+4096
   static constexpr int kExt = kOnes + 2 * 4096;            // B, stage s at kExt + s*4096: the 128 statistics rows
   static constexpr int kBar = kExt + kStages * 4096;
-  // kv_full, kv_empty, qd_full[S], qd_empty[S], s_full, s_empty, p_full, p_empty, acc_full, acc_empty, drain[2]
-  static constexpr int kNumBars = 2 + 2 * kStages + 8;
+  // kv_full, kv_empty, qd_full[S], qd_empty[S], s_full, s_empty, p_full[2], p_empty[2], acc_full, acc_empty,
+  // drain[2]
+  static constexpr int kNumBars = 2 + 2 * kStages + 10;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kSmem = kMisc + 16 + 1024;
   // TMEM: S'^T 0, dP'^T 128, P'^T (packed) 256, dS^T (packed) 320, dV 384, dK 448
@@ -134,9 +140,9 @@ __global__ void __launch_bounds__(kThreads64, 1)
   uint64_t* qd_empty = qd_full + C::kStages;
   uint64_t* s_full = qd_empty + C::kStages;
   uint64_t* s_empty = s_full + 1;
-  uint64_t* p_full = s_empty + 1;
-  uint64_t* p_empty = p_full + 1;
-  uint64_t* acc_full = p_empty + 1;
+  uint64_t* p_full = s_empty + 1;   // [2]: one per half of the packed operand
+  uint64_t* p_empty = p_full + 2;   // [2]
+  uint64_t* acc_full = p_empty + 2;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* drain = acc_empty + 1;  // [2]: one per issuing thread
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
@@ -169,8 +175,10 @@ __global__ void __launch_bounds__(kThreads64, 1)
     }
     mbar_init(s_full, 1);
     mbar_init(s_empty, kMath64);
-    mbar_init(p_full, kMath64);
-    mbar_init(p_empty, 1);
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(p_full + h, kMath64 / 2);
+      mbar_init(p_empty + h, 1);
+    }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, kMath64);
     mbar_init(drain, 1);
@@ -299,17 +307,22 @@ __global__ void __launch_bounds__(kThreads64, 1)
           const uint32_t st = G % C::kStages;
           // p_full(G) implies s_full(G): the score products of this stage are
           // complete, so the qd_empty commit below covers every reader
-          if (!(ok = WAIT(p_full, G & 1))) break;
-          if (i == 0 && !(ok = WAIT(acc_empty, (W & 1) ^ 1))) break;
-          tc_fence_after();
           const uint64_t bq = dmove(dQ0, st * 2 * kBox), bdo = dmove(bq, kBox);
 #pragma unroll
-          for (int ks = 0; ks < 8; ++ks) {
-            const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
-            umma_bf16_ts(tmem + C::kColDV, tmem + C::kColP + ks * 8, dmove(bdo, ks * 2048), idA, acc);
-            umma_bf16_ts(tmem + C::kColDK, tmem + C::kColDS + ks * 8, dmove(bq, ks * 2048), idA, acc);
+          for (int h = 0; h < 2; ++h) {
+            if (!(ok = WAIT(p_full + h, G & 1))) break;
+            if (i == 0 && h == 0 && !(ok = WAIT(acc_empty, (W & 1) ^ 1))) break;
+            tc_fence_after();
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const int ks = 4 * h + k4;
+              const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
+              umma_bf16_ts(tmem + C::kColDV, tmem + C::kColP + ks * 8, dmove(bdo, ks * 2048), idA, acc);
+              umma_bf16_ts(tmem + C::kColDK, tmem + C::kColDS + ks * 8, dmove(bq, ks * 2048), idA, acc);
+            }
+            umma_commit(p_empty + h);
           }
-          umma_commit(p_empty);
+          if (!ok) break;
           umma_commit(qd_empty + st);
         }
         if (!ok) break;
@@ -346,14 +359,15 @@ __global__ void __launch_bounds__(kThreads64, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(s_empty);  // the next box's score products may overwrite S'^T, dP'^T
         kv_chunk(sv, dv, s2, pp, pd);
-        if (G > 0 && !(ok = WAIT(p_empty, (G - 1) & 1))) break;  // gradient products of box G-1 done
+        // this half's gradient products of box G-1 are done with the packed operand
+        if (G > 0 && !(ok = WAIT(p_empty + (c4 >> 1), (G - 1) & 1))) break;
         tc_fence_after();
         tmem_st16(tl + C::kColP + c4 * 16, pp);
         tmem_st16(tl + C::kColDS + c4 * 16, pd);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(p_full);
+        if (lane == 0) mbar_arrive(p_full + (c4 >> 1));
       }
       if (!ok) break;
       // ---- epilogue: this thread's key row of dK, dV (columns [16 c4, 16 c4 + 16))
@@ -393,9 +407,9 @@ struct Q64 {
   static constexpr int kDO = kBox;
   static constexpr int kK = 2 * kBox;  // stage s: K at kK + s*2*kBox, V after it
   static constexpr int kBar = kK + kStages * 2 * kBox;
-  // qd_full, qd_empty, qt_full, kv_full[S], kv_empty[S], s_full, s_empty, p_full, p_empty, acc_full, acc_empty,
-  // drain[2]
-  static constexpr int kNumBars = 3 + 2 * kStages + 8;
+  // qd_full, qd_empty, qt_full, kv_full[S], kv_empty[S], s_full, s_empty, p_full[2], p_empty[2], acc_full,
+  // acc_empty, drain[2]
+  static constexpr int kNumBars = 3 + 2 * kStages + 10;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kSmem = kMisc + 16 + 1024;
   // TMEM: S 0, dP 128, dS (packed) 256, dQ 320, Q (packed) 384, dOut (packed) 416
@@ -417,9 +431,9 @@ __global__ void __launch_bounds__(kThreads64, 1)
   uint64_t* kv_empty = kv_full + C::kStages;
   uint64_t* s_full = kv_empty + C::kStages;
   uint64_t* s_empty = s_full + 1;
-  uint64_t* p_full = s_empty + 1;
-  uint64_t* p_empty = p_full + 1;
-  uint64_t* acc_full = p_empty + 1;
+  uint64_t* p_full = s_empty + 1;   // [2]: one per half of dS
+  uint64_t* p_empty = p_full + 2;   // [2]
+  uint64_t* acc_full = p_empty + 2;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* drain = acc_empty + 1;  // [2]: one per issuing thread
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
@@ -436,8 +450,10 @@ __global__ void __launch_bounds__(kThreads64, 1)
     }
     mbar_init(s_full, 1);
     mbar_init(s_empty, kMath64);
-    mbar_init(p_full, kMath64);
-    mbar_init(p_empty, 1);
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(p_full + h, kMath64 / 2);
+      mbar_init(p_empty + h, 1);
+    }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, kMath64);
     mbar_init(drain, 1);
@@ -557,15 +573,21 @@ __global__ void __launch_bounds__(kThreads64, 1)
           const uint32_t st = G % C::kStages;
           // p_full(G) implies s_full(G): the score products of this stage are
           // complete, so the kv_empty commit below covers every reader
-          if (!(ok = WAIT(p_full, G & 1))) break;
-          if (j == 0 && !(ok = WAIT(acc_empty, (W & 1) ^ 1))) break;
-          tc_fence_after();
           const uint64_t bk = dmove(bK0, st * 2 * kBox);
 #pragma unroll
-          for (int ks = 0; ks < 8; ++ks)
-            umma_bf16_ts(tmem + C::kColDQ, tmem + C::kColDS + ks * 8, dmove(bk, ks * 2048), idA,
-                         (j > 0 || ks > 0) ? 1u : 0u);
-          umma_commit(p_empty);
+          for (int h = 0; h < 2; ++h) {
+            if (!(ok = WAIT(p_full + h, G & 1))) break;
+            if (j == 0 && h == 0 && !(ok = WAIT(acc_empty, (W & 1) ^ 1))) break;
+            tc_fence_after();
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const int ks = 4 * h + k4;
+              umma_bf16_ts(tmem + C::kColDQ, tmem + C::kColDS + ks * 8, dmove(bk, ks * 2048), idA,
+                           (j > 0 || ks > 0) ? 1u : 0u);
+            }
+            umma_commit(p_empty + h);
+          }
+          if (!ok) break;
           umma_commit(kv_empty + st);
         }
         if (!ok) break;
@@ -642,13 +664,14 @@ __global__ void __launch_bounds__(kThreads64, 1)
           dq_half<false>(sv, dv, 0u, sl2, nL, nD, pk);
         else
           dq_half<true>(sv, dv, kmask, sl2, nL, nD, pk);
-        if (G > 0 && !(ok = WAIT(p_empty, (G - 1) & 1))) break;  // dQ products of box G-1 done
+        // this half's dQ products of box G-1 are done with dS
+        if (G > 0 && !(ok = WAIT(p_empty + (c4 >> 1), (G - 1) & 1))) break;
         tc_fence_after();
         tmem_st16(tl + C::kColDS + c4 * 16, pk);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(p_full);
+        if (lane == 0) mbar_arrive(p_full + (c4 >> 1));
       }
       if (!ok) break;
       if (!(ok = WAIT(acc_full, W & 1))) break;
