@@ -113,10 +113,33 @@ __device__ __forceinline__ uint4 stat_row(float x, float y) {
 // D = dOut . O_t.  O_t is the output itself for single-cover rows, else the
 // FP32 per-tile value saved by the forward.  Both are stored negated
 // (-lse', -D) so that the backward kernels form exp2(s log2e + (-lse')) and
-// dP + (-D) with single fused/packed instructions.  Slots of a box that fall
-// outside the tile get -lse' = -inf and -D = 0, so the tensor-core backward
-// can run whole boxes without masking queries.  One lane group of d/4 lanes
-// per slot.
+// dP + (-D) with single fused/packed instructions; with `ext` the slot's
+// statistics row (stat_row) is written too.  Slots of a box that fall outside
+// the tile get -lse' = -inf and -D = 0, so the tensor-core backward can run
+// whole boxes without masking queries.  One thread per slot: consecutive slots
+// of a box are consecutive tokens of a row, so a warp's 16-byte loads of its
+// rows cover contiguous memory, and the geometry and merge weights are
+// computed lane-parallel.
+template <typename T>
+__device__ __forceinline__ void load8(const T* p, float (&v)[8]);
+template <>
+__device__ __forceinline__ void load8<float>(const float* p, float (&v)[8]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void load8<__nv_bfloat16>(const __nv_bfloat16* p, float (&v)[8]) {
+  const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+
 template <typename OutT, typename InT>
 __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* __restrict__ out,
                                                             const InT* __restrict__ dout,
@@ -124,65 +147,67 @@ __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* 
                                                             const float* __restrict__ ot,
                                                             float* __restrict__ lse2c, float* __restrict__ dd,
                                                             uint4* __restrict__ ext) {
-  const int F4 = g.d / 4;  // 8, 16 or 32 lanes per slot
   const int64_t S = (int64_t)g.B * g.nh * g.ntiles * g.per_tile;
-  const int64_t total = S * F4;
-  // the grid-stride loop keeps all lanes of a group together (total % F4 == 0)
-  for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx - threadIdx.x % 32 < total;
-       idx += (int64_t)gridDim.x * kThreads) {
-    const bool in = idx < total;
-    const int f = (int)(idx % F4);
-    const int64_t slot = in ? idx / F4 : 0;
-    const int within = (int)(slot % g.per_tile);
+  for (int64_t slot = (int64_t)blockIdx.x * kThreads + threadIdx.x; slot < S; slot += (int64_t)gridDim.x * kThreads) {
     const int64_t ut = slot / g.per_tile;
+    const int within = (int)(slot - ut * g.per_tile);
     const int tile = (int)(ut % g.ntiles);
     const int bh = (int)(ut / g.ntiles);
     TileBox tb;
     tile_box(g, tile, tb);
     int lr[3];
-    const bool valid = in && slot_local(g, tb.e, within >> 7, within & 127, lr) && (within >> 7) < g.nbmax_tot;
-    float part = 0.f;
-    int p[3];
-    int64_t tok = 0;
-    bool single = true;
-    if (valid) {
-      tok = grid_token(g, tb, lr);
-      token_pos(g, tok, p);
-      single = single_cover(g, p);
-      const int64_t off = ((int64_t)bh * g.N + tok) * g.d + 4 * f;
-      float4 a = load4<InT>(dout + off);
-      float4 o = single ? load4<OutT>(out + off) : __ldg(reinterpret_cast<const float4*>(ot + slot * g.d) + f);
-      part = a.x * o.x + a.y * o.y + a.z * o.z + a.w * o.w;
-    }
-    for (int o = 1; o < F4; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (in && !valid && f == 0) {
+    if (!slot_local(g, tb.e, within >> 7, within & 127, lr) || (within >> 7) >= g.nbmax_tot) {
       // padding slot of a box that sticks out of the tile: probability 0
       lse2c[slot] = -INFINITY;
       dd[slot] = 0.f;
       // finite (the extension MMA multiplies it by the other statistic's zero weights)
       if (ext) ext[slot] = stat_row(-1e30f, 0.f);
+      continue;
     }
-    if (valid && f == 0) {
-      float lc = lse2[slot];
-      if (!single) {
-        // c = w_t / sum over covering tiles of w
-        Cover c;
-        cover_of(g, tok, c);
-        int kt[3];
-        kt[0] = tile / (g.n[1] * g.n[2]);
-        kt[1] = (tile / g.n[2]) % g.n[1];
-        kt[2] = tile % g.n[2];
-        float wt = tile_weight(g, p, kt), ws = 0.f;
-        int k[3];
-        for (k[0] = c.k0[0]; k[0] <= c.k1[0]; ++k[0])
-          for (k[1] = c.k0[1]; k[1] <= c.k1[1]; ++k[1])
-            for (k[2] = c.k0[2]; k[2] <= c.k1[2]; ++k[2]) ws += tile_weight(g, p, k);
-        lc -= log2f(wt / ws);
+    const int64_t tok = grid_token(g, tb, lr);
+    int p[3];
+    token_pos(g, tok, p);
+    const bool single = single_cover(g, p);
+    const InT* a = dout + ((int64_t)bh * g.N + tok) * g.d;
+    float part = 0.f;
+    if (single) {
+      const OutT* o = out + ((int64_t)bh * g.N + tok) * g.d;
+      for (int c = 0; c < g.d; c += 8) {
+        float x[8], y[8];
+        load8<InT>(a + c, x);
+        load8<OutT>(o + c, y);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) part = fmaf(x[e], y[e], part);
       }
-      lse2c[slot] = -lc;
-      dd[slot] = -part;
-      if (ext) ext[slot] = stat_row(-lc / g.scale_log2, -part);
+    } else {
+      const float* o = ot + slot * g.d;
+      for (int c = 0; c < g.d; c += 8) {
+        float x[8], y[8];
+        load8<InT>(a + c, x);
+        load8<float>(o + c, y);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) part = fmaf(x[e], y[e], part);
+      }
     }
+    float lc = lse2[slot];
+    if (!single) {
+      // c = w_t / sum over covering tiles of w
+      Cover c;
+      cover_of(g, tok, c);
+      int kt[3];
+      kt[0] = tile / (g.n[1] * g.n[2]);
+      kt[1] = (tile / g.n[2]) % g.n[1];
+      kt[2] = tile % g.n[2];
+      float wt = tile_weight(g, p, kt), ws = 0.f;
+      int k[3];
+      for (k[0] = c.k0[0]; k[0] <= c.k1[0]; ++k[0])
+        for (k[1] = c.k0[1]; k[1] <= c.k1[1]; ++k[1])
+          for (k[2] = c.k0[2]; k[2] <= c.k1[2]; ++k[2]) ws += tile_weight(g, p, k);
+      lc -= log2f(wt / ws);
+    }
+    lse2c[slot] = -lc;
+    dd[slot] = -part;
+    if (ext) ext[slot] = stat_row(-lc / g.scale_log2, -part);
   }
 }
 
@@ -243,7 +268,7 @@ cudaError_t launch_bwd_prep(const Geom& g, const void* out, int out_dtype, const
                             const float* lse2, const float* ot, float* lse2c, float* dd, void* ext_,
                             cudaStream_t st) {
   uint4* ext = static_cast<uint4*>(ext_);
-  const int64_t total = (int64_t)g.B * g.nh * g.ntiles * g.per_tile * (g.d / 4);
+  const int64_t total = (int64_t)g.B * g.nh * g.ntiles * g.per_tile;  // one thread per slot
   const unsigned grid = grid_for(total);
   using bf = __nv_bfloat16;
   if (out_dtype == GATTN_BF16 && in_dtype == GATTN_BF16)
