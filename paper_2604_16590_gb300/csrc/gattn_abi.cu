@@ -327,7 +327,7 @@ int32_t gattn_profile_read(gattn_kernel_stat* out, int32_t max) {
 
 gattn_status gattn_stream_status(gattn_stream_t stream) {
   if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return GATTN_ERR_CUDA;
-  uint32_t words[] = {fetch_status_simt(), fetch_status_merge(), fetch_status_sm103_fwd(), fetch_status_sm103_bwd(),
+  uint32_t words[] = {fetch_status_simt(), fetch_status_merge(), fetch_status_sm103_fwd(), fetch_status_sm103_fwd64(), fetch_status_sm103_bwd(),
                       fetch_status_sm103_bwd64(),
                       fetch_status_serve()};
   for (uint32_t w : words)

@@ -76,6 +76,7 @@ enum : uint32_t { kStatusOk = 0, kStatusTimeout = GATTN_ERR_TIMEOUT, kStatusBoun
 uint32_t fetch_status_simt();
 uint32_t fetch_status_merge();
 uint32_t fetch_status_sm103_fwd();
+uint32_t fetch_status_sm103_fwd64();
 uint32_t fetch_status_sm103_bwd();
 uint32_t fetch_status_sm103_bwd64();
 uint32_t fetch_status_serve();
@@ -101,6 +102,9 @@ cudaError_t launch_merge_bwd(const Geom& g, const float* dq_s, const float* dk_s
 cudaError_t launch_sm103_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k,
                              const __nv_bfloat16* v, void* out, int out_dtype, float* lse2, float* ot,
                              uint32_t flags, cudaStream_t st);
+cudaError_t launch_sm103_fwd64(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k,
+                               const __nv_bfloat16* v, void* out, int out_dtype, float* lse2, float* ot,
+                               uint32_t flags, cudaStream_t st);
 cudaError_t launch_sm103_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k,
                              const __nv_bfloat16* v, const __nv_bfloat16* dout, const float* lse2c,
                              const float* dd, const void* ext, void* dq, void* dk, void* dv, int out_dtype,

@@ -707,9 +707,7 @@ cudaError_t launch_sm103_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, 
 cudaError_t launch_sm103_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v,
                              void* out, int out_dtype, float* lse2, float* ot, uint32_t flags, cudaStream_t st) {
   const bool bf = out_dtype == GATTN_BF16;
-  if (g.d == 64)
-    return bf ? run_fwd<64, __nv_bfloat16>(g, q, k, v, out, lse2, ot, flags, st)
-              : run_fwd<64, float>(g, q, k, v, out, lse2, ot, flags, st);
+  if (g.d == 64) return launch_sm103_fwd64(g, q, k, v, out, out_dtype, lse2, ot, flags, st);
   if (g.d == 128)
     return bf ? run_fwd<128, __nv_bfloat16>(g, q, k, v, out, lse2, ot, flags, st)
               : run_fwd<128, float>(g, q, k, v, out, lse2, ot, flags, st);
