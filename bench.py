@@ -34,7 +34,7 @@ UNIT = "Gtokens/s"
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
 # from the ncu capture summarised in profiles/ (None until captured for the
 # kernel as built now).
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {"bwd_dkdv": 24.59e9}  # profiles/bwd_fwd64_c2_262k_p1.md: 1536.8 MB x 16 units
 
 
 def _extents(G, c, h):

@@ -48,6 +48,8 @@ WORKLOADS = {
     "c1_4k": Workload("c1_4k", 1, 1, 64, (1, 64, 64), (1, 16, 16), (0, 4, 4), 1.0, 20261, "fp32"),
     # 32 frames x 64 x 128 patch grid, Tiles = 16 (paper regime): core 32 x 16 x 32, halo 0/4/8
     "c2_262k_p": Workload("c2_262k_p", 4, 16, 64, (32, 64, 128), (32, 16, 32), (0, 4, 8), 0.5, 20262, "bf16"),
+    # the same geometry with 1 x 4 heads (1/16 of the units, each tensor still larger than L2): profiling case
+    "c2_262k_p1": Workload("c2_262k_p1", 1, 4, 64, (32, 64, 128), (32, 16, 32), (0, 4, 8), 0.5, 20262, "bf16"),
     # same grid, small tiles near the HBM/tensor ridge: core 1 x 16 x 16, halo 0/4/4
     "c2_262k_s": Workload("c2_262k_s", 4, 16, 64, (32, 64, 128), (1, 16, 16), (0, 4, 4), 0.5, 20262, "bf16"),
     # long temporal context: 2048 frames x 32 x 64, d = 128, Tiles = 16 along time, halo 8 frames
