@@ -1,35 +1,37 @@
 // sm103_fwd64.cu -- BF16 tensor-core forward of STORM-GPA tile attention for
-// head size d = 64 on GB300 (sm_103a): two query boxes per work item in
-// ping-pong.
+// head size d = 64 on GB300 (sm_103a): two query boxes per work item, each
+// with its own scores, probabilities and output in tensor memory.
 //
 // Per extended tile t (arXiv 2604.16590, Sec. III-C) and pair of 128-query
 // boxes (A, B) of the tile, the CTA streams the tile's 128-key boxes once for
 // both query boxes (flash-style online softmax, the FlashAttention of
 // Sec. III-D Level 5):
-//   S_x  = Q_x K_j^T                    tcgen05, A = Q_x from TMEM, B = K_j (smem)
+//   S_x  = Q_x K_j^T                    tcgen05, A = Q_x, B = K_j (both shared memory)
 //   m_x  = max(m_x, rowmax(s S_x))      log2 domain, lazily moved (threshold 8)
-//   P_x  = exp2(s S_x log2e - m_x)      BF16 pairs written over S_x's first 64 columns
+//   P_x  = exp2(s S_x log2e - m_x)      BF16 pairs -> TMEM
 //   O_x += P_x V_j                      tcgen05, A = P_x from TMEM, B = V_j (MN-major)
-// While the softmax warps of one box work on its scores, the tensor core runs
-// the other box's products: each box's chain (S, softmax, P V) is serial --
-// S_x(j+1) overwrites the P_x that P V_x(j) reads -- and two chains in flight
-// keep the tensor pipe and the MUFU units busy at the same time.  K and V are
-// loaded once for both boxes.  The epilogue writes O / l for rows covered by
-// one tile straight to the output and parks multiply-covered rows (FP32) for
-// the deterministic Hann merge, and stores the row log-sum-exp.
+// A softmax thread reads its row's 128 scores into registers at once and
+// releases S_x, so S_x(j+1) is computed while the exponentials of box j run;
+// P_x(j) waits only for P V_x(j-1).  With two boxes in flight the tensor pipe
+// and the exp unit are busy at the same time.  The epilogue writes O / l for
+// rows covered by one tile straight to the output and parks multiply-covered
+// rows (FP32) for the deterministic Hann merge, and stores the row log-sum-exp.
 //
-// Warp roles (352 threads, one CTA per SM, persistent over work items
-// (batch*head, tile, box pair)):
+// Warp roles (384 threads = three warpgroups, one CTA per SM, persistent over
+// work items (batch*head, tile, box pair)):
 //   warp 0        TMA producer (Q_A, Q_B once per item; K_j, V_j through a ring)
 //   warp 1        TMEM allocator + issuer of the S products
 //   warp 2        issuer of the P V products (a thread's mbarrier waits stall
 //                 until its own issued MMAs drain, so the two product streams
 //                 come from two threads)
-//   warps 3..6    softmax + epilogue of box A, warps 7..10 of box B: one warp
+//   warp 3        idle (completes the first warpgroup)
+//   warps 4..7    softmax + epilogue of box A, warps 8..11 of box B: one warp
 //                 per TMEM lane quadrant, one thread per query row owning all
 //                 128 key columns (no cross-warp reduction)
-// TMEM (448 columns): S_x at 128 x (P_x over its first 64), O_x at 256 + 64 x,
-// Q_x at 384 + 32 x.
+// Registers: the first warpgroup gives up registers (setmaxnreg) so that the
+// softmax threads hold a whole row of scores: 128 x 72 + 2 x 128 x 216 =
+// 384 x 168, the launch's allocation.
+// TMEM (512 columns): S_x at 128 x, P_x at 256 + 64 x, O_x at 384 + 64 x.
 #include "internal.cuh"
 #include "sm103_common.cuh"
 
@@ -45,8 +47,9 @@ __device__ void set_status_f64(uint32_t c) { set_status(c); }
 constexpr int kD = 64;
 constexpr int kBox = 128 * kD * 2;  // one 128-token box of one operand, BF16, 16 KB
 constexpr int kStages = 4;          // K/V ring depth
-constexpr int kSoft0 = 3;           // first softmax warp
-constexpr int kThreadsF = 32 * (kSoft0 + 8);
+constexpr int kSoft0 = 4;           // first softmax warp
+constexpr int kThreadsF = 384;
+constexpr uint32_t kRegsLow = 72, kRegsHigh = 216;  // 128 x 72 + 256 x 216 = 384 x 168
 constexpr float kRescaleLog2 = 8.f;
 
 struct Cfg {
@@ -55,14 +58,14 @@ struct Cfg {
   static constexpr int kV = kK + kStages * kBox;
   static constexpr int kBar = kV + kStages * kBox;
   // q_full, q_empty, k_full[S], k_empty[S], v_full[S], v_empty[S],
-  // per box: qt_full, s_full, p_full, pv_done, o_empty; drain[2], never
-  static constexpr int kNumBars = 2 + 4 * kStages + 2 * 5 + 3;
+  // per box: s_full, s_empty, p_full, p_empty, o_full, o_empty; drain[2], never
+  static constexpr int kNumBars = 2 + 4 * kStages + 2 * 6 + 3;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kSmem = kMisc + 16 + 1024;
 };
 __device__ __forceinline__ uint32_t col_s(int x) { return 128u * x; }
-__device__ __forceinline__ uint32_t col_o(int x) { return 256u + 64u * x; }
-__device__ __forceinline__ uint32_t col_q(int x) { return 384u + 32u * x; }
+__device__ __forceinline__ uint32_t col_p(int x) { return 256u + 64u * x; }
+__device__ __forceinline__ uint32_t col_o(int x) { return 384u + 64u * x; }
 
 struct Fwd64Args {
   Geom g;
@@ -83,7 +86,7 @@ __device__ __forceinline__ void decode_pair(const Fwd64Args& a, int w, int& bh, 
 
 // running max of 32 scores into 4 partial maxima (3-input max)
 template <bool MASK>
-__device__ __forceinline__ void chunk_max(const uint32_t (&r)[32], uint32_t mbits, float (&mx)[4]) {
+__device__ __forceinline__ void chunk_max(const uint32_t* r, uint32_t mbits, float (&mx)[4]) {
 #pragma unroll
   for (int i = 0; i < 32; i += 2) {
     float x0 = __uint_as_float(r[i]), x1 = __uint_as_float(r[i + 1]);
@@ -97,7 +100,7 @@ __device__ __forceinline__ void chunk_max(const uint32_t (&r)[32], uint32_t mbit
 
 // exp2 of 32 scores -> 16 BF16 pairs, row sum in packed FP32 pairs
 template <bool MASK>
-__device__ __forceinline__ void exp_chunk(const uint32_t (&r)[32], uint32_t mbits, uint64_t s2, uint64_t nm2,
+__device__ __forceinline__ void exp_chunk(const uint32_t* r, uint32_t mbits, uint64_t s2, uint64_t nm2,
                                           uint64_t (&acc)[4], uint32_t (&pk)[16]) {
 #pragma unroll
   for (int i = 0; i < 32; i += 2) {
@@ -113,76 +116,23 @@ __device__ __forceinline__ void exp_chunk(const uint32_t (&r)[32], uint32_t mbit
   }
 }
 
-// One key box of the online softmax for this thread's query row: row max over
-// the 128 scores, lazy move of the reference max (rescaling O in TMEM -- the
-// previous P V of this box is complete, because these scores were computed
-// after it), then exp2 of the scores written as BF16 pairs over the scores'
-// first 64 columns (chunk c of 32 scores -> columns [16c, 16c+16), which only
-// ever covers scores already read).
-template <bool MASK>
-__device__ __forceinline__ void softmax_box(float& m, float& l, uint32_t tS, uint32_t tO, const uint32_t (&km)[4],
-                                            float sl2, bool first) {
-  float mx[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
-  {
-    uint32_t r0[32], r1[32];
+// multiply this thread's 64 O columns by f
+__device__ __forceinline__ void rescale_o(uint32_t tO, float f) {
+  const uint64_t f2 = f2pack(f, f);
+  uint32_t r[32];
 #pragma unroll
-    for (int c = 0; c < 4; c += 2) {
-      tmem_ld32(tS + 32 * c, r0);
-      tmem_ld32(tS + 32 * c + 32, r1);
-      tmem_wait_ld(r0);
-      tmem_wait_ld(r1);
-      chunk_max<MASK>(r0, km[c], mx);
-      chunk_max<MASK>(r1, km[c + 1], mx);
-    }
-  }
-  const float mblk = fmaxf(fmaxf(mx[0], mx[1]), fmaxf(mx[2], mx[3])) * sl2;
-  if (first) {
-    m = mblk;
-  } else {
-    const bool grow = mblk > m + kRescaleLog2;
-    if (__any_sync(0xffffffffu, grow)) {
-      const float f = grow ? ex2(m - mblk) : 1.f;
-      const uint64_t f2 = f2pack(f, f);
-      uint32_t r[32];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        tmem_ld32(tO + 32 * c, r);
-        tmem_wait_ld(r);
-#pragma unroll
-        for (int i = 0; i < 32; i += 2) {
-          float x, y;
-          f2unpack(fmul2(u2pack(r[i], r[i + 1]), f2), x, y);
-          r[i] = __float_as_uint(x);
-          r[i + 1] = __float_as_uint(y);
-        }
-        tmem_st32(tO + 32 * c, r);
-      }
-      tmem_wait_st();
-      l *= f;
-      if (grow) m = mblk;
-    }
-  }
-  const uint64_t s2 = f2pack(sl2, sl2), nm2 = f2pack(-m, -m);
-  uint64_t acc[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) acc[i] = f2pack(0.f, 0.f);
-#pragma unroll 1
-  for (int c = 0; c < 4; ++c) {
-    uint32_t r[32], pk[16];
-    tmem_ld32(tS + 32 * c, r);
-    const uint32_t mb = c == 0 ? km[0] : c == 1 ? km[1] : c == 2 ? km[2] : km[3];
+  for (int c = 0; c < 2; ++c) {
+    tmem_ld32(tO + 32 * c, r);
     tmem_wait_ld(r);
-    exp_chunk<MASK>(r, mb, s2, nm2, acc, pk);
-    tmem_st16(tS + 16 * c, pk);
-  }
-  float lsum = 0.f;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    float x, y;
-    f2unpack(acc[i], x, y);
-    lsum += x + y;
+    for (int i = 0; i < 32; i += 2) {
+      float x, y;
+      f2unpack(fmul2(u2pack(r[i], r[i + 1]), f2), x, y);
+      r[i] = __float_as_uint(x);
+      r[i + 1] = __float_as_uint(y);
+    }
+    tmem_st32(tO + 32 * c, r);
   }
-  l += lsum;
   tmem_wait_st();
 }
 
@@ -200,13 +150,14 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   uint64_t* k_empty = k_full + kStages;
   uint64_t* v_full = k_empty + kStages;
   uint64_t* v_empty = v_full + kStages;
-  uint64_t* boxbar = v_empty + kStages;  // [x * 5 + i]
-  auto qt_full = [&](int x) { return boxbar + 5 * x; };
-  auto s_full = [&](int x) { return boxbar + 5 * x + 1; };
-  auto p_full = [&](int x) { return boxbar + 5 * x + 2; };
-  auto pv_done = [&](int x) { return boxbar + 5 * x + 3; };
-  auto o_empty = [&](int x) { return boxbar + 5 * x + 4; };
-  uint64_t* drain = boxbar + 10;  // [2]
+  uint64_t* boxbar = v_empty + kStages;  // [x * 6 + i]
+  auto s_full = [&](int x) { return boxbar + 6 * x; };
+  auto s_empty = [&](int x) { return boxbar + 6 * x + 1; };
+  auto p_full = [&](int x) { return boxbar + 6 * x + 2; };
+  auto p_empty = [&](int x) { return boxbar + 6 * x + 3; };
+  auto o_full = [&](int x) { return boxbar + 6 * x + 4; };
+  auto o_empty = [&](int x) { return boxbar + 6 * x + 5; };
+  uint64_t* drain = boxbar + 12;  // [2]
   uint64_t* never = drain + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
@@ -214,7 +165,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(q_full, 1);
-    mbar_init(q_empty, 8);
+    mbar_init(q_empty, 1);
     for (int s = 0; s < kStages; ++s) {
       mbar_init(k_full + s, 1);
       mbar_init(k_empty + s, 1);
@@ -222,10 +173,11 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       mbar_init(v_empty + s, 1);
     }
     for (int x = 0; x < 2; ++x) {
-      mbar_init(qt_full(x), 4);
       mbar_init(s_full(x), 1);
+      mbar_init(s_empty(x), 4);
       mbar_init(p_full(x), 4);
-      mbar_init(pv_done(x), 1);
+      mbar_init(p_empty(x), 1);
+      mbar_init(o_full(x), 1);
       mbar_init(o_empty(x), 4);
     }
     mbar_init(drain, 1);
@@ -247,9 +199,10 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   const uint32_t tmem = *tmem_slot;
   const Geom& g = a.g;
 
-  if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
+  if (warp < kSoft0) {
+    setmaxnreg_dec<kRegsLow>();
+    if (warp == 0 && lane == 0) {
+      // ---------------------------------------------------------- TMA producer
       uint32_t G = 0, W = 0;
       uint32_t q_arm = 0, q_par = 0, k_arm = 0, k_par = 0, v_arm = 0, v_par = 0;
       bool ok = true;
@@ -303,13 +256,12 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           if (v_arm & (1u << s)) mbar_wait<set_status_f64>(v_full + s, (v_par >> s) & 1, abort_flag, false);
         }
       }
-    }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------ issuer of S_x = Q_x K^T
-    if (lane == 0) {
+    } else if (warp == 1 && lane == 0) {
+      // ---------------------------------------------------------- issuer of S_x = Q_x K^T
       constexpr uint32_t idS = idesc_bf16(128, 128, 0);
+      const uint64_t dQ0 = sw128_desc(smem_u32(smem + C::kQ), 16, 1024);
       const uint64_t dK0 = sw128_desc(smem_u32(smem + C::kK), 16, 1024);
-      uint32_t G = 0, GX[2] = {0, 0}, WX[2] = {0, 0};
+      uint32_t G = 0, W = 0, GX0 = 0, GX1 = 0;
       bool ok = true;
       if (a.flags & GATTN_FLAG_TEST_STALL)  // failure-detection hook: a wait that cannot complete
         ok = mbar_wait<set_status_f64>(never, 0, abort_flag, true, 20000000ull);
@@ -321,9 +273,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         const int qa = 2 * pair;
         if (qa >= tbk.NB) continue;
         const int nact = qa + 1 < tbk.NB ? 2 : 1;
-#pragma unroll
-        for (int x = 0; x < 2; ++x)  // Q_x in TMEM
-          if (x < nact && ok) ok = WAIT(qt_full(x), WX[x] & 1);
+        if (!(ok = WAIT(q_full, W & 1))) break;  // Q_A, Q_B in shared memory
         for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
           const uint32_t st = G % kStages;
           if (!(ok = WAIT(k_full + st, (G / kStages) & 1))) break;
@@ -331,31 +281,31 @@ __global__ void __launch_bounds__(kThreadsF, 1)
 #pragma unroll
           for (int x = 0; x < 2; ++x) {
             if (x >= nact) break;
-            // S_x overwrites P_x: the previous P V of box x must be complete
-            if (GX[x] > 0 && !(ok = WAIT(pv_done(x), (GX[x] - 1) & 1))) break;
+            uint32_t& gx = x == 0 ? GX0 : GX1;
+            // S_x is free once the softmax threads have read the previous scores
+            if (gx > 0 && !(ok = WAIT(s_empty(x), (gx - 1) & 1))) break;
             tc_fence_after();
+            const uint64_t dq = dmove(dQ0, x * kBox);
 #pragma unroll
             for (int ks = 0; ks < kD / 16; ++ks)
-              umma_bf16_ts(tmem + col_s(x), tmem + col_q(x) + ks * 8, dmove(dk, ks * 32), idS, ks > 0);
+              umma_bf16(tmem + col_s(x), dmove(dq, ks * 32), dmove(dk, ks * 32), idS, ks > 0);
             umma_commit(s_full(x));
-            ++GX[x];
+            ++gx;
           }
           if (!ok) break;
           umma_commit(k_empty + st);
         }
-#pragma unroll
-        for (int x = 0; x < 2; ++x)
-          if (x < nact) ++WX[x];
+        if (!ok) break;
+        umma_commit(q_empty);  // Q_A, Q_B no longer read
+        ++W;
       }
       umma_commit(drain);
       mbar_wait<set_status_f64>(drain, 0, abort_flag, false);
-    }
-  } else if (warp == 2) {
-    // ------------------------------------------------------------ issuer of O_x += P_x V
-    if (lane == 0) {
+    } else if (warp == 2 && lane == 0) {
+      // ---------------------------------------------------------- issuer of O_x += P_x V
       constexpr uint32_t idO = idesc_bf16(128, kD, 1);
       const uint64_t dV0 = sw128_desc(smem_u32(smem + C::kV), 16384, 1024);  // MN-major (K = keys)
-      uint32_t G = 0, GX[2] = {0, 0}, WX[2] = {0, 0};
+      uint32_t G = 0, GX0 = 0, GX1 = 0, WX0 = 0, WX1 = 0;
       bool ok = true;
       for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
         int bh, tile, pair;
@@ -372,35 +322,39 @@ __global__ void __launch_bounds__(kThreadsF, 1)
 #pragma unroll
           for (int x = 0; x < 2; ++x) {
             if (x >= nact) break;
-            if (!(ok = WAIT(p_full(x), GX[x] & 1))) break;
-            if (j == 0 && !(ok = WAIT(o_empty(x), (WX[x] & 1) ^ 1))) break;
+            uint32_t& gx = x == 0 ? GX0 : GX1;
+            const uint32_t wx = x == 0 ? WX0 : WX1;
+            if (!(ok = WAIT(p_full(x), gx & 1))) break;
+            if (j == 0 && !(ok = WAIT(o_empty(x), (wx & 1) ^ 1))) break;
             tc_fence_after();
 #pragma unroll
             for (int ks = 0; ks < 8; ++ks)
-              umma_bf16_ts(tmem + col_o(x), tmem + col_s(x) + ks * 8, dmove(dv, ks * 2048), idO,
+              umma_bf16_ts(tmem + col_o(x), tmem + col_p(x) + ks * 8, dmove(dv, ks * 2048), idO,
                            (j > 0 || ks > 0) ? 1u : 0u);
-            umma_commit(pv_done(x));
-            ++GX[x];
+            umma_commit(p_empty(x));
+            if (j == tbk.NB - 1) umma_commit(o_full(x));
+            ++gx;
           }
           if (!ok) break;
           umma_commit(v_empty + st);
         }
-#pragma unroll
-        for (int x = 0; x < 2; ++x)
-          if (x < nact) ++WX[x];
+        ++WX0;
+        if (nact > 1) ++WX1;
       }
       umma_commit(drain + 1);
       mbar_wait<set_status_f64>(drain + 1, 0, abort_flag, false);
     }
   } else {
+    setmaxnreg_inc<kRegsHigh>();
     // ------------------------------------------------------------ softmax + epilogue of box x
     const int x = (warp - kSoft0) >> 2;
     const int quad = warp & 3;
     const int row = quad * 32 + lane;  // TMEM lane = query row of the box
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
-    const uint32_t tS = tl + col_s(x), tO = tl + col_o(x);
+    const uint32_t tS = tl + col_s(x), tP = tl + col_p(x), tO = tl + col_o(x);
     const float sl2 = g.scale_log2;
-    uint32_t GX = 0, W = 0;
+    const uint64_t s2 = f2pack(sl2, sl2);
+    uint32_t GX = 0, WX = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
       int bh, tile, pair;
@@ -408,25 +362,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       TileBlocks tbk;
       tile_blocks(g, tile, tbk);
       const int qa = 2 * pair;
-      if (qa >= tbk.NB) continue;
-      const bool active = qa + x < tbk.NB;
-      // the query boxes: shared memory (TMA) -> TMEM (A operand of S = Q K^T);
-      // both groups take part in the Q handshake of every item
-      if (!(ok = WAIT(q_full, W & 1))) break;
-      ++W;
-      if (active) {
-        uint32_t qr[32];
-        ld_swizzled_row<8>(smem_u32(smem + C::kQ + x * kBox), row, 0, qr);
-        tmem_st32(tl + col_q(x), qr);
-        tmem_wait_st();
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(q_empty);
-        if (active) mbar_arrive(qt_full(x));
-      }
-      if (!active) continue;
+      if (qa + x >= tbk.NB) continue;
       const int qb = qa + x;
       int qo[3], ql[3];
       block_origin(g, tbk, qb, qo);
@@ -455,18 +391,93 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         }
         if (!(ok = WAIT(s_full(x), GX & 1))) break;
         tc_fence_after();
-        if (full)
-          softmax_box<false>(m, l, tS, tO, km, sl2, j == 0);
-        else
-          softmax_box<true>(m, l, tS, tO, km, sl2, j == 0);
+        // the row's 128 scores into registers, then S_x is released
+        uint32_t s0[32], s1[32], s2r[32], s3[32];
+        tmem_ld32(tS, s0);
+        tmem_ld32(tS + 32, s1);
+        tmem_ld32(tS + 64, s2r);
+        tmem_ld32(tS + 96, s3);
+        tmem_wait_ld(s0);
+        tmem_wait_ld(s1);
+        tmem_wait_ld(s2r);
+        tmem_wait_ld(s3);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(s_empty(x));
+        float mx[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        if (full) {
+          chunk_max<false>(s0, 0u, mx);
+          chunk_max<false>(s1, 0u, mx);
+          chunk_max<false>(s2r, 0u, mx);
+          chunk_max<false>(s3, 0u, mx);
+        } else {
+          chunk_max<true>(s0, km[0], mx);
+          chunk_max<true>(s1, km[1], mx);
+          chunk_max<true>(s2r, km[2], mx);
+          chunk_max<true>(s3, km[3], mx);
+        }
+        const float mblk = fmaxf(fmaxf(mx[0], mx[1]), fmaxf(mx[2], mx[3])) * sl2;
+        float f = 1.f;
+        bool any_grow = false;
+        if (j == 0) {
+          m = mblk;
+        } else {
+          const bool grow = mblk > m + kRescaleLog2;
+          any_grow = __any_sync(0xffffffffu, grow);
+          if (grow) {
+            f = ex2(m - mblk);
+            m = mblk;
+          }
+        }
+        // P_x and O_x are free once the previous P V of this box completed
+        if (GX > 0 && !(ok = WAIT(p_empty(x), (GX - 1) & 1))) break;
+        tc_fence_after();
+        if (any_grow) {
+          rescale_o(tO, f);
+          l *= f;
+        }
+        const uint64_t nm2 = f2pack(-m, -m);
+        uint64_t acc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] = f2pack(0.f, 0.f);
+        uint32_t pk[16];
+        if (full) {
+          exp_chunk<false>(s0, 0u, s2, nm2, acc, pk);
+          tmem_st16(tP, pk);
+          exp_chunk<false>(s1, 0u, s2, nm2, acc, pk);
+          tmem_st16(tP + 16, pk);
+          exp_chunk<false>(s2r, 0u, s2, nm2, acc, pk);
+          tmem_st16(tP + 32, pk);
+          exp_chunk<false>(s3, 0u, s2, nm2, acc, pk);
+          tmem_st16(tP + 48, pk);
+        } else {
+          exp_chunk<true>(s0, km[0], s2, nm2, acc, pk);
+          tmem_st16(tP, pk);
+          exp_chunk<true>(s1, km[1], s2, nm2, acc, pk);
+          tmem_st16(tP + 16, pk);
+          exp_chunk<true>(s2r, km[2], s2, nm2, acc, pk);
+          tmem_st16(tP + 32, pk);
+          exp_chunk<true>(s3, km[3], s2, nm2, acc, pk);
+          tmem_st16(tP + 48, pk);
+        }
+        float lsum = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          float u, v;
+          f2unpack(acc[i], u, v);
+          lsum += u + v;
+        }
+        l += lsum;
+        tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(p_full(x));
       }
       if (!ok) break;
       // ---- epilogue: wait for the last P V, O / l
-      if (!(ok = WAIT(pv_done(x), (GX - 1) & 1))) break;
+      if (!(ok = WAIT(o_full(x), WX & 1))) break;
       tc_fence_after();
+      ++WX;
       const float inv = 1.f / l;
       const int64_t slot = tile_slot0(g, bh, tile) + qb * 128 + row;
       if (qvalid && a.lse2) a.lse2[slot] = m + __log2f(l);
