@@ -27,6 +27,8 @@ FWD_CASES = [
     ("d128_temporal", 1, 2, 128, (16, 8, 8), (8, 8, 8), (2, 0, 0)),
     ("long_tile_ring_wrap", 1, 1, 64, (8, 32, 32), (8, 16, 16), (0, 4, 4)),
     ("d128_s_spec", 1, 1, 128, (1, 48, 40), (1, 16, 16), (0, 4, 4)),
+    # one 1x8x48 tile = three 1x8x16 boxes: the second box of the last query pair is empty
+    ("odd_box_count", 1, 2, 64, (1, 8, 48), (1, 8, 48), (0, 0, 0)),
 ]
 
 
