@@ -126,12 +126,15 @@ struct alignas(128) ReqDesc {
   float* ot;             // per-slot FP32 outputs of multiply-covered rows
   int64_t tok0;          // first global (head, token) row of this request (step kernel)
   int item0;             // first global attention work item of this request
-  int items;             // nh * ntiles * nbmax_tot
+  int items;             // work items of the request (see the ragged launchers)
 };
 // counts[0] = number of requests, counts[1] = total attention work items,
 // counts[2] = total (head, token) rows; read on the device so that one
 // captured launch serves any active set.
 cudaError_t launch_sm103_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, int d, cudaStream_t st);
+// d = 64: the two-box kernel; its work items per (head, tile) are pairs of boxes
+cudaError_t launch_sm103_fwd64_ragged(const ReqDesc* reqs, const int64_t* counts, cudaStream_t st);
+int fwd64_ragged_items(const Geom& g);  // nh * ntiles * ceil(nbmax_tot / 2)
 cudaError_t launch_serve_update(const ReqDesc* reqs, const int64_t* counts, int d, float c, cudaStream_t st);
 
 // ---- small device helpers

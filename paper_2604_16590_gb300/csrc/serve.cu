@@ -310,7 +310,8 @@ gattn_status gattn_serve_step(gattn_server* s, int32_t* n_active, int32_t* n_wai
       d.ot = r->ot;
       d.tok0 = rows;
       d.item0 = (int)item;
-      d.items = r->g.nh * r->g.ntiles * r->g.nbmax_tot;
+      // work items as the ragged forward counts them (box pairs for d = 64, boxes otherwise)
+      d.items = s->cfg.d == 64 ? fwd64_ragged_items(r->g) : r->g.nh * r->g.ntiles * r->g.nbmax_tot;
       item += d.items;
       rows += (int64_t)r->g.nh * r->g.N;
     }

@@ -699,7 +699,7 @@ cudaError_t run_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, cudaStrea
 }  // namespace
 
 cudaError_t launch_sm103_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, int d, cudaStream_t st) {
-  if (d == 64) return run_fwd_ragged<64>(reqs, counts, st);
+  if (d == 64) return launch_sm103_fwd64_ragged(reqs, counts, st);
   if (d == 128) return run_fwd_ragged<128>(reqs, counts, st);
   return cudaErrorNotSupported;
 }

@@ -32,6 +32,13 @@
 // softmax threads hold a whole row of scores: 128 x 72 + 2 x 128 x 216 =
 // 384 x 168, the launch's allocation.
 // TMEM (512 columns): S_x at 128 x, P_x at 256 + 64 x, O_x at 384 + 64 x.
+//
+// Ragged mode (the serving engine): the work items of all active requests in
+// one launch; each item resolves through the request table in device memory
+// (tensor map over the request's state z = Q = K = V, geometry, outputs), and
+// the producer acquires a request's tensor map before its first load from it.
+#include <string.h>
+
 #include "internal.cuh"
 #include "sm103_common.cuh"
 
@@ -73,15 +80,76 @@ struct Fwd64Args {
   float* lse2;
   float* ot;
   int items;  // B*nh * ntiles * box pairs
-  int npairs;
   uint32_t flags;
+  // ragged mode (serving): per-request descriptors and device-side counts
+  const ReqDesc* reqs;
+  const int64_t* counts;
 };
 
-__device__ __forceinline__ void decode_pair(const Fwd64Args& a, int w, int& bh, int& tile, int& pair) {
-  pair = w % a.npairs;
-  const int r = w / a.npairs;
-  tile = r % a.g.ntiles;
-  bh = r / a.g.ntiles;
+// One work item: a (batch*head, tile, pair of query boxes) of a geometry.
+struct Item {
+  const Geom* g;
+  const CUtensorMap* tq;
+  const CUtensorMap* tk;
+  const CUtensorMap* tv;
+  void* out;
+  float* lse2;  // may be null (no backward)
+  float* ot;
+  int bh, tile, pair;
+  int req;  // request index (ragged mode), else -1
+};
+
+__host__ __device__ __forceinline__ int box_pairs(const Geom& g) { return (g.nbmax_tot + 1) / 2; }
+
+// Returns false (after recording GATTN_ERR_DEVICE_BOUNDS) if a ragged work item
+// does not decode to a valid (request, head, tile, pair); every role decodes
+// the same item identically, so all of them skip it together.
+template <bool RAGGED>
+__device__ __forceinline__ bool resolve(const Fwd64Args& a, const CUtensorMap* tq, const CUtensorMap* tk,
+                                        const CUtensorMap* tv, int w, Item& it) {
+  int req = -1;
+  if constexpr (RAGGED) {
+    // requests are sorted by item0: binary search for the last item0 <= w
+    const int nreq = (int)a.counts[0];
+    int lo = 0, hi = nreq - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.reqs[mid].item0 <= w) lo = mid;
+      else hi = mid - 1;
+    }
+    if (nreq < 1 || w < a.reqs[lo].item0 || w >= a.reqs[lo].item0 + a.reqs[lo].items) {
+      set_status(kStatusBounds);
+      return false;
+    }
+    req = lo;
+    const ReqDesc& r = a.reqs[lo];
+    it.g = &r.g;
+    it.tq = it.tk = it.tv = &r.tmap;
+    it.out = r.out;
+    it.lse2 = nullptr;
+    it.ot = r.ot;
+    w -= r.item0;
+  } else {
+    it.g = &a.g;
+    it.tq = tq;
+    it.tk = tk;
+    it.tv = tv;
+    it.out = a.out;
+    it.lse2 = a.lse2;
+    it.ot = a.ot;
+  }
+  const Geom& g = *it.g;
+  const int np = box_pairs(g);
+  it.pair = w % np;
+  const int r = w / np;
+  it.tile = r % g.ntiles;
+  it.bh = r / g.ntiles;
+  it.req = req;
+  if (RAGGED && (it.bh >= g.B * g.nh || g.d != kD)) {
+    set_status(kStatusBounds);
+    return false;
+  }
+  return true;
 }
 
 // running max of 32 scores into 4 partial maxima (3-input max)
@@ -136,7 +204,7 @@ __device__ __forceinline__ void rescale_o(uint32_t tO, float f) {
   tmem_wait_st();
 }
 
-template <typename OutT>
+template <typename OutT, bool RAGGED>
 __global__ void __launch_bounds__(kThreadsF, 1)
     fwd64_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
                  const __grid_constant__ CUtensorMap tv, const Fwd64Args a) {
@@ -185,9 +253,11 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     mbar_init(never, 1);
     *abort_flag = 0;
     fence_mbar_init();
-    prefetch_tmap(&tq);
-    prefetch_tmap(&tk);
-    prefetch_tmap(&tv);
+    if (!RAGGED) {
+      prefetch_tmap(&tq);
+      prefetch_tmap(&tk);
+      prefetch_tmap(&tv);
+    }
   }
   if (warp == 1) {
     tmem_alloc(tmem_slot, 512);
@@ -197,7 +267,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const Geom& g = a.g;
+  const int n_items = RAGGED ? (int)a.counts[1] : a.items;
 
   if (warp < kSoft0) {
     setmaxnreg_dec<kRegsLow>();
@@ -205,15 +275,22 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       // ---------------------------------------------------------- TMA producer
       uint32_t G = 0, W = 0;
       uint32_t q_arm = 0, q_par = 0, k_arm = 0, k_par = 0, v_arm = 0, v_par = 0;
+      int last_req = -1;
       bool ok = true;
-      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-        int bh, tile, pair;
-        decode_pair(a, w, bh, tile, pair);
+      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+        Item it;
+        if (!resolve<RAGGED>(a, &tq, &tk, &tv, w, it)) continue;
+        const Geom& g = *it.g;
+        const int bh = it.bh;
         TileBlocks tbk;
-        tile_blocks(g, tile, tbk);
-        const int qa = 2 * pair;
+        tile_blocks(g, it.tile, tbk);
+        const int qa = 2 * it.pair;
         if (qa >= tbk.NB) continue;
         const int nact = qa + 1 < tbk.NB ? 2 : 1;
+        if (RAGGED && it.req != last_req) {
+          tmap_acquire(it.tq);  // this launch's descriptor table may hold a new map here
+          last_req = it.req;
+        }
         if (!(ok = WAIT(q_empty, (W & 1) ^ 1))) break;
         mbar_arrive_expect_tx(q_full, nact * kBox);
         q_arm = 1;
@@ -221,7 +298,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         for (int x = 0; x < nact; ++x) {
           int o[3];
           block_origin(g, tbk, qa + x, o);
-          tma_load_5d(smem + C::kQ + x * kBox, &tq, q_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
+          tma_load_5d(smem + C::kQ + x * kBox, it.tq, q_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
                       tbk.tb.lo[0] + o[0], bh);
         }
         int jt = 0, jy = 0, jx = 0;
@@ -239,12 +316,12 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           mbar_arrive_expect_tx(k_full + st, kBox);
           k_arm |= 1u << st;
           k_par = (k_par & ~(1u << st)) | ((n & 1) << st);
-          tma_load_5d(smem + C::kK + st * kBox, &tk, k_full + st, 0, c1, c2, c3, bh);
+          tma_load_5d(smem + C::kK + st * kBox, it.tk, k_full + st, 0, c1, c2, c3, bh);
           if (!(ok = WAIT(v_empty + st, (n & 1) ^ 1))) break;
           mbar_arrive_expect_tx(v_full + st, kBox);
           v_arm |= 1u << st;
           v_par = (v_par & ~(1u << st)) | ((n & 1) << st);
-          tma_load_5d(smem + C::kV + st * kBox, &tv, v_full + st, 0, c1, c2, c3, bh);
+          tma_load_5d(smem + C::kV + st * kBox, it.tv, v_full + st, 0, c1, c2, c3, bh);
         }
         ++W;
       }
@@ -265,12 +342,12 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       bool ok = true;
       if (a.flags & GATTN_FLAG_TEST_STALL)  // failure-detection hook: a wait that cannot complete
         ok = mbar_wait<set_status_f64>(never, 0, abort_flag, true, 20000000ull);
-      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-        int bh, tile, pair;
-        decode_pair(a, w, bh, tile, pair);
+      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+        Item it;
+        if (!resolve<RAGGED>(a, &tq, &tk, &tv, w, it)) continue;
         TileBlocks tbk;
-        tile_blocks(g, tile, tbk);
-        const int qa = 2 * pair;
+        tile_blocks(*it.g, it.tile, tbk);
+        const int qa = 2 * it.pair;
         if (qa >= tbk.NB) continue;
         const int nact = qa + 1 < tbk.NB ? 2 : 1;
         if (!(ok = WAIT(q_full, W & 1))) break;  // Q_A, Q_B in shared memory
@@ -307,12 +384,12 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       const uint64_t dV0 = sw128_desc(smem_u32(smem + C::kV), 16384, 1024);  // MN-major (K = keys)
       uint32_t G = 0, GX0 = 0, GX1 = 0, WX0 = 0, WX1 = 0;
       bool ok = true;
-      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-        int bh, tile, pair;
-        decode_pair(a, w, bh, tile, pair);
+      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+        Item it;
+        if (!resolve<RAGGED>(a, &tq, &tk, &tv, w, it)) continue;
         TileBlocks tbk;
-        tile_blocks(g, tile, tbk);
-        const int qa = 2 * pair;
+        tile_blocks(*it.g, it.tile, tbk);
+        const int qa = 2 * it.pair;
         if (qa >= tbk.NB) continue;
         const int nact = qa + 1 < tbk.NB ? 2 : 1;
         for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
@@ -352,16 +429,18 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     const int row = quad * 32 + lane;  // TMEM lane = query row of the box
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     const uint32_t tS = tl + col_s(x), tP = tl + col_p(x), tO = tl + col_o(x);
-    const float sl2 = g.scale_log2;
-    const uint64_t s2 = f2pack(sl2, sl2);
     uint32_t GX = 0, WX = 0;
     bool ok = true;
-    for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-      int bh, tile, pair;
-      decode_pair(a, w, bh, tile, pair);
+    for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+      Item it;
+      if (!resolve<RAGGED>(a, &tq, &tk, &tv, w, it)) continue;
+      const Geom& g = *it.g;
+      const int bh = it.bh, tile = it.tile;
+      const float sl2 = g.scale_log2;
+      const uint64_t s2 = f2pack(sl2, sl2);
       TileBlocks tbk;
       tile_blocks(g, tile, tbk);
-      const int qa = 2 * pair;
+      const int qa = 2 * it.pair;
       if (qa + x >= tbk.NB) continue;
       const int qb = qa + x;
       int qo[3], ql[3];
@@ -480,12 +559,12 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       ++WX;
       const float inv = 1.f / l;
       const int64_t slot = tile_slot0(g, bh, tile) + qb * 128 + row;
-      if (qvalid && a.lse2) a.lse2[slot] = m + __log2f(l);
+      if (qvalid && it.lse2) it.lse2[slot] = m + __log2f(l);
       const int p[3] = {tbk.tb.lo[0] + ql[0], tbk.tb.lo[1] + ql[1], tbk.tb.lo[2] + ql[2]};
       const int64_t tok = qvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
       const bool single = qvalid && single_cover(g, p);
-      OutT* dst_out = static_cast<OutT*>(a.out) + ((int64_t)bh * g.N + tok) * kD;
-      float* dst_scr = a.ot + slot * kD;
+      OutT* dst_out = static_cast<OutT*>(it.out) + ((int64_t)bh * g.N + tok) * kD;
+      float* dst_scr = it.ot + slot * kD;
       uint32_t r[32];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
@@ -520,13 +599,13 @@ template <typename OutT>
 cudaError_t run_fwd64(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v,
                       void* out, float* lse2, float* ot, uint32_t flags, cudaStream_t st) {
   Fwd64Args a;
+  memset(&a, 0, sizeof(a));
   a.g = g;
   a.out = out;
   a.lse2 = lse2;
   a.ot = ot;
   a.flags = flags;
-  a.npairs = (g.nbmax_tot + 1) / 2;
-  const int64_t items = (int64_t)g.B * g.nh * g.ntiles * a.npairs;
+  const int64_t items = (int64_t)g.B * g.nh * g.ntiles * box_pairs(g);
   if (items >= (1LL << 31)) return cudaErrorNotSupported;
   a.items = (int)items;
   const int BH = g.B * g.nh;
@@ -535,7 +614,7 @@ cudaError_t run_fwd64(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16
       !make_tmap_5d(&mk, k, kD, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
       !make_tmap_5d(&mv, v, kD, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt))
     return cudaErrorInvalidValue;
-  auto kern = fwd64_kernel<OutT>;
+  auto kern = fwd64_kernel<OutT, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
   if (e != cudaSuccess) return e;
   const int grid = (int)(a.items < num_sms() ? a.items : num_sms());
@@ -550,6 +629,22 @@ cudaError_t launch_sm103_fwd64(const Geom& g, const __nv_bfloat16* q, const __nv
   if (g.d != kD) return cudaErrorNotSupported;
   if (out_dtype == GATTN_BF16) return run_fwd64<__nv_bfloat16>(g, q, k, v, out, lse2, ot, flags, st);
   return run_fwd64<float>(g, q, k, v, out, lse2, ot, flags, st);
+}
+
+int fwd64_ragged_items(const Geom& g) { return g.nh * g.ntiles * box_pairs(g); }
+
+cudaError_t launch_sm103_fwd64_ragged(const ReqDesc* reqs, const int64_t* counts, cudaStream_t st) {
+  Fwd64Args a;
+  memset(&a, 0, sizeof(a));
+  a.reqs = reqs;
+  a.counts = counts;
+  CUtensorMap dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  auto kern = fwd64_kernel<__nv_bfloat16, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+  if (e != cudaSuccess) return e;
+  kern<<<num_sms(), kThreadsF, Cfg::kSmem, st>>>(dummy, dummy, dummy, a);
+  return cudaGetLastError();
 }
 
 }  // namespace gattn
