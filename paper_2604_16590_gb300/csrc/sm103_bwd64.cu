@@ -18,7 +18,9 @@
 // shape.  The packed P'/dS operand has its own TMEM columns, so the next box's
 // score products start as soon as the math warps have read the current scores
 // (s_empty), while the gradient products of the current box wait only for
-// the packed values (p_full).  The packed operand and its gradient products
+// the packed values (p_full).  The two score chains (S and dP) have their own
+// ready/free barriers: the math warps exponentiate S while dP is still being
+// computed, and the next box's S chain starts once S (not S and dP) was read.  The packed operand and its gradient products
 // come in two halves (K-steps 0..3 and 4..7, written by the warps of column
 // groups 0-1 and 2-3) with a ready and a free barrier each: a half of box G can
 // be written while the other half of box G-1 is still being read, so the
@@ -100,27 +102,34 @@ struct Kv64 {
   static constexpr int kOnes = kQ + kStages * 2 * kBox;  // A: ones in K 0..2 at kOnes, ones in K 3..5 at kOnes+4096
   static constexpr int kExt = kOnes + 2 * 4096;            // B, stage s at kExt + s*4096: the 128 statistics rows
   static constexpr int kBar = kExt + kStages * 4096;
-  // kv_full, kv_empty, qd_full[S], qd_empty[S], s_full, s_empty, p_full[2], p_empty[2], acc_full, acc_empty,
-  // drain[2]
-  static constexpr int kNumBars = 2 + 2 * kStages + 10;
+  // kv_full, kv_empty, qd_full[S], qd_empty[S], s_full[2], s_empty[2], p_full[2], p_empty[2], acc_full,
+  // acc_empty, drain[2]   (s_*[0]: the S chain, s_*[1]: the dP chain)
+  static constexpr int kNumBars = 2 + 2 * kStages + 12;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kSmem = kMisc + 16 + 1024;
   // TMEM: S'^T 0, dP'^T 128, P'^T (packed) 256, dS^T (packed) 320, dV 384, dK 448
   static constexpr uint32_t kColST = 0, kColDP = 128, kColP = 256, kColDS = 320, kColDV = 384, kColDK = 448;
 };
 
-// P'^T and dS^T of 32 columns of this thread's key row (S'^T, dP'^T already
-// carry the statistics), packed as BF16 pairs.
-__device__ __forceinline__ void kv_chunk(const uint32_t (&s)[32], const uint32_t (&dp)[32], uint64_t s2,
-                                         uint32_t (&pp)[16], uint32_t (&pd)[16]) {
+// P'^T of 32 columns of this thread's key row (S'^T already carries the
+// statistics): FP32 in place of the scores, and as BF16 pairs.
+__device__ __forceinline__ void kv_p(uint32_t (&s)[32], uint64_t s2, uint32_t (&pp)[16]) {
 #pragma unroll
   for (int c = 0; c < 32; c += 2) {
     float a0, a1;
     f2unpack(fmul2(u2pack(s[c], s[c + 1]), s2), a0, a1);
     const float p0 = ex2(a0), p1 = ex2(a1);
-    float e0, e1;
-    f2unpack(fmul2(f2pack(p0, p1), u2pack(dp[c], dp[c + 1])), e0, e1);
+    s[c] = __float_as_uint(p0);
+    s[c + 1] = __float_as_uint(p1);
     pp[c >> 1] = pack_bf16(p0, p1);
+  }
+}
+// dS^T = P'^T dP'^T (dP'^T already carries -D) as BF16 pairs
+__device__ __forceinline__ void kv_ds(const uint32_t (&p)[32], const uint32_t (&dp)[32], uint32_t (&pd)[16]) {
+#pragma unroll
+  for (int c = 0; c < 32; c += 2) {
+    float e0, e1;
+    f2unpack(fmul2(u2pack(p[c], p[c + 1]), u2pack(dp[c], dp[c + 1])), e0, e1);
     pd[c >> 1] = pack_bf16(e0, e1);
   }
 }
@@ -139,8 +148,8 @@ __global__ void __launch_bounds__(kThreads64, 1)
   uint64_t* qd_full = bars + 2;
   uint64_t* qd_empty = qd_full + C::kStages;
   uint64_t* s_full = qd_empty + C::kStages;
-  uint64_t* s_empty = s_full + 1;
-  uint64_t* p_full = s_empty + 1;   // [2]: one per half of the packed operand
+  uint64_t* s_empty = s_full + 2;
+  uint64_t* p_full = s_empty + 2;   // [2]: one per half of the packed operand
   uint64_t* p_empty = p_full + 2;   // [2]
   uint64_t* acc_full = p_empty + 2;
   uint64_t* acc_empty = acc_full + 1;
@@ -173,8 +182,10 @@ __global__ void __launch_bounds__(kThreads64, 1)
       mbar_init(qd_full + s, 1);
       mbar_init(qd_empty + s, 1);
     }
-    mbar_init(s_full, 1);
-    mbar_init(s_empty, kMath64);
+    for (int c = 0; c < 2; ++c) {
+      mbar_init(s_full + c, 1);
+      mbar_init(s_empty + c, kMath64);
+    }
     for (int h = 0; h < 2; ++h) {
       mbar_init(p_full + h, kMath64 / 2);
       mbar_init(p_empty + h, 1);
@@ -271,18 +282,21 @@ __global__ void __launch_bounds__(kThreads64, 1)
         for (int i = 0; i < tbk.NB; ++i, ++G) {
           const uint32_t st = G % C::kStages;
           if (!(ok = WAIT(qd_full + st, (G / C::kStages) & 1))) break;
-          if (G > 0 && !(ok = WAIT(s_empty, (G - 1) & 1))) break;  // scores of box G-1 read
+          if (G > 0 && !(ok = WAIT(s_empty, (G - 1) & 1))) break;  // S'^T of box G-1 read
           tc_fence_after();
           const uint64_t dq = dmove(dQ0, st * 2 * kBox), ddo = dmove(dq, kBox), de = dmove(dExt0, st * 4096);
 #pragma unroll
           for (int ks = 0; ks < kD / 16; ++ks)
             umma_bf16(tmem + C::kColST, dmove(dK, ks * 32), dmove(dq, ks * 32), idS, ks > 0);
           umma_bf16(tmem + C::kColST, dOnesS, de, idS, 1u);
+          umma_commit(s_full);
+          if (G > 0 && !(ok = WAIT(s_empty + 1, (G - 1) & 1))) break;  // dP'^T of box G-1 read
+          tc_fence_after();
 #pragma unroll
           for (int ks = 0; ks < kD / 16; ++ks)
             umma_bf16(tmem + C::kColDP, dmove(dV, ks * 32), dmove(ddo, ks * 32), idS, ks > 0);
           umma_bf16(tmem + C::kColDP, dOnesD, de, idS, 1u);
-          umma_commit(s_full);
+          umma_commit(s_full + 1);
           if (i == tbk.NB - 1) umma_commit(kv_empty);  // K, V of this item no longer read
         }
         ++W;
@@ -350,20 +364,26 @@ __global__ void __launch_bounds__(kThreads64, 1)
       for (int i = 0; i < tbk.NB && ok; ++i, ++G) {
         if (!(ok = WAIT(s_full, G & 1))) break;
         tc_fence_after();
-        uint32_t sv[32], dv[32], pp[16], pd[16];
+        uint32_t sv[32], dv[32], pk[16];
         tmem_ld32(tl + C::kColST + c4 * 32, sv);
-        tmem_ld32(tl + C::kColDP + c4 * 32, dv);
         tmem_wait_ld(sv);
-        tmem_wait_ld(dv);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(s_empty);  // the next box's score products may overwrite S'^T, dP'^T
-        kv_chunk(sv, dv, s2, pp, pd);
+        if (lane == 0) mbar_arrive(s_empty);  // the next box's S'^T may overwrite this one
+        kv_p(sv, s2, pk);  // sv <- P'^T (FP32), pk <- P'^T (BF16 pairs)
         // this half's gradient products of box G-1 are done with the packed operand
         if (G > 0 && !(ok = WAIT(p_empty + (c4 >> 1), (G - 1) & 1))) break;
         tc_fence_after();
-        tmem_st16(tl + C::kColP + c4 * 16, pp);
-        tmem_st16(tl + C::kColDS + c4 * 16, pd);
+        tmem_st16(tl + C::kColP + c4 * 16, pk);
+        if (!(ok = WAIT(s_full + 1, G & 1))) break;
+        tc_fence_after();
+        tmem_ld32(tl + C::kColDP + c4 * 32, dv);
+        tmem_wait_ld(dv);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(s_empty + 1);  // the next box's dP'^T may overwrite this one
+        kv_ds(sv, dv, pk);  // dS^T = P'^T dP'^T (BF16 pairs)
+        tmem_st16(tl + C::kColDS + c4 * 16, pk);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
@@ -401,19 +421,49 @@ __global__ void __launch_bounds__(kThreads64, 1)
 }
 
 // =============================================================== dQ
+// P' = exp2(s S log2e - lse') of 32 columns of this thread's query row, FP32
+// in place of the scores (keys outside the tile masked to 0)
+template <bool MASK>
+__device__ __forceinline__ void q_p(uint32_t (&s)[32], uint32_t mbits, float sl2, float nL) {
+  const uint64_t s2 = f2pack(sl2, sl2), nl2 = f2pack(nL, nL);
+#pragma unroll
+  for (int c = 0; c < 32; c += 2) {
+    float a0, a1;
+    f2unpack(ffma2(u2pack(s[c], s[c + 1]), s2, nl2), a0, a1);
+    float p0 = ex2(a0), p1 = ex2(a1);
+    if (MASK) {
+      p0 = (mbits >> c) & 1u ? p0 : 0.f;
+      p1 = (mbits >> (c + 1)) & 1u ? p1 : 0.f;
+    }
+    s[c] = __float_as_uint(p0);
+    s[c + 1] = __float_as_uint(p1);
+  }
+}
+// dS = P' (dP - D) as BF16 pairs
+__device__ __forceinline__ void q_ds(const uint32_t (&p)[32], const uint32_t (&dp)[32], float nD, uint32_t (&pk)[16]) {
+  const uint64_t nd2 = f2pack(nD, nD);
+#pragma unroll
+  for (int c = 0; c < 32; c += 2) {
+    float e0, e1;
+    f2unpack(fmul2(u2pack(p[c], p[c + 1]), fadd2(u2pack(dp[c], dp[c + 1]), nd2)), e0, e1);
+    pk[c >> 1] = pack_bf16(e0, e1);
+  }
+}
+
 struct Q64 {
   static constexpr int kStages = 4;  // (K, V) ring
   static constexpr int kQ = 0;
   static constexpr int kDO = kBox;
   static constexpr int kK = 2 * kBox;  // stage s: K at kK + s*2*kBox, V after it
   static constexpr int kBar = kK + kStages * 2 * kBox;
-  // qd_full, qd_empty, qt_full, kv_full[S], kv_empty[S], s_full, s_empty, p_full[2], p_empty[2], acc_full,
-  // acc_empty, drain[2]
-  static constexpr int kNumBars = 3 + 2 * kStages + 10;
+  // qd_full, qd_empty, qt_full, kv_full[S], kv_empty[S], s_full[2], s_empty[2], p_full[2], p_empty[2],
+  // acc_full, acc_empty, drain[2]   (s_*[0]: the S chain, s_*[1]: the dP chain)
+  static constexpr int kNumBars = 3 + 2 * kStages + 12;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kSmem = kMisc + 16 + 1024;
-  // TMEM: S 0, dP 128, dS (packed) 256, dQ 320, Q (packed) 384, dOut (packed) 416
-  static constexpr uint32_t kColS = 0, kColDP = 128, kColDS = 256, kColDQ = 320, kColQ = 384, kColDO = 416;
+  // TMEM: S 0, dP 128, dS buffer 0 (packed) 256, dQ 320, Q (packed) 384, dOut (packed) 416, dS buffer 1 448
+  static constexpr uint32_t kColS = 0, kColDP = 128, kColDQ = 320, kColQ = 384, kColDO = 416;
+  __device__ static uint32_t col_ds(uint32_t b) { return b ? 448u : 256u; }
 };
 
 template <typename OutT>
@@ -430,8 +480,8 @@ __global__ void __launch_bounds__(kThreads64, 1)
   uint64_t* kv_full = bars + 3;
   uint64_t* kv_empty = kv_full + C::kStages;
   uint64_t* s_full = kv_empty + C::kStages;
-  uint64_t* s_empty = s_full + 1;
-  uint64_t* p_full = s_empty + 1;   // [2]: one per half of dS
+  uint64_t* s_empty = s_full + 2;
+  uint64_t* p_full = s_empty + 2;   // [2]: one per dS buffer
   uint64_t* p_empty = p_full + 2;   // [2]
   uint64_t* acc_full = p_empty + 2;
   uint64_t* acc_empty = acc_full + 1;
@@ -448,11 +498,13 @@ __global__ void __launch_bounds__(kThreads64, 1)
       mbar_init(kv_full + s, 1);
       mbar_init(kv_empty + s, 1);
     }
-    mbar_init(s_full, 1);
-    mbar_init(s_empty, kMath64);
-    for (int h = 0; h < 2; ++h) {
-      mbar_init(p_full + h, kMath64 / 2);
-      mbar_init(p_empty + h, 1);
+    for (int c = 0; c < 2; ++c) {
+      mbar_init(s_full + c, 1);
+      mbar_init(s_empty + c, kMath64);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(p_full + b, kMath64);
+      mbar_init(p_empty + b, 1);
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, kMath64);
@@ -540,16 +592,19 @@ __global__ void __launch_bounds__(kThreads64, 1)
         for (int j = 0; j < tbk.NB; ++j, ++G) {
           const uint32_t st = G % C::kStages;
           if (!(ok = WAIT(kv_full + st, (G / C::kStages) & 1))) break;
-          if (G > 0 && !(ok = WAIT(s_empty, (G - 1) & 1))) break;  // scores of box G-1 read
+          if (G > 0 && !(ok = WAIT(s_empty, (G - 1) & 1))) break;  // S of box G-1 read
           tc_fence_after();
           const uint64_t dk = dmove(dK0, st * 2 * kBox), dv = dmove(dk, kBox);
 #pragma unroll
           for (int ks = 0; ks < kD / 16; ++ks)
             umma_bf16_ts(tmem + C::kColS, tmem + C::kColQ + ks * 8, dmove(dk, ks * 32), idS, ks > 0);
+          umma_commit(s_full);
+          if (G > 0 && !(ok = WAIT(s_empty + 1, (G - 1) & 1))) break;  // dP of box G-1 read
+          tc_fence_after();
 #pragma unroll
           for (int ks = 0; ks < kD / 16; ++ks)
             umma_bf16_ts(tmem + C::kColDP, tmem + C::kColDO + ks * 8, dmove(dv, ks * 32), idS, ks > 0);
-          umma_commit(s_full);
+          umma_commit(s_full + 1);
         }
         ++W;
       }
@@ -572,22 +627,18 @@ __global__ void __launch_bounds__(kThreads64, 1)
         for (int j = 0; j < tbk.NB; ++j, ++G) {
           const uint32_t st = G % C::kStages;
           // p_full(G) implies s_full(G): the score products of this stage are
-          // complete, so the kv_empty commit below covers every reader
+          // complete, so the kv_empty commit below covers every reader.  dS is
+          // double-buffered: box G uses buffer G & 1.
+          const uint32_t b = G & 1;
+          if (!(ok = WAIT(p_full + b, (G >> 1) & 1))) break;
+          if (j == 0 && !(ok = WAIT(acc_empty, (W & 1) ^ 1))) break;
+          tc_fence_after();
           const uint64_t bk = dmove(bK0, st * 2 * kBox);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (!(ok = WAIT(p_full + h, G & 1))) break;
-            if (j == 0 && h == 0 && !(ok = WAIT(acc_empty, (W & 1) ^ 1))) break;
-            tc_fence_after();
-#pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-              const int ks = 4 * h + k4;
-              umma_bf16_ts(tmem + C::kColDQ, tmem + C::kColDS + ks * 8, dmove(bk, ks * 2048), idA,
-                           (j > 0 || ks > 0) ? 1u : 0u);
-            }
-            umma_commit(p_empty + h);
-          }
-          if (!ok) break;
+          for (int ks = 0; ks < 8; ++ks)
+            umma_bf16_ts(tmem + C::kColDQ, tmem + C::col_ds(b) + ks * 8, dmove(bk, ks * 2048), idA,
+                         (j > 0 || ks > 0) ? 1u : 0u);
+          umma_commit(p_empty + b);
           umma_commit(kv_empty + st);
         }
         if (!ok) break;
@@ -654,24 +705,31 @@ __global__ void __launch_bounds__(kThreads64, 1)
         tc_fence_after();
         uint32_t sv[32], dv[32], pk[16];
         tmem_ld32(tl + C::kColS + c4 * 32, sv);
-        tmem_ld32(tl + C::kColDP + c4 * 32, dv);
         tmem_wait_ld(sv);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(s_empty);  // the next box's S may overwrite this one
+        if (full)
+          q_p<false>(sv, 0u, sl2, nL);  // sv <- P' (FP32)
+        else
+          q_p<true>(sv, kmask, sl2, nL);
+        if (!(ok = WAIT(s_full + 1, G & 1))) break;
+        tc_fence_after();
+        tmem_ld32(tl + C::kColDP + c4 * 32, dv);
         tmem_wait_ld(dv);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(s_empty);  // the next box's score products may overwrite S, dP
-        if (full)
-          dq_half<false>(sv, dv, 0u, sl2, nL, nD, pk);
-        else
-          dq_half<true>(sv, dv, kmask, sl2, nL, nD, pk);
-        // this half's dQ products of box G-1 are done with dS
-        if (G > 0 && !(ok = WAIT(p_empty + (c4 >> 1), (G - 1) & 1))) break;
+        if (lane == 0) mbar_arrive(s_empty + 1);  // the next box's dP may overwrite this one
+        q_ds(sv, dv, nD, pk);
+        // dS buffer G & 1 is free once the dQ products of box G-2 are done
+        const uint32_t b = G & 1;
+        if (G > 1 && !(ok = WAIT(p_empty + b, ((G >> 1) - 1) & 1))) break;
         tc_fence_after();
-        tmem_st16(tl + C::kColDS + c4 * 16, pk);
+        tmem_st16(tl + C::col_ds(b) + c4 * 16, pk);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(p_full + (c4 >> 1));
+        if (lane == 0) mbar_arrive(p_full + b);
       }
       if (!ok) break;
       if (!(ok = WAIT(acc_full, W & 1))) break;
