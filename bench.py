@@ -34,9 +34,9 @@ UNIT = "Gtokens/s"
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
 # from the ncu capture summarised in profiles/ (None until captured for the
 # kernel as built now).
-# dkdv64: 1536.8 MB in one ncu capture of the same geometry with 1/16 of the
+# dkdv64: 1535.0 MB in one ncu capture of the same geometry with 1/16 of the
 # (batch*head) units, times 16 (the units are independent)
-TRAFFIC_PER_LAUNCH = {"bwd_dkdv": 24.59e9}
+TRAFFIC_PER_LAUNCH = {"bwd_dkdv": 24.56e9}
 
 
 def _extents(G, c, h):
