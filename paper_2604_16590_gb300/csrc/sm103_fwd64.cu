@@ -508,36 +508,23 @@ __global__ void __launch_bounds__(kThreadsF, 1)
             m = mblk;
           }
         }
-        // P_x and O_x are free once the previous P V of this box completed
-        if (GX > 0 && !(ok = WAIT(p_empty(x), (GX - 1) & 1))) break;
-        tc_fence_after();
-        if (any_grow) {
-          rescale_o(tO, f);
-          l *= f;
-        }
+        // the exponentials depend only on the scores and the new reference max:
+        // they are computed into registers before P_x is known to be free
         const uint64_t nm2 = f2pack(-m, -m);
         uint64_t acc[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[i] = f2pack(0.f, 0.f);
-        uint32_t pk[16];
+        uint32_t pk0[16], pk1[16], pk2[16], pk3[16];
         if (full) {
-          exp_chunk<false>(s0, 0u, s2, nm2, acc, pk);
-          tmem_st16(tP, pk);
-          exp_chunk<false>(s1, 0u, s2, nm2, acc, pk);
-          tmem_st16(tP + 16, pk);
-          exp_chunk<false>(s2r, 0u, s2, nm2, acc, pk);
-          tmem_st16(tP + 32, pk);
-          exp_chunk<false>(s3, 0u, s2, nm2, acc, pk);
-          tmem_st16(tP + 48, pk);
+          exp_chunk<false>(s0, 0u, s2, nm2, acc, pk0);
+          exp_chunk<false>(s1, 0u, s2, nm2, acc, pk1);
+          exp_chunk<false>(s2r, 0u, s2, nm2, acc, pk2);
+          exp_chunk<false>(s3, 0u, s2, nm2, acc, pk3);
         } else {
-          exp_chunk<true>(s0, km[0], s2, nm2, acc, pk);
-          tmem_st16(tP, pk);
-          exp_chunk<true>(s1, km[1], s2, nm2, acc, pk);
-          tmem_st16(tP + 16, pk);
-          exp_chunk<true>(s2r, km[2], s2, nm2, acc, pk);
-          tmem_st16(tP + 32, pk);
-          exp_chunk<true>(s3, km[3], s2, nm2, acc, pk);
-          tmem_st16(tP + 48, pk);
+          exp_chunk<true>(s0, km[0], s2, nm2, acc, pk0);
+          exp_chunk<true>(s1, km[1], s2, nm2, acc, pk1);
+          exp_chunk<true>(s2r, km[2], s2, nm2, acc, pk2);
+          exp_chunk<true>(s3, km[3], s2, nm2, acc, pk3);
         }
         float lsum = 0.f;
 #pragma unroll
@@ -546,7 +533,18 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           f2unpack(acc[i], u, v);
           lsum += u + v;
         }
+        // P_x and O_x are free once the previous P V of this box completed
+        if (GX > 0 && !(ok = WAIT(p_empty(x), (GX - 1) & 1))) break;
+        tc_fence_after();
+        if (any_grow) {
+          rescale_o(tO, f);
+          l *= f;
+        }
         l += lsum;
+        tmem_st16(tP, pk0);
+        tmem_st16(tP + 16, pk1);
+        tmem_st16(tP + 32, pk2);
+        tmem_st16(tP + 48, pk3);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
