@@ -198,6 +198,88 @@ def run_serving(n_requests, rank=0):
     }
 
 
+def run_compress(steps, warmup, dev, rank=0, cpu=True, peaks=None):
+    """Temporal compression (learned query per head over S history frames per
+    location) on the long-temporal-context shape: 2048 frames x 32 x 64
+    locations, 8 heads, d = 128, BF16 keys/values (17.2 GB read per call, > L2,
+    no flush).  Device time from CUDA events on the launching stream."""
+    import torch
+
+    from paper_2604_16590_gb300 import gattn
+    from paper_2604_16590_gb300.inputs import HISTORY_WORKLOADS, history_inputs
+    from paper_2604_16590_gb300.replicas import replica_seed
+
+    w = HISTORY_WORKLOADS["h3_2k"]
+    w = type(w)(**{**w.__dict__, "seed": replica_seed(w.seed, rank)})
+    q, k, v = history_inputs(w, dev)
+    desc = gattn.compress_desc(k)
+    out = torch.empty((w.B, w.nh, w.M, w.d), dtype=torch.bfloat16, device=dev)
+    lse = torch.empty((w.B, w.nh, w.M), dtype=torch.float32, device=dev)
+    nws = gattn.gattn_compress_workspace_bytes(desc)
+    ws = torch.empty(max(nws, 16), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def call():
+        gattn.check(gattn.gattn_compress_fwd(desc, q, k, v, out, lse, ws if nws else None, stream=stream),
+                    "gattn_compress_fwd")
+
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    gattn.gattn_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = gattn.gattn_profile_read()
+    gattn.gattn_profile_enable(False)
+    gattn.check(gattn.gattn_stream_status(), "compress status")
+    ms = e0.elapsed_time(e1) / steps
+    kv_bytes = 2 * k.numel() * k.element_size()
+    alg = kv_bytes + q.numel() * 4 + out.numel() * 2 + lse.numel() * 4
+    main_ms = prof.get("compress", (steps, ms * steps))[1] / steps
+    peak, src = (peaks[0], peaks[3]) if peaks else (6800.0, "fallback")
+    res = {
+        "workload": f"{w.name}: {w.S} history frames x {w.Y}x{w.X} locations, B={w.B}, {w.nh} heads, d={w.d}, "
+                    "BF16 k/v N(0,0.5), FP32 learned query",
+        "ms_per_call": ms, "calls": steps, "warmup": warmup,
+        "frames_per_s": w.B * w.nh * w.S * w.M / (ms * 1e-3),
+        "kernels": {n: {"launches": c, "ms_per_launch": t / c} for n, (c, t) in prof.items()},
+        "workspace_bytes": nws,
+        "roofline": {"kernel": "compress", "bound": "hbm", "achieved": alg / (main_ms * 1e-3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": alg / (main_ms * 1e-3) / 1e9 / peak,
+                     "peak_source": f"hbm_gbs of {src}", "algorithmic_bytes": alg, "traffic": None},
+        "call_gbs": alg / (ms * 1e-3) / 1e9,
+    }
+    if cpu:
+        import numpy as np
+
+        from oracle import compress as oc
+
+        # the oracle as it stands on whole locations (all S frames), ~5-10 s
+        rng = np.random.default_rng(1)
+        n_loc, spent, done = 0, 0.0, 0
+        while spent < 5.0 and n_loc < 4096:
+            h, m = int(rng.integers(0, w.nh)), int(rng.integers(0, w.M))
+            kl = k[0, h, :, m].double().cpu().numpy()[None, None, :, None, :]
+            vl = v[0, h, :, m].double().cpu().numpy()[None, None, :, None, :]
+            qh = q[h:h + 1].double().cpu().numpy()
+            t0 = time.perf_counter()
+            oc.forward(qh, kl, vl)
+            spent += time.perf_counter() - t0
+            n_loc += 1
+        per_call_s = spent / n_loc * w.B * w.nh * w.M
+        res["cpu_baseline"] = {"value": w.B * w.nh * w.S * w.M / per_call_s, "unit": "frames/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"{n_loc} (head, location) units of {w.S} frames, {spent:.1f} s; "
+                                         f"scaled by units to the whole call"}
+    del q, k, v, out, lse, ws
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args, w):
     import torch
 
@@ -239,6 +321,8 @@ def main():
     ap.add_argument("--workload", default="c2_262k_p")
     ap.add_argument("--fp32-steps", type=int, default=1, help="timed steps of the plain FP32 form (0 = skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--compress-steps", type=int, default=10,
+                    help="timed calls of the temporal compression (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=256,
                     help="requests of the serving run (Poisson 40/s, 20 steps; 0 = skip)")
     args = ap.parse_args()
@@ -280,6 +364,12 @@ def main():
         if world > 1:
             t_srv = replicas.max_over_ranks(serve["wall_s"], device=dev)
             serve["token_steps_per_s_all_ranks"] = replicas.sum_over_ranks(serve["token_steps"], device=dev) / t_srv
+
+    # ---------------------------------------------------------------- temporal compression (rank-local)
+    compress = None
+    if args.compress_steps > 0:
+        compress = run_compress(args.compress_steps, 3, dev, rank, cpu=rank == 0 and world == 1 and not args.no_cpu,
+                                peaks=measured_peaks())
 
     # ---------------------------------------------------------------- inputs (per rank)
     q, k, v = qkv(w.shape, replicas.replica_seed(w.seed, rank), w.std, "bf16", device=dev)
@@ -430,6 +520,7 @@ def main():
             "kernels": kernels,
             "fp32_form": fp32,
             "serve": serve,
+            "compress": compress,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -266,6 +266,58 @@ void gattn_serve_destroy(gattn_server *s);
 gattn_status gattn_fwd_noalloc(const gattn_desc *desc, const void *q, const void *k, const void *v,
                                void *out, gattn_stream_t stream);
 
+/*
+ * Temporal compression (arXiv 2604.16590, Sec. III-B, the STORM-DiT
+ * architecture paragraph and Fig. 2(b)): history states are folded into one
+ * global temporal representation by cross-attention across the temporal
+ * dimension.  At every spatial location m a learned query per head attends
+ * over the S history frames of that location and returns one token:
+ *
+ *     out[b,h,m] = sum_t softmax_t(scale q_h . k[b,h,t,m]) v[b,h,t,m]
+ *     lse[b,h,m] = log sum_t exp(scale q_h . k[b,h,t,m])
+ *
+ * The same call aggregates the variable dimension (S = number of variables,
+ * M = tokens per variable).  The cost is linear in S: every history token is
+ * read once, and the pass is bound by HBM bandwidth.
+ *
+ *   B, nh, d   batch, heads, head dim: d in {64, 128} for BF16 inputs,
+ *              {32, 64, 128} for FP32 inputs.
+ *   S          frames pooled per location (>= 1).
+ *   M          locations per frame (>= 1), e.g. Y * X.
+ *   in_dtype   dtype of k and v; out_dtype the dtype of out.
+ *   scale      softmax scale; 0 means 1/sqrt(d).
+ */
+typedef struct {
+  int32_t B, nh, d;
+  int32_t S, M;
+  int32_t in_dtype;
+  int32_t out_dtype;
+  float scale;
+} gattn_compress_desc;
+
+/* Bytes of the workspace gattn_compress_fwd needs: nonzero when the frames
+ * are split into ranges to fill the GPU (few locations, long histories);
+ * then it holds FP32 per-range partials.  0 also on an invalid desc. */
+size_t gattn_compress_workspace_bytes(const gattn_compress_desc *desc);
+
+/*
+ * Forward of the temporal compression.
+ *   q     [nh, d] FP32 learned queries (device).
+ *   k, v  [B, nh, S, M, d] in in_dtype (device), location m contiguous within
+ *         a frame.
+ *   out   [B, nh, M, d] in out_dtype (device), fully overwritten.
+ *   lse   [B, nh, M] FP32 natural-log normaliser (device), or NULL.
+ *   ws    device workspace of gattn_compress_workspace_bytes(desc) bytes
+ *         (may be NULL when that is 0).
+ * All pointers 16-byte aligned (lse 4-byte).  One streaming kernel (online
+ * softmax, S-long sums compensated by 256-frame blocking); when the frames
+ * are split, a second kernel merges the ranges in fixed order.  Deterministic.
+ * GATTN_ERR_INVALID_ARG on a bad desc or pointer, GATTN_ERR_WORKSPACE when the
+ * workspace is missing or short, GATTN_ERR_CUDA when a launch fails.
+ */
+gattn_status gattn_compress_fwd(const gattn_compress_desc *desc, const float *q, const void *k, const void *v,
+                                void *out, float *lse, void *ws, size_t ws_bytes, gattn_stream_t stream);
+
 /* Synchronises `stream`, then returns (and clears) the device status word of
  * this library on the current device: GATTN_OK, GATTN_ERR_TIMEOUT or
  * GATTN_ERR_DEVICE_BOUNDS; GATTN_ERR_CUDA if the stream reported an error. */
@@ -280,7 +332,8 @@ gattn_status gattn_stream_status(gattn_stream_t stream);
  * guarded by a mutex; at most 65536 launches are recorded per enable.
  */
 typedef struct {
-  char name[24];    /* "fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd" */
+  char name[24];    /* "fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd",
+                       "compress", "compress_combine" */
   int64_t launches;
   double total_ms;
 } gattn_kernel_stat;

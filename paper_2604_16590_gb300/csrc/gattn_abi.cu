@@ -13,7 +13,8 @@ namespace gattn {
 
 // ------------------------------------------------------------ kernel timing
 namespace {
-const char* const kKernelNames[kKCount] = {"fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd"};
+const char* const kKernelNames[kKCount] = {"fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd",
+                                           "compress", "compress_combine"};
 struct ProfRecord {
   int kernel;
   cudaEvent_t start, stop;
@@ -283,6 +284,38 @@ gattn_status gattn_bwd(const gattn_desc* desc, const void* q, const void* k, con
     prof_end(kKMergeBwd, st);
   }
   return from_cuda(e);
+}
+
+static bool compress_desc_ok(const gattn_compress_desc* c) {
+  if (!c) return false;
+  if (c->B < 1 || c->nh < 1 || c->S < 1 || c->M < 1) return false;
+  if (!dtype_ok(c->in_dtype) || !dtype_ok(c->out_dtype)) return false;
+  if (c->in_dtype == GATTN_BF16 && c->d != 64 && c->d != 128) return false;
+  if (c->in_dtype == GATTN_FP32 && c->d != 32 && c->d != 64 && c->d != 128) return false;
+  if (!(c->scale >= 0.f) || !isfinite(c->scale)) return false;
+  // element offsets of k/v stay below 2^62 and grid sizes below 2^31
+  const double kv = (double)c->B * c->nh * c->S * c->M * c->d;
+  const double items = (double)c->B * c->nh * ((c->M + 31) / 32) * 64.0;
+  return kv < 4.0e18 && items < 2.0e9;
+}
+
+size_t gattn_compress_workspace_bytes(const gattn_compress_desc* c) {
+  if (!compress_desc_ok(c)) return 0;
+  return compress_ws_bytes(c->B, c->nh, c->S, c->M, c->d);
+}
+
+gattn_status gattn_compress_fwd(const gattn_compress_desc* c, const float* q, const void* k, const void* v, void* out,
+                                float* lse, void* ws, size_t ws_bytes, gattn_stream_t stream) {
+  if (!compress_desc_ok(c)) return GATTN_ERR_INVALID_ARG;
+  if (!q || !k || !v || !out) return GATTN_ERR_INVALID_ARG;
+  if (!aligned16(q) || !aligned16(k) || !aligned16(v) || !aligned16(out)) return GATTN_ERR_INVALID_ARG;
+  if (lse && ((uintptr_t)lse & 3u)) return GATTN_ERR_INVALID_ARG;
+  const size_t need = compress_ws_bytes(c->B, c->nh, c->S, c->M, c->d);
+  if (need && (!ws || ws_bytes < need || !aligned16(ws))) return GATTN_ERR_WORKSPACE;
+  const float scale = c->scale > 0.f ? c->scale : 1.f / sqrtf((float)c->d);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return from_cuda(launch_compress(q, k, v, out, lse, need ? static_cast<float*>(ws) : nullptr, c->B, c->nh, c->S,
+                                   c->M, c->d, c->in_dtype == GATTN_BF16, c->out_dtype == GATTN_BF16, scale, st));
 }
 
 gattn_status gattn_profile_enable(int32_t enable) {

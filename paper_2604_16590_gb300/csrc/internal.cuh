@@ -82,9 +82,27 @@ uint32_t fetch_status_sm103_bwd64();
 uint32_t fetch_status_serve();
 
 // ---- per-kernel device timing (gattn_profile_*); no-ops unless enabled
-enum KernelId : int { kKFwdTiles = 0, kKMergeFwd, kKBwdPrep, kKBwdDkdv, kKBwdDq, kKMergeBwd, kKCount };
+enum KernelId : int {
+  kKFwdTiles = 0, kKMergeFwd, kKBwdPrep, kKBwdDkdv, kKBwdDq, kKMergeBwd, kKCompress, kKCompressCombine, kKCount
+};
 void prof_begin(int kernel, cudaStream_t st);
 void prof_end(int kernel, cudaStream_t st);
+
+// Temporal compression (compress.cu): frames are split into `splits` ranges of
+// `chunk` frames when the (b, h, 32-location block) units alone cannot fill the
+// GPU; the partials then live in the caller's workspace:
+//   acc [splits, B*nh, M, d] FP32, then (log2 max, sum) [splits, B*nh, M, 2] FP32.
+struct CompressPlan {
+  int splits, chunk, mblocks;
+};
+CompressPlan compress_plan(int B, int nh, int S, int M);
+inline size_t compress_ws_bytes(int B, int nh, int S, int M, int d) {
+  const CompressPlan p = compress_plan(B, nh, S, M);
+  if (p.splits <= 1) return 0;
+  return (size_t)p.splits * B * nh * M * (size_t)(d + 2) * sizeof(float);
+}
+cudaError_t launch_compress(const float* q, const void* k, const void* v, void* out, float* lse, float* ws, int B,
+                            int nh, int S, int M, int d, bool in_bf16, bool out_bf16, float scale, cudaStream_t st);
 
 // ---- launchers (return cudaGetLastError() of their launches)
 cudaError_t launch_simt_fwd(const Geom& g, const float* q, const float* k, const float* v, void* out,

@@ -111,6 +111,19 @@ class gattn_desc(ctypes.Structure):
     ]
 
 
+class gattn_compress_desc(ctypes.Structure):
+    _fields_ = [
+        ("B", ctypes.c_int32),
+        ("nh", ctypes.c_int32),
+        ("d", ctypes.c_int32),
+        ("S", ctypes.c_int32),
+        ("M", ctypes.c_int32),
+        ("in_dtype", ctypes.c_int32),
+        ("out_dtype", ctypes.c_int32),
+        ("scale", ctypes.c_float),
+    ]
+
+
 _lib = None
 
 
@@ -147,6 +160,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         ),
         "gattn_serve_stats": ([P, ctypes.POINTER(gattn_serve_stats_t)], ctypes.c_int),
         "gattn_serve_destroy": ([P], None),
+        "gattn_compress_workspace_bytes": ([ctypes.POINTER(gattn_compress_desc)], S),
+        "gattn_compress_fwd": ([ctypes.POINTER(gattn_compress_desc), P, P, P, P, P, P, S, P], ctypes.c_int),
         "gattn_profile_enable": ([ctypes.c_int32], ctypes.c_int),
         "gattn_profile_read": ([ctypes.POINTER(gattn_kernel_stat), ctypes.c_int32], ctypes.c_int32),
     }
@@ -245,6 +260,17 @@ def gattn_fwd_noalloc(desc, q, k, v, out, stream=None) -> int:
 
 def gattn_stream_status(stream=None) -> int:
     return load_library().gattn_stream_status(_stream(stream))
+
+
+def gattn_compress_workspace_bytes(desc) -> int:
+    return load_library().gattn_compress_workspace_bytes(ctypes.byref(desc))
+
+
+def gattn_compress_fwd(desc, q, k, v, out, lse, ws, ws_bytes=None, stream=None) -> int:
+    return load_library().gattn_compress_fwd(
+        ctypes.byref(desc), _ptr(q), _ptr(k), _ptr(v), _ptr(out), _ptr(lse), _ptr(ws),
+        0 if ws is None else _nbytes(ws, ws_bytes), _stream(stream),
+    )
 
 
 def gattn_profile_enable(enable: bool) -> int:
@@ -461,3 +487,36 @@ class GlobalAttention(torch.autograd.Function):
 
 def global_attention(q, k, v, tiling: Tiling):
     return GlobalAttention.apply(q, k, v, tiling)
+
+
+# ---------------------------------------------------------------- temporal compression
+def compress_desc(k: torch.Tensor, out_dtype=None, scale: float = 0.0):
+    """gattn_compress_desc for history keys/values k of shape [B, nh, S, M, d]."""
+    if k.dim() != 5:
+        raise ValueError("expected [B, heads, S, M, d]")
+    B, nh, S, M, d = k.shape
+    desc = gattn_compress_desc()
+    desc.B, desc.nh, desc.d, desc.S, desc.M = int(B), int(nh), int(d), int(S), int(M)
+    desc.in_dtype = _DTYPES[k.dtype]
+    desc.out_dtype = _DTYPES[out_dtype if out_dtype is not None else k.dtype]
+    desc.scale = float(scale or 0.0)
+    return desc
+
+
+def compress_forward(q, k, v, scale: float = 0.0, out_dtype=None, with_lse: bool = True, stream=None):
+    """Temporal compression: (out [B, nh, M, d], lse [B, nh, M] or None).
+
+    q [nh, d] FP32 learned queries; k, v [B, nh, S, M, d] (BF16 or FP32)."""
+    _require_cuda(q, k, v)
+    if q.dtype != torch.float32 or k.dtype != v.dtype or k.shape != v.shape:
+        raise ValueError("q must be FP32 [nh, d]; k and v the same dtype and shape")
+    desc = compress_desc(k, out_dtype, scale)
+    if tuple(q.shape) != (desc.nh, desc.d):
+        raise ValueError("q must be [nh, d]")
+    B, nh, S, M, d = k.shape
+    out = torch.empty((B, nh, M, d), dtype=_TORCH_DTYPE[desc.out_dtype], device=k.device)
+    lse = torch.empty((B, nh, M), dtype=torch.float32, device=k.device) if with_lse else None
+    nws = gattn_compress_workspace_bytes(desc)
+    ws = torch.empty(nws, dtype=torch.uint8, device=k.device) if nws else None
+    check(gattn_compress_fwd(desc, q, k, v, out, lse, ws, stream=stream), "gattn_compress_fwd")
+    return out, lse

@@ -61,6 +61,49 @@ WORKLOADS = {
 }
 
 
+@dataclass(frozen=True)
+class HistoryWorkload:
+    """One synthetic temporal-compression workload: S history frames of a Y x X
+    patch grid (M = Y * X locations), keys/values iid N(0, std^2), and one
+    learned query per head iid N(0, 1) in FP32."""
+
+    name: str
+    B: int
+    nh: int
+    d: int
+    S: int
+    Y: int
+    X: int
+    std: float = 0.5
+    seed: int = 0
+    dtype: str = "bf16"
+
+    @property
+    def M(self) -> int:
+        return self.Y * self.X
+
+    @property
+    def shape(self):
+        return (self.B, self.nh, self.S, self.M, self.d)
+
+
+HISTORY_WORKLOADS = {
+    # the long-temporal-context shape (2048 frames x 32 x 64, 8 heads, d = 128) as history to compress
+    "h3_2k": HistoryWorkload("h3_2k", 1, 8, 128, 2048, 32, 64, 0.5, 20266, "bf16"),
+    # a long history on a few locations: 131072 frames x 8 x 8, 2 heads, d = 64 (S-long sums)
+    "h_128k": HistoryWorkload("h_128k", 1, 2, 64, 131072, 8, 8, 0.5, 20267, "bf16"),
+}
+
+
+def history_inputs(w: HistoryWorkload, device="cpu"):
+    """(q [nh, d] FP32, k, v [B, nh, S, M, d] in w.dtype) for a history workload."""
+    k, v = qkv(w.shape, w.seed, w.std, w.dtype, device, n=2)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(w.seed) + 104729)
+    q = torch.randn((w.nh, w.d), generator=gen, device=device, dtype=torch.float32)
+    return q, k, v
+
+
 def qkv(shape, seed: int, std: float = 1.0, dtype: str = "fp32", device="cpu", n: int = 3):
     """n iid N(0, std^2) tensors of `shape` from one seeded generator.
 

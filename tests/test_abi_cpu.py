@@ -89,3 +89,27 @@ def test_serve_request_bytes_on_host(lib):
     assert b >= 2 * nh * N * 64 * 2  # state + attention output (BF16)
     assert gattn.gattn_serve_request_bytes(cfg, 0, nh) == 0
     assert gattn.gattn_serve_request_bytes(cfg, 2 * T, nh) > b
+
+
+def test_compress_validation_on_the_host(lib):
+    """Temporal-compression descriptors and pointers are checked before any launch."""
+    d = gattn.gattn_compress_desc()
+    d.B, d.nh, d.d, d.S, d.M, d.in_dtype, d.out_dtype = 1, 8, 128, 2048, 2048, gattn.GATTN_BF16, gattn.GATTN_BF16
+    # 64 location blocks x 8 heads = 512 units < 152 x 16: the frames are split
+    ws = gattn.gattn_compress_workspace_bytes(d)
+    splits = ws // (8 * 2048 * (128 + 2) * 4)
+    assert ws == splits * 8 * 2048 * 130 * 4 and splits >= 2
+    d.M = 152 * 16 * 32  # enough location blocks: no split, no workspace
+    assert gattn.gattn_compress_workspace_bytes(d) == 0
+    for field, bad in (("S", 0), ("M", 0), ("d", 32), ("d", 96), ("B", 0)):
+        e = gattn.gattn_compress_desc()
+        e.B, e.nh, e.d, e.S, e.M, e.in_dtype, e.out_dtype = 1, 2, 64, 16, 16, gattn.GATTN_BF16, gattn.GATTN_FP32
+        setattr(e, field, bad)
+        assert gattn.gattn_compress_workspace_bytes(e) == 0
+        assert gattn.gattn_compress_fwd(e, 16, 16, 16, 16, None, None, stream=0) == 1
+    e.d = 64
+    e.S = 16
+    e.B = 1
+    # null or misaligned pointers
+    assert gattn.gattn_compress_fwd(e, None, 16, 16, 16, None, None, stream=0) == 1
+    assert gattn.gattn_compress_fwd(e, 16, 24, 16, 16, None, None, stream=0) == 1
