@@ -11,13 +11,17 @@
 // Layout: k, v [B, nh, S, M, d] (location m contiguous within a frame), q [nh, d]
 // FP32, out [B, nh, M, d], lse [B, nh, M] (natural log).
 //
-// Kernel design.  Eight lanes own one location (16-byte loads, the eight lanes
-// of a group read 128 contiguous bytes per instruction, a warp four
-// locations); a block of 256 threads streams 32 consecutive locations through
-// a range of frames, four frames per step so that eight 16-byte loads per
-// thread are in flight.  The score is a group dot product (three xor
-// shuffles).  Softmax is online in the log2 domain with one rescale per
-// four-frame step.  The S-long sums are compensated by blocking: an inner
+// Kernel design.  A work item is 32 consecutive locations of one (b, h) over a
+// range of frames.  Per frame, the keys (and the values) of those locations are
+// one contiguous slab; a producer warp streams the slabs of successive frames
+// into a ring of shared-memory stages with bulk asynchronous copies (TMA,
+// completion on an mbarrier), ~190 KB in flight per SM, so that the HBM stream
+// never waits on the arithmetic.  Eight consumer warps read the stages: eight
+// lanes own one location (16-byte shared loads, a warp reads 512 contiguous
+// bytes per instruction), and release the stage with one arrival per warp.
+// Persistent CTAs (two per SM) take the items in a fixed stride.  The score is
+// a group dot product (three xor shuffles).  Softmax is online in the log2
+// domain with one rescale per stage.  The S-long sums are compensated by blocking: an inner
 // accumulator covers at most 256 frames and is folded into the outer one at
 // each block boundary, so the rounding error grows with 256 + S/256 instead
 // of S.  When (b, h, location-block) units alone cannot fill the GPU, the
@@ -27,6 +31,9 @@
 #include <math.h>
 
 #include "internal.cuh"
+#include "sm103_ptx.cuh"
+
+GATTN_DEFINE_STATUS(compress)
 
 namespace gattn {
 namespace {
@@ -34,7 +41,8 @@ namespace {
 constexpr int kThreadsC = 256;
 constexpr int kLocPerBlock = 32;   // 8 warps x 4 locations
 constexpr int kInner = 256;        // frames per inner (compensated) accumulation block
-constexpr int kTargetItems = 152 * 16;
+constexpr int kPersistentCtas = 152 * 2;  // two CTAs per SM
+constexpr int kTargetItems = 152 * 32;
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kLog2e = 1.4426950408889634f;
 
@@ -42,14 +50,6 @@ __device__ __forceinline__ float ex2f(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-__device__ __forceinline__ uint4 ld_stream(const void* p) {
-  uint4 r;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-               : "l"(p));
-  return r;
 }
 
 // Elements of one 16-byte chunk as floats.
@@ -101,171 +101,218 @@ struct CArgs {
   float sl2;  // scale * log2(e)
 };
 
+__device__ void set_status_c(uint32_t c) { set_status(c); }
+
+// Ring geometry per (input type, head dim): a slab is the 32 locations of one
+// frame of one tensor; a stage holds FR frames of keys and values.
+template <typename InT, int D>
+struct Ring {
+  static constexpr int kSlab = kLocPerBlock * D * (int)sizeof(InT);
+  static constexpr int kFR = kSlab >= 8192 ? 1 : 8192 / kSlab;
+  static constexpr int kStage = kFR * 2 * kSlab;
+  static constexpr int kStages = 98304 / kStage;
+  static constexpr int kBars = kStages * kStage;  // barrier block offset
+  static constexpr int kSmem = kBars + 2 * kStages * 8 + 16;
+};
+constexpr int kConsumerWarps = 8;
+constexpr int kThreadsT = 32 * (kConsumerWarps + 1);
+
 // Element j of lane `sub` (chunk c, position i) is d-index c * 8 * CE + sub * CE + i:
-// each load instruction of the eight lanes covers 128 contiguous bytes.
+// each 16-byte load of the eight lanes of a group covers 128 contiguous bytes.
 template <typename InT, typename OutT, int D>
-__global__ void __launch_bounds__(kThreadsC) compress_kernel(const CArgs a) {
+__global__ void __launch_bounds__(kThreadsT, 2) compress_kernel(const CArgs a) {
   using C = Chunk<InT>;
+  using R = Ring<InT, D>;
   constexpr int CE = C::kE;
   constexpr int NC = D / (8 * CE);  // 16-byte chunks per lane and frame
   constexpr int E = NC * CE;        // elements per lane
-  constexpr int F = (NC <= 2) ? 4 : 2;  // frames per step
+  constexpr int FR = R::kFR;
   static_assert(NC >= 1 && D % (8 * CE) == 0, "head dim");
-  static_assert(kInner % F == 0, "inner block");
+  static_assert(kInner % FR == 0, "inner block");
 
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + R::kBars);
+  uint64_t* empty = full + R::kStages;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + R::kStages);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int sub = lane & 7, grp = lane >> 3;
-  const long long item = blockIdx.x;
-  const int split = (int)(item % a.splits);
-  const long long rest = item / a.splits;
-  const int mb = (int)(rest % a.mblocks);
-  const int bh = (int)(rest / a.mblocks);
-  const int h = bh % a.nh;
-  const int m_raw = mb * kLocPerBlock + warp * 4 + grp;
-  const bool valid = m_raw < a.M;
-  const int m = valid ? m_raw : a.M - 1;  // out-of-range groups stream a valid location and store nothing
-  const int t0 = split * a.chunk;
-  const int t1 = min(a.S, t0 + a.chunk);
-
-  float qv[E];
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
-#pragma unroll
-    for (int i = 0; i < CE; ++i) qv[c * CE + i] = a.q[(size_t)h * D + c * 8 * CE + sub * CE + i] * a.sl2;
-
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < R::kStages; ++i) {
+      sm103::mbar_init(full + i, 1);
+      sm103::mbar_init(empty + i, kConsumerWarps);
+    }
+    *abort_flag = 0;
+    sm103::fence_mbar_init();
+  }
+  __syncthreads();
+  const long long n_items = (long long)a.BH * a.mblocks * a.splits;
   const size_t fstride = (size_t)a.M * D;  // elements between consecutive frames
-  const InT* kp = static_cast<const InT*>(a.k) + ((size_t)bh * a.S * a.M + m) * D + sub * CE;
-  const InT* vp = static_cast<const InT*>(a.v) + ((size_t)bh * a.S * a.M + m) * D + sub * CE;
 
-  float mo = -INFINITY, lo = 0.f, acco[E];
-  float mi = -INFINITY, li = 0.f, acci[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) acco[e] = acci[e] = 0.f;
-
-  auto fold = [&]() {
-    const float mn = fmaxf(mo, mi);
-    const float fa = ex2f(mo - mn), fb = ex2f(mi - mn);
-    lo = lo * fa + li * fb;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      acco[e] = acco[e] * fa + acci[e] * fb;
-      acci[e] = 0.f;
-    }
-    mo = mn;
-    mi = -INFINITY;
-    li = 0.f;
-  };
-
-  int t = t0;
-  int inner = 0;
-  for (; t + F <= t1; t += F) {
-    uint4 kr[F][NC], vr[F][NC];
-#pragma unroll
-    for (int f = 0; f < F; ++f)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        kr[f][c] = ld_stream(kp + (size_t)(t + f) * fstride + c * 8 * CE);
-        vr[f][c] = ld_stream(vp + (size_t)(t + f) * fstride + c * 8 * CE);
-      }
-    float s[F];
-#pragma unroll
-    for (int f = 0; f < F; ++f) {
-      float acc = 0.f;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        float kf[CE];
-        C::to_float(kr[f][c], kf);
-#pragma unroll
-        for (int i = 0; i < CE; ++i) acc = fmaf(qv[c * CE + i], kf[i], acc);
-      }
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-      s[f] = acc;
-    }
-    float mx = mi;
-#pragma unroll
-    for (int f = 0; f < F; ++f) mx = fmaxf(mx, s[f]);
-    const float al = ex2f(mi - mx);
-    float p[F], psum = 0.f;
-#pragma unroll
-    for (int f = 0; f < F; ++f) {
-      p[f] = ex2f(s[f] - mx);
-      psum += p[f];
-    }
-    li = li * al + psum;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      float vf[F][CE];
-#pragma unroll
-      for (int f = 0; f < F; ++f) C::to_float(vr[f][c], vf[f]);
-#pragma unroll
-      for (int i = 0; i < CE; ++i) {
-        float x = acci[c * CE + i] * al;
-#pragma unroll
-        for (int f = 0; f < F; ++f) x = fmaf(p[f], vf[f][i], x);
-        acci[c * CE + i] = x;
+  if (warp == kConsumerWarps) {
+    // ------------------------------------------------------------ producer
+    if (lane != 0) return;
+    uint32_t G = 0, armed = 0, par = 0;
+    bool ok = true;
+    for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+      const int split = (int)(item % a.splits);
+      const long long rest = item / a.splits;
+      const int mb = (int)(rest % a.mblocks);
+      const int bh = (int)(rest / a.mblocks);
+      const int m0 = mb * kLocPerBlock;
+      const int nval = min(kLocPerBlock, a.M - m0);
+      const uint32_t slab = (uint32_t)(nval * D * (int)sizeof(InT));
+      const int t0 = split * a.chunk, t1 = min(a.S, t0 + a.chunk);
+      const InT* kb = static_cast<const InT*>(a.k) + ((size_t)bh * a.S * a.M + m0) * D;
+      const InT* vb = static_cast<const InT*>(a.v) + ((size_t)bh * a.S * a.M + m0) * D;
+      for (int t = t0; t < t1; t += FR, ++G) {
+        const uint32_t st = G % R::kStages, n = G / R::kStages;
+        if (!(ok = sm103::mbar_wait<set_status_c>(empty + st, (n & 1) ^ 1, abort_flag))) break;
+        const int nf = min(FR, t1 - t);
+        sm103::mbar_arrive_expect_tx(full + st, 2u * nf * slab);
+        armed |= 1u << st;
+        par = (par & ~(1u << st)) | ((n & 1) << st);
+        uint8_t* dst = smem + st * R::kStage;
+        for (int f = 0; f < nf; ++f) {
+          sm103::bulk_load(dst + (2 * f) * R::kSlab, kb + (size_t)(t + f) * fstride, slab, full + st);
+          sm103::bulk_load(dst + (2 * f + 1) * R::kSlab, vb + (size_t)(t + f) * fstride, slab, full + st);
+        }
       }
     }
-    mi = mx;
-    inner += F;
-    if (inner == kInner) {
-      fold();
-      inner = 0;
+    if (!ok) {  // let every copy this thread issued land before the CTA exits
+      for (int s = 0; s < R::kStages; ++s)
+        if (armed & (1u << s)) sm103::mbar_wait<set_status_c>(full + s, (par >> s) & 1, abort_flag, false);
     }
+    return;
   }
-  for (; t < t1; ++t) {  // ragged tail of the frame range
-    uint4 kr[NC], vr[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      kr[c] = ld_stream(kp + (size_t)t * fstride + c * 8 * CE);
-      vr[c] = ld_stream(vp + (size_t)t * fstride + c * 8 * CE);
-    }
-    float acc = 0.f;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      float kf[CE];
-      C::to_float(kr[c], kf);
-#pragma unroll
-      for (int i = 0; i < CE; ++i) acc = fmaf(qv[c * CE + i], kf[i], acc);
-    }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-    const float mx = fmaxf(mi, acc);
-    const float al = ex2f(mi - mx), p = ex2f(acc - mx);
-    li = li * al + p;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      float vf[CE];
-      C::to_float(vr[c], vf);
-#pragma unroll
-      for (int i = 0; i < CE; ++i) acci[c * CE + i] = fmaf(p, vf[i], acci[c * CE + i] * al);
-    }
-    mi = mx;
-  }
-  if (t1 > t0) fold();
-  if (!valid) return;
 
-  const size_t loc = (size_t)bh * a.M + m;
-  if (a.splits == 1) {
-    const float inv = 1.f / lo;
-    OutT* o = static_cast<OutT*>(a.out) + loc * D;
+  // -------------------------------------------------------------- consumers
+  const int sub = lane & 7, grp = lane >> 3;
+  const int lm = warp * 4 + grp;  // location within the block
+  uint32_t G = 0;
+  bool ok = true;
+  for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+    const int split = (int)(item % a.splits);
+    const long long rest = item / a.splits;
+    const int mb = (int)(rest % a.mblocks);
+    const int bh = (int)(rest / a.mblocks);
+    const int h = bh % a.nh;
+    const int m = mb * kLocPerBlock + lm;
+    const bool valid = m < a.M;
+    const int t0 = split * a.chunk, t1 = min(a.S, t0 + a.chunk);
+
+    float qv[E];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
-      for (int i = 0; i < CE; ++i) store_out<OutT>(o + c * 8 * CE + sub * CE + i, acco[c * CE + i] * inv);
-    if (a.lse && sub == 0) a.lse[loc] = (mo + __log2f(lo)) * kLn2;
-  } else {
-    const size_t ploc = (size_t)split * a.BH * a.M + loc;
-    float* w = a.ws_acc + ploc * D;
+      for (int i = 0; i < CE; ++i) qv[c * CE + i] = a.q[(size_t)h * D + c * 8 * CE + sub * CE + i] * a.sl2;
+
+    float mo = -INFINITY, lo = 0.f, acco[E];
+    float mi = -INFINITY, li = 0.f, acci[E];
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
+    for (int e = 0; e < E; ++e) acco[e] = acci[e] = 0.f;
+    auto fold = [&]() {
+      const float mn = fmaxf(mo, mi);
+      const float fa = ex2f(mo - mn), fb = ex2f(mi - mn);
+      lo = lo * fa + li * fb;
 #pragma unroll
-      for (int i = 0; i < CE; ++i) w[c * 8 * CE + sub * CE + i] = acco[c * CE + i];
-    if (sub == 0) {
-      a.ws_ml[2 * ploc] = mo;
-      a.ws_ml[2 * ploc + 1] = lo;
+      for (int e = 0; e < E; ++e) {
+        acco[e] = acco[e] * fa + acci[e] * fb;
+        acci[e] = 0.f;
+      }
+      mo = mn;
+      mi = -INFINITY;
+      li = 0.f;
+    };
+
+    int inner = 0;
+    for (int t = t0; t < t1; t += FR, ++G) {
+      const uint32_t st = G % R::kStages;
+      if (!(ok = sm103::mbar_wait<set_status_c>(full + st, (G / R::kStages) & 1, abort_flag))) break;
+      const int nf = min(FR, t1 - t);
+      const uint8_t* src = smem + st * R::kStage + lm * D * (int)sizeof(InT) + sub * 16;
+      float s[FR];
+      uint4 vr[FR][NC];
+#pragma unroll
+      for (int f = 0; f < FR; ++f) {
+        float acc = 0.f;
+        if (f < nf) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const uint4 kr = *reinterpret_cast<const uint4*>(src + (2 * f) * R::kSlab + c * 128);
+            vr[f][c] = *reinterpret_cast<const uint4*>(src + (2 * f + 1) * R::kSlab + c * 128);
+            float kf[CE];
+            C::to_float(kr, kf);
+#pragma unroll
+            for (int i = 0; i < CE; ++i) acc = fmaf(qv[c * CE + i], kf[i], acc);
+          }
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        s[f] = f < nf ? acc : -INFINITY;
+      }
+      __syncwarp();
+      if (lane == 0) sm103::mbar_arrive(empty + st);
+      float mx = mi;
+#pragma unroll
+      for (int f = 0; f < FR; ++f) mx = fmaxf(mx, s[f]);
+      const float al = ex2f(mi - mx);
+      float p[FR], psum = 0.f;
+#pragma unroll
+      for (int f = 0; f < FR; ++f) {
+        p[f] = f < nf ? ex2f(s[f] - mx) : 0.f;
+        psum += p[f];
+      }
+      li = li * al + psum;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float vf[FR][CE];
+#pragma unroll
+        for (int f = 0; f < FR; ++f) {
+          if (f < nf)
+            C::to_float(vr[f][c], vf[f]);
+          else
+#pragma unroll
+            for (int i = 0; i < CE; ++i) vf[f][i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < CE; ++i) {
+          float x = acci[c * CE + i] * al;
+#pragma unroll
+          for (int f = 0; f < FR; ++f) x = fmaf(p[f], vf[f][i], x);
+          acci[c * CE + i] = x;
+        }
+      }
+      mi = mx;
+      inner += FR;
+      if (inner >= kInner) {
+        fold();
+        inner = 0;
+      }
+    }
+    if (!ok) break;
+    fold();
+    if (!valid) continue;
+
+    const size_t loc = (size_t)bh * a.M + m;
+    if (a.splits == 1) {
+      const float inv = 1.f / lo;
+      OutT* o = static_cast<OutT*>(a.out) + loc * D;
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int i = 0; i < CE; ++i) store_out<OutT>(o + c * 8 * CE + sub * CE + i, acco[c * CE + i] * inv);
+      if (a.lse && sub == 0) a.lse[loc] = (mo + __log2f(lo)) * kLn2;
+    } else {
+      const size_t ploc = (size_t)split * a.BH * a.M + loc;
+      float* w = a.ws_acc + ploc * D;
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int i = 0; i < CE; ++i) w[c * 8 * CE + sub * CE + i] = acco[c * CE + i];
+      if (sub == 0) {
+        a.ws_ml[2 * ploc] = mo;
+        a.ws_ml[2 * ploc + 1] = lo;
+      }
     }
   }
 }
@@ -302,9 +349,18 @@ __global__ void __launch_bounds__(kThreadsC) compress_combine_kernel(const CArgs
 
 template <typename InT, typename OutT, int D>
 cudaError_t launch_t(const CArgs& a, cudaStream_t st) {
+  using R = Ring<InT, D>;
   const long long items = (long long)a.BH * a.mblocks * a.splits;
+  auto kern = compress_kernel<InT, OutT, D>;
+  static bool attr = false;  // per instantiation
+  if (!attr) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, R::kSmem) != cudaSuccess)
+      return cudaErrorInvalidValue;
+    attr = true;
+  }
+  const long long grid = items < kPersistentCtas ? items : kPersistentCtas;
   prof_begin(kKCompress, st);
-  compress_kernel<InT, OutT, D><<<(unsigned)items, kThreadsC, 0, st>>>(a);
+  kern<<<(unsigned)grid, kThreadsT, R::kSmem, st>>>(a);
   cudaError_t e = cudaGetLastError();
   prof_end(kKCompress, st);
   if (e != cudaSuccess || a.splits == 1) return e;

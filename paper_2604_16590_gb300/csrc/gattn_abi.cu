@@ -362,7 +362,7 @@ gattn_status gattn_stream_status(gattn_stream_t stream) {
   if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return GATTN_ERR_CUDA;
   uint32_t words[] = {fetch_status_simt(), fetch_status_merge(), fetch_status_sm103_fwd(), fetch_status_sm103_fwd64(), fetch_status_sm103_bwd(),
                       fetch_status_sm103_bwd64(),
-                      fetch_status_serve()};
+                      fetch_status_serve(), fetch_status_compress()};
   for (uint32_t w : words)
     if (w == ~0u) return GATTN_ERR_CUDA;
   for (uint32_t w : words)

@@ -80,6 +80,7 @@ uint32_t fetch_status_sm103_fwd64();
 uint32_t fetch_status_sm103_bwd();
 uint32_t fetch_status_sm103_bwd64();
 uint32_t fetch_status_serve();
+uint32_t fetch_status_compress();
 
 // ---- per-kernel device timing (gattn_profile_*); no-ops unless enabled
 enum KernelId : int {
