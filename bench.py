@@ -198,7 +198,14 @@ def run_serving(n_requests, rank=0):
     }
 
 
-def run_compress(steps, warmup, dev, rank=0, cpu=True, peaks=None):
+# DRAM bytes (read + write) per launch of the compression kernel from one ncu
+# capture of the 512-frame case (h3_512, 4.295 GB read, 69.5 MB written), reads
+# scaled by frames to the 2048-frame case and writes = its 10 ranges' partials;
+# None once the kernel changes.
+COMPRESS_TRAFFIC_PER_LAUNCH = {"h3_2k": 17.27e9, "h3_512": 4.365e9}
+
+
+def run_compress(steps, warmup, dev, rank=0, cpu=True, peaks=None, workload="h3_2k"):
     """Temporal compression (learned query per head over S history frames per
     location) on the long-temporal-context shape: 2048 frames x 32 x 64
     locations, 8 heads, d = 128, BF16 keys/values (17.2 GB read per call, > L2,
@@ -209,7 +216,7 @@ def run_compress(steps, warmup, dev, rank=0, cpu=True, peaks=None):
     from paper_2604_16590_gb300.inputs import HISTORY_WORKLOADS, history_inputs
     from paper_2604_16590_gb300.replicas import replica_seed
 
-    w = HISTORY_WORKLOADS["h3_2k"]
+    w = HISTORY_WORKLOADS[workload]
     w = type(w)(**{**w.__dict__, "seed": replica_seed(w.seed, rank)})
     q, k, v = history_inputs(w, dev)
     desc = gattn.compress_desc(k)
@@ -250,7 +257,8 @@ def run_compress(steps, warmup, dev, rank=0, cpu=True, peaks=None):
         "workspace_bytes": nws,
         "roofline": {"kernel": "compress", "bound": "hbm", "achieved": alg / (main_ms * 1e-3) / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": alg / (main_ms * 1e-3) / 1e9 / peak,
-                     "peak_source": f"hbm_gbs of {src}", "algorithmic_bytes": alg, "traffic": None},
+                     "peak_source": f"hbm_gbs of {src}", "algorithmic_bytes": alg,
+                     "traffic": COMPRESS_TRAFFIC_PER_LAUNCH.get(workload)},
         "call_gbs": alg / (ms * 1e-3) / 1e9,
     }
     if cpu:
@@ -323,6 +331,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--compress-steps", type=int, default=10,
                     help="timed calls of the temporal compression (0 = skip)")
+    ap.add_argument("--compress-workload", default="h3_2k")
     ap.add_argument("--serve-requests", type=int, default=256,
                     help="requests of the serving run (Poisson 40/s, 20 steps; 0 = skip)")
     args = ap.parse_args()
@@ -369,7 +378,7 @@ def main():
     compress = None
     if args.compress_steps > 0:
         compress = run_compress(args.compress_steps, 3, dev, rank, cpu=rank == 0 and world == 1 and not args.no_cpu,
-                                peaks=measured_peaks())
+                                peaks=measured_peaks(), workload=args.compress_workload)
 
     # ---------------------------------------------------------------- inputs (per rank)
     q, k, v = qkv(w.shape, replicas.replica_seed(w.seed, rank), w.std, "bf16", device=dev)

@@ -90,6 +90,8 @@ class HistoryWorkload:
 HISTORY_WORKLOADS = {
     # the long-temporal-context shape (2048 frames x 32 x 64, 8 heads, d = 128) as history to compress
     "h3_2k": HistoryWorkload("h3_2k", 1, 8, 128, 2048, 32, 64, 0.5, 20266, "bf16"),
+    # the same locations and heads with 512 frames (4.3 GB of keys and values): profiling case
+    "h3_512": HistoryWorkload("h3_512", 1, 8, 128, 512, 32, 64, 0.5, 20266, "bf16"),
     # a long history on a few locations: 131072 frames x 8 x 8, 2 heads, d = 64 (S-long sums)
     "h_128k": HistoryWorkload("h_128k", 1, 2, 64, 131072, 8, 8, 0.5, 20267, "bf16"),
 }
