@@ -288,6 +288,56 @@ def run_compress(steps, warmup, dev, rank=0, cpu=True, peaks=None, workload="h3_
     return res
 
 
+def run_gated(steps, warmup, dev, w, rank=0):
+    """Noise-gated self + cross attention on the bench workload's grid and
+    tiling: two GPA forwards (the cross branch with a separate key/value
+    source, standing in for the compressed temporal representation) and the
+    per-head blend.  Device time from CUDA events on the launching stream."""
+    import torch
+
+    from paper_2604_16590_gb300 import gattn
+    from paper_2604_16590_gb300.inputs import qkv
+    from paper_2604_16590_gb300.replicas import replica_seed
+
+    q, k, v, kc, vc = qkv(w.shape, replica_seed(w.seed + 31, rank), w.std, "bf16", device=dev, n=5)
+    gate = torch.linspace(0.1, 0.9, w.nh, device=dev, dtype=torch.float32)
+    tiling = gattn.Tiling(w.grid, w.core, w.halo)
+    desc = gattn.desc_for(q, tiling, torch.bfloat16)
+    out = torch.empty_like(q)
+    ws = torch.empty(gattn.gattn_gated_workspace_bytes(desc), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def call():
+        gattn.check(gattn.gattn_gated_fwd(desc, q, k, v, kc, vc, gate, out, ws, stream=stream), "gattn_gated_fwd")
+
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    gattn.gattn_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = gattn.gattn_profile_read()
+    gattn.gattn_profile_enable(False)
+    gattn.check(gattn.gattn_stream_status(), "gated status")
+    ms = e0.elapsed_time(e1) / steps
+    mix_ms = prof.get("gated_mix", (steps, 0.0))[1] / steps
+    mix_bytes = 3 * q.numel() * 2 + w.nh * 4
+    res = {
+        "workload": f"{w.name} grid and tiling, self + cross branch (separate BF16 K/V source), per-head gate",
+        "ms_per_call": ms, "calls": steps, "warmup": warmup,
+        "tokens_per_s": w.B * w.N / (ms * 1e-3),
+        "kernels": {n: {"launches": c, "ms_per_launch": t / c} for n, (c, t) in prof.items()},
+        "mix_gbs": mix_bytes / (mix_ms * 1e-3) / 1e9 if mix_ms > 0 else None,
+    }
+    del q, k, v, kc, vc, out, ws
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args, w):
     import torch
 
@@ -332,6 +382,8 @@ def main():
     ap.add_argument("--compress-steps", type=int, default=10,
                     help="timed calls of the temporal compression (0 = skip)")
     ap.add_argument("--compress-workload", default="h3_2k")
+    ap.add_argument("--gated-steps", type=int, default=2,
+                    help="timed calls of the noise-gated self + cross attention (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=256,
                     help="requests of the serving run (Poisson 40/s, 20 steps; 0 = skip)")
     args = ap.parse_args()
@@ -379,6 +431,10 @@ def main():
     if args.compress_steps > 0:
         compress = run_compress(args.compress_steps, 3, dev, rank, cpu=rank == 0 and world == 1 and not args.no_cpu,
                                 peaks=measured_peaks(), workload=args.compress_workload)
+
+    gated = None
+    if args.gated_steps > 0:
+        gated = run_gated(args.gated_steps, 1, dev, w, rank)
 
     # ---------------------------------------------------------------- inputs (per rank)
     q, k, v = qkv(w.shape, replicas.replica_seed(w.seed, rank), w.std, "bf16", device=dev)
@@ -530,6 +586,7 @@ def main():
             "fp32_form": fp32,
             "serve": serve,
             "compress": compress,
+            "gated": gated,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

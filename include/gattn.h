@@ -267,6 +267,29 @@ gattn_status gattn_fwd_noalloc(const gattn_desc *desc, const void *q, const void
                                void *out, gattn_stream_t stream);
 
 /*
+ * Noise-gated self + cross attention (arXiv 2604.16590, Sec. III-B, the
+ * STORM-DiT layer and the noise-gated attention paragraph): each layer runs
+ * spatial self-attention on the current state and cross-attention from the
+ * current state to the compressed temporal representation, and blends them
+ * with a gate set by the diffusion noise level (more weight on the temporal
+ * branch at high noise).  With GPA tiling both branches are tile-local:
+ *
+ *     out = g_h GPA(q, k, v) + (1 - g_h) GPA(q, kc, vc)
+ *
+ * q, k, v from the current state and kc, vc from the temporal representation,
+ * all [B, nh, N, d] in in_dtype on the same grid and tiling (desc); gate [nh]
+ * FP32 on the device (the caller maps sigma_t to g; the paper does not give
+ * the map).  out [B, nh, N, d] in out_dtype.  Forward only.
+ * ws: device workspace of gattn_gated_workspace_bytes(desc) bytes (the
+ * attention saved state, reused by both branches, and the cross branch's
+ * output).  Launches: both GPA forwards, then one blend kernel.
+ */
+size_t gattn_gated_workspace_bytes(const gattn_desc *desc);
+gattn_status gattn_gated_fwd(const gattn_desc *desc, const void *q, const void *k, const void *v,
+                             const void *kc, const void *vc, const float *gate, void *out,
+                             void *ws, size_t ws_bytes, gattn_stream_t stream);
+
+/*
  * Temporal compression (arXiv 2604.16590, Sec. III-B, the STORM-DiT
  * architecture paragraph and Fig. 2(b)): history states are folded into one
  * global temporal representation by cross-attention across the temporal
@@ -333,7 +356,7 @@ gattn_status gattn_stream_status(gattn_stream_t stream);
  */
 typedef struct {
   char name[24];    /* "fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd",
-                       "compress", "compress_combine" */
+                       "compress", "compress_combine", "gated_mix" */
   int64_t launches;
   double total_ms;
 } gattn_kernel_stat;

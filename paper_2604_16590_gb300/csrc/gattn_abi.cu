@@ -14,7 +14,7 @@ namespace gattn {
 // ------------------------------------------------------------ kernel timing
 namespace {
 const char* const kKernelNames[kKCount] = {"fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd",
-                                           "compress", "compress_combine"};
+                                           "compress", "compress_combine", "gated_mix"};
 struct ProfRecord {
   int kernel;
   cudaEvent_t start, stop;
@@ -283,6 +283,39 @@ gattn_status gattn_bwd(const gattn_desc* desc, const void* q, const void* k, con
     e = launch_merge_bwd(g, dq_s, dk_s, dv_s, dq, dk, dv, desc->out_dtype, st);
     prof_end(kKMergeBwd, st);
   }
+  return from_cuda(e);
+}
+
+// Noise-gated self + cross attention (Sec. III-B): the workspace holds the
+// saved state (reused by both attentions; forward only) and the cross output.
+static size_t gated_cross_off(const Geom& g) { return align_up(saved_layout(g).bytes); }
+static size_t out_elem_bytes(int32_t t) { return t == GATTN_BF16 ? 2 : 4; }
+
+size_t gattn_gated_workspace_bytes(const gattn_desc* desc) {
+  Geom g;
+  if (!make_geom(desc, &g)) return 0;
+  return gated_cross_off(g) + align_up((size_t)g.B * g.nh * g.N * g.d * out_elem_bytes(desc->out_dtype));
+}
+
+gattn_status gattn_gated_fwd(const gattn_desc* desc, const void* q, const void* k, const void* v, const void* kc,
+                             const void* vc, const float* gate, void* out, void* ws, size_t ws_bytes,
+                             gattn_stream_t stream) {
+  Geom g;
+  if (!make_geom(desc, &g)) return GATTN_ERR_INVALID_ARG;
+  const void* ptrs[] = {q, k, v, kc, vc, gate, out, ws};
+  for (const void* p : ptrs)
+    if (!p || !aligned16(p)) return GATTN_ERR_INVALID_ARG;
+  if (ws_bytes < gattn_gated_workspace_bytes(desc)) return GATTN_ERR_WORKSPACE;
+  const SavedLayout sl = saved_layout(g);
+  void* cross = static_cast<char*>(ws) + gated_cross_off(g);
+  gattn_status s = gattn_fwd(desc, q, k, v, out, ws, sl.bytes, stream);
+  if (s != GATTN_OK) return s;
+  s = gattn_fwd(desc, q, kc, vc, cross, ws, sl.bytes, stream);
+  if (s != GATTN_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  prof_begin(kKGatedMix, st);
+  const cudaError_t e = launch_gated_mix(g, out, cross, gate, desc->out_dtype, st);
+  prof_end(kKGatedMix, st);
   return from_cuda(e);
 }
 

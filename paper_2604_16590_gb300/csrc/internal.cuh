@@ -84,7 +84,7 @@ uint32_t fetch_status_compress();
 
 // ---- per-kernel device timing (gattn_profile_*); no-ops unless enabled
 enum KernelId : int {
-  kKFwdTiles = 0, kKMergeFwd, kKBwdPrep, kKBwdDkdv, kKBwdDq, kKMergeBwd, kKCompress, kKCompressCombine, kKCount
+  kKFwdTiles = 0, kKMergeFwd, kKBwdPrep, kKBwdDkdv, kKBwdDq, kKMergeBwd, kKCompress, kKCompressCombine, kKGatedMix, kKCount
 };
 void prof_begin(int kernel, cudaStream_t st);
 void prof_end(int kernel, cudaStream_t st);
@@ -113,6 +113,9 @@ cudaError_t launch_simt_bwd(const Geom& g, const float* q, const float* k, const
                             void* dv, int out_dtype, float* dq_s, float* dk_s, float* dv_s,
                             cudaStream_t st);
 cudaError_t launch_merge_fwd(const Geom& g, const float* ot, void* out, int out_dtype, cudaStream_t st);
+// out <- gate[h] * out + (1 - gate[h]) * cross over [B, nh, N, d] (gated.cu)
+cudaError_t launch_gated_mix(const Geom& g, void* out, const void* cross, const float* gate, int out_dtype,
+                             cudaStream_t st);
 cudaError_t launch_bwd_prep(const Geom& g, const void* out, int out_dtype, const void* dout,
                             int in_dtype, const float* lse2, const float* ot, float* lse2c, float* dd,
                             void* ext, cudaStream_t st);

@@ -160,6 +160,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         ),
         "gattn_serve_stats": ([P, ctypes.POINTER(gattn_serve_stats_t)], ctypes.c_int),
         "gattn_serve_destroy": ([P], None),
+        "gattn_gated_workspace_bytes": ([D], S),
+        "gattn_gated_fwd": ([D, P, P, P, P, P, P, P, P, S, P], ctypes.c_int),
         "gattn_compress_workspace_bytes": ([ctypes.POINTER(gattn_compress_desc)], S),
         "gattn_compress_fwd": ([ctypes.POINTER(gattn_compress_desc), P, P, P, P, P, P, S, P], ctypes.c_int),
         "gattn_profile_enable": ([ctypes.c_int32], ctypes.c_int),
@@ -260,6 +262,17 @@ def gattn_fwd_noalloc(desc, q, k, v, out, stream=None) -> int:
 
 def gattn_stream_status(stream=None) -> int:
     return load_library().gattn_stream_status(_stream(stream))
+
+
+def gattn_gated_workspace_bytes(desc) -> int:
+    return load_library().gattn_gated_workspace_bytes(ctypes.byref(desc))
+
+
+def gattn_gated_fwd(desc, q, k, v, kc, vc, gate, out, ws, ws_bytes=None, stream=None) -> int:
+    return load_library().gattn_gated_fwd(
+        ctypes.byref(desc), _ptr(q), _ptr(k), _ptr(v), _ptr(kc), _ptr(vc), _ptr(gate), _ptr(out), _ptr(ws),
+        _nbytes(ws, ws_bytes), _stream(stream),
+    )
 
 
 def gattn_compress_workspace_bytes(desc) -> int:
@@ -487,6 +500,19 @@ class GlobalAttention(torch.autograd.Function):
 
 def global_attention(q, k, v, tiling: Tiling):
     return GlobalAttention.apply(q, k, v, tiling)
+
+
+def gated_forward(q, k, v, kc, vc, gate, tiling: Tiling, out_dtype=None, stream=None):
+    """Noise-gated blend gate[h] * GPA(q, k, v) + (1 - gate[h]) * GPA(q, kc, vc);
+    gate: FP32 CUDA tensor [nh]."""
+    _require_cuda(q, k, v, kc, vc, gate)
+    if gate.dtype != torch.float32 or gate.shape != (q.shape[1],):
+        raise ValueError("gate must be FP32 [heads]")
+    desc = desc_for(q, tiling, out_dtype)
+    out = torch.empty(q.shape, dtype=_TORCH_DTYPE[desc.out_dtype], device=q.device)
+    ws = torch.empty(gattn_gated_workspace_bytes(desc), dtype=torch.uint8, device=q.device)
+    check(gattn_gated_fwd(desc, q, k, v, kc, vc, gate, out, ws, stream=stream), "gattn_gated_fwd")
+    return out
 
 
 # ---------------------------------------------------------------- temporal compression
