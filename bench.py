@@ -338,6 +338,105 @@ def run_gated(steps, warmup, dev, w, rank=0):
     return res
 
 
+def run_dps(steps, warmup, dev, w, rank=0, n_prop=20):
+    """Diffusion posterior sampling with the GPA denoiser (gattn_dps_step).
+
+    (1) Step time on the bench workload's grid and tiling (BF16 attention, FP32
+        state, 25 % of the tokens observed).
+    The synthetic denoiser is GPA(z, z, z) with attention scale 1/d: at
+    1/sqrt(d) a unit-variance state attends almost only to itself and the
+    likelihood gradient through the softmax makes the sampler diverge.
+    (2) Context propagation (Sec. III-C): a 64 x 256 frame cut into 4 x 8 tiles
+        of 16 x 32 with a 4/8-token halo; only the first tile's core is
+        observed.  Two runs share the noise, one with the likelihood term and
+        one without; after every step the farthest tile (Chebyshev distance in
+        tiles) whose state moved by more than 1e-3 of the state's scale is the
+        propagation front.
+    (3) The same sampling with Tiles = 1 (global attention): relative L2
+        distance of the final states of the tiled run with halos, and of a
+        tiled run without halos, to the global run."""
+    import torch
+
+    from paper_2604_16590_gb300 import gattn
+    from paper_2604_16590_gb300.replicas import replica_seed
+
+    # (1) step time at the bench size
+    g = torch.Generator(device=dev)
+    g.manual_seed(replica_seed(w.seed + 57, rank))
+    z = torch.randn(w.shape, generator=g, device=dev) * 0.5
+    y = torch.randn(w.shape, generator=g, device=dev) * 0.5
+    eps = torch.randn(w.shape, generator=g, device=dev)
+    mask = (torch.rand((w.B, w.N), generator=g, device=dev) < 0.25).to(torch.uint8)
+    smp = gattn.PosteriorSampler(z, gattn.Tiling(w.grid, w.core, w.halo, scale=1.0 / w.d), "bf16")
+    sig = gattn.sigma_schedule(steps + warmup, 2.0, 0.05)
+    stream = torch.cuda.current_stream()
+    for i in range(warmup):
+        smp.step(y, mask, eps, sig[i], sig[i + 1], 0.5)
+    torch.cuda.synchronize()
+    gattn.gattn_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(warmup, warmup + steps):
+        smp.step(y, mask, eps, sig[i], sig[i + 1], 0.5)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = gattn.gattn_profile_read()
+    gattn.gattn_profile_enable(False)
+    gattn.check(gattn.gattn_stream_status(), "dps status")
+    ms = e0.elapsed_time(e1) / steps
+    del smp, z, y, eps, mask
+    torch.cuda.empty_cache()
+
+    # (2)-(3) propagation on a 64 x 256 frame, 2 heads, d = 64
+    grid, d, nh = (1, 64, 256), 64, 2
+    N = grid[1] * grid[2]
+    g.manual_seed(replica_seed(20270, rank))
+    z0 = torch.randn((1, nh, N, d), generator=g, device=dev)
+    y = torch.randn((1, nh, N, d), generator=g, device=dev) * 0.5
+    tok = torch.arange(N, device=dev)
+    mask = (((tok // grid[2]) < 16) & ((tok % grid[2]) < 32)).to(torch.uint8)[None]
+    noise = [torch.randn((1, nh, N, d), generator=g, device=dev) for _ in range(n_prop)]
+    sig = gattn.sigma_schedule(n_prop, 2.0, 0.05)
+
+    def run(core, halo, lam, keep=False):
+        smp = gattn.PosteriorSampler(z0.clone(), gattn.Tiling(grid, core, halo, scale=1.0 / d), "bf16")
+        states = []
+        for i in range(n_prop):
+            smp.step(y, mask, noise[i], sig[i], sig[i + 1], lam)
+            if keep:
+                states.append(smp.z.clone())
+        return smp.z.clone(), states
+
+    tiled, halo = (1, 16, 32), (0, 4, 8)
+    _, with_obs = run(tiled, halo, 0.5, keep=True)
+    _, without = run(tiled, halo, 0.0, keep=True)
+    front = []
+    for a, b in zip(with_obs, without):
+        diff = (a - b).abs().amax(dim=(0, 1, 3)).reshape(grid[1] // 16, 16, grid[2] // 32, 32).amax(dim=(1, 3))
+        scale = b.abs().amax()
+        moved = (diff > 1e-3 * scale).nonzero()
+        front.append(int(moved.max(dim=0).values.max()) if moved.numel() else -1)
+    z_glob, _ = run(grid, (0, 0, 0), 0.5)
+    z_halo = with_obs[-1]
+    z_nohalo, _ = run(tiled, (0, 0, 0), 0.5)
+    ref = (z_glob - z0).norm()
+    res = {
+        "workload": f"{w.name} grid and tiling, attention scale 1/d, FP32 state, BF16 attention, 25 % of tokens "
+                    "observed, lam 0.5",
+        "ms_per_step": ms, "steps": steps, "warmup": warmup,
+        "kernels": {n: {"launches": c, "ms_per_launch": t / c} for n, (c, t) in prof.items()},
+        "propagation": {
+            "setup": "64 x 256 frame, 4 x 8 tiles of 16 x 32, halo 4/8, 2 heads, d 64, attention scale 1/d, lam 0.5; "
+                     f"observations in tile (0,0) only; {n_prop} steps, sigma 2.0 -> 0.05",
+            "front_tiles_per_step": front,
+            "rel_dist_to_tiles1_with_halo": float((z_halo - z_glob).norm() / ref),
+            "rel_dist_to_tiles1_without_halo": float((z_nohalo - z_glob).norm() / ref),
+        },
+    }
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args, w):
     import torch
 
@@ -382,6 +481,8 @@ def main():
     ap.add_argument("--compress-steps", type=int, default=10,
                     help="timed calls of the temporal compression (0 = skip)")
     ap.add_argument("--compress-workload", default="h3_2k")
+    ap.add_argument("--dps-steps", type=int, default=2,
+                    help="timed posterior-sampling steps (0 = skip the posterior-sampling leg)")
     ap.add_argument("--gated-steps", type=int, default=2,
                     help="timed calls of the noise-gated self + cross attention (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=256,
@@ -432,6 +533,9 @@ def main():
         compress = run_compress(args.compress_steps, 3, dev, rank, cpu=rank == 0 and world == 1 and not args.no_cpu,
                                 peaks=measured_peaks(), workload=args.compress_workload)
 
+    dps = None
+    if args.dps_steps > 0:
+        dps = run_dps(args.dps_steps, 1, dev, w, rank)
     gated = None
     if args.gated_steps > 0:
         gated = run_gated(args.gated_steps, 1, dev, w, rank)
@@ -587,6 +691,7 @@ def main():
             "serve": serve,
             "compress": compress,
             "gated": gated,
+            "dps": dps,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -267,6 +267,43 @@ gattn_status gattn_fwd_noalloc(const gattn_desc *desc, const void *q, const void
                                void *out, gattn_stream_t stream);
 
 /*
+ * One diffusion posterior-sampling step with the GPA denoiser (arXiv
+ * 2604.16590, Sec. III-A: the reverse SDE, the decomposition of the posterior
+ * score into prior and likelihood scores, the DPS likelihood score, and the
+ * prior score from the denoiser, Eq. denoise; Sec. III-C: the per-step merge
+ * is what propagates context across tiles).  With D(z) = GPA(z, z, z) (a
+ * synthetic one-layer denoiser; heads act as channels) and a token mask H:
+ *
+ *     S      = (D(z) - z) / sigma^2 - lam J_D(z)^T H^T (H D(z) - y)
+ *     z_next = z + delta S + sqrt(delta) eps,   delta = sigma^2 - sigma_next^2
+ *
+ * (Euler-Maruyama step of the variance-exploding reverse SDE; lam folds the
+ * guidance weight zeta_t, the factor 2 and the observation-error variance).
+ *   desc      the GPA problem; out_dtype must be GATTN_FP32 (D and the
+ *             gradients are kept in FP32); in_dtype BF16 runs the tensor-core
+ *             attention on zb, FP32 the plain form on z.
+ *   z         [B, nh, N, d] FP32 state (device), updated in place.
+ *   zb        [B, nh, N, d] BF16 copy of z (device; BF16 form only, else
+ *             ignored): read as the attention input, rewritten as bf16(z_next).
+ *   y         [B, nh, N, d] FP32 observations (read where the mask is set).
+ *   mask      [B, N] uint8, nonzero where a token is observed.
+ *   eps       [B, nh, N, d] FP32 standard normal noise for this step.
+ *   ws        device workspace of gattn_dps_workspace_bytes(desc) bytes.
+ * Launches: the GPA forward, the residual kernel, the GPA backward with
+ * dOut = the residual, the update kernel.
+ */
+typedef struct {
+  float sigma;       /* current noise level (> 0) */
+  float sigma_next;  /* next noise level (0 <= sigma_next <= sigma) */
+  float lam;         /* likelihood guidance weight */
+} gattn_dps_params;
+
+size_t gattn_dps_workspace_bytes(const gattn_desc *desc);
+gattn_status gattn_dps_step(const gattn_desc *desc, const gattn_dps_params *params, float *z, void *zb,
+                            const float *y, const uint8_t *mask, const float *eps, void *ws, size_t ws_bytes,
+                            gattn_stream_t stream);
+
+/*
  * Noise-gated self + cross attention (arXiv 2604.16590, Sec. III-B, the
  * STORM-DiT layer and the noise-gated attention paragraph): each layer runs
  * spatial self-attention on the current state and cross-attention from the
@@ -356,7 +393,7 @@ gattn_status gattn_stream_status(gattn_stream_t stream);
  */
 typedef struct {
   char name[24];    /* "fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd",
-                       "compress", "compress_combine", "gated_mix" */
+                       "compress", "compress_combine", "gated_mix", "dps_residual", "dps_update" */
   int64_t launches;
   double total_ms;
 } gattn_kernel_stat;

@@ -14,7 +14,8 @@ namespace gattn {
 // ------------------------------------------------------------ kernel timing
 namespace {
 const char* const kKernelNames[kKCount] = {"fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd",
-                                           "compress", "compress_combine", "gated_mix"};
+                                           "compress", "compress_combine", "gated_mix", "dps_residual",
+                                           "dps_update"};
 struct ProfRecord {
   int kernel;
   cudaEvent_t start, stop;
@@ -283,6 +284,69 @@ gattn_status gattn_bwd(const gattn_desc* desc, const void* q, const void* k, con
     e = launch_merge_bwd(g, dq_s, dk_s, dv_s, dq, dk, dv, desc->out_dtype, st);
     prof_end(kKMergeBwd, st);
   }
+  return from_cuda(e);
+}
+
+// Posterior-sampling step (Sec. III-A).  Workspace: attention saved state,
+// backward workspace, then D, dq, dk, dv (FP32) and the residual r (in_dtype).
+struct DpsLayout {
+  size_t saved, bws, D, dq, dk, dv, r, bytes;
+};
+static DpsLayout dps_layout(const gattn_desc* desc, const Geom& g) {
+  DpsLayout l;
+  const size_t nd = (size_t)g.B * g.nh * g.N * g.d;
+  l.saved = 0;
+  l.bws = align_up(saved_layout(g).bytes);
+  l.D = l.bws + align_up(bwd_layout(g).bytes);
+  l.dq = l.D + align_up(nd * 4);
+  l.dk = l.dq + align_up(nd * 4);
+  l.dv = l.dk + align_up(nd * 4);
+  l.r = l.dv + align_up(nd * 4);
+  l.bytes = l.r + align_up(nd * (desc->in_dtype == GATTN_BF16 ? 2 : 4));
+  return l;
+}
+
+size_t gattn_dps_workspace_bytes(const gattn_desc* desc) {
+  Geom g;
+  if (!make_geom(desc, &g) || desc->out_dtype != GATTN_FP32) return 0;
+  return dps_layout(desc, g).bytes;
+}
+
+gattn_status gattn_dps_step(const gattn_desc* desc, const gattn_dps_params* p, float* z, void* zb, const float* y,
+                            const uint8_t* mask, const float* eps, void* ws, size_t ws_bytes,
+                            gattn_stream_t stream) {
+  Geom g;
+  if (!make_geom(desc, &g) || desc->out_dtype != GATTN_FP32 || !p) return GATTN_ERR_INVALID_ARG;
+  const bool bf16 = desc->in_dtype == GATTN_BF16;
+  const void* ptrs[] = {z, y, eps, ws};
+  for (const void* q : ptrs)
+    if (!q || !aligned16(q)) return GATTN_ERR_INVALID_ARG;
+  if (!mask || (bf16 && (!zb || !aligned16(zb)))) return GATTN_ERR_INVALID_ARG;
+  if (!(p->sigma > 0.f) || !(p->sigma_next >= 0.f) || !(p->sigma_next <= p->sigma) || !isfinite(p->sigma) ||
+      !isfinite(p->lam))
+    return GATTN_ERR_INVALID_ARG;
+  const DpsLayout l = dps_layout(desc, g);
+  if (ws_bytes < l.bytes) return GATTN_ERR_WORKSPACE;
+  char* w = static_cast<char*>(ws);
+  float* D = reinterpret_cast<float*>(w + l.D);
+  float* dq = reinterpret_cast<float*>(w + l.dq);
+  float* dk = reinterpret_cast<float*>(w + l.dk);
+  float* dv = reinterpret_cast<float*>(w + l.dv);
+  void* r = w + l.r;
+  const void* a = bf16 ? static_cast<const void*>(zb) : static_cast<const void*>(z);
+  const size_t sb = saved_layout(g).bytes, bb = bwd_layout(g).bytes;
+  gattn_status s = gattn_fwd(desc, a, a, a, D, w + l.saved, sb, stream);
+  if (s != GATTN_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  prof_begin(kKDpsResidual, st);
+  cudaError_t e = launch_dps_residual(g, D, y, mask, r, bf16, st);
+  prof_end(kKDpsResidual, st);
+  if (e != cudaSuccess) return GATTN_ERR_CUDA;
+  s = gattn_bwd(desc, a, a, a, D, r, w + l.saved, sb, dq, dk, dv, w + l.bws, bb, stream);
+  if (s != GATTN_OK) return s;
+  prof_begin(kKDpsUpdate, st);
+  e = launch_dps_update(g, z, bf16 ? zb : nullptr, D, dq, dk, dv, eps, p->sigma, p->sigma_next, p->lam, st);
+  prof_end(kKDpsUpdate, st);
   return from_cuda(e);
 }
 

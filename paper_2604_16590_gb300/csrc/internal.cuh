@@ -84,7 +84,7 @@ uint32_t fetch_status_compress();
 
 // ---- per-kernel device timing (gattn_profile_*); no-ops unless enabled
 enum KernelId : int {
-  kKFwdTiles = 0, kKMergeFwd, kKBwdPrep, kKBwdDkdv, kKBwdDq, kKMergeBwd, kKCompress, kKCompressCombine, kKGatedMix, kKCount
+  kKFwdTiles = 0, kKMergeFwd, kKBwdPrep, kKBwdDkdv, kKBwdDq, kKMergeBwd, kKCompress, kKCompressCombine, kKGatedMix, kKDpsResidual, kKDpsUpdate, kKCount
 };
 void prof_begin(int kernel, cudaStream_t st);
 void prof_end(int kernel, cudaStream_t st);
@@ -113,6 +113,12 @@ cudaError_t launch_simt_bwd(const Geom& g, const float* q, const float* k, const
                             void* dv, int out_dtype, float* dq_s, float* dk_s, float* dv_s,
                             cudaStream_t st);
 cudaError_t launch_merge_fwd(const Geom& g, const float* ot, void* out, int out_dtype, cudaStream_t st);
+// posterior-sampling step, elementwise parts (dps.cu)
+cudaError_t launch_dps_residual(const Geom& g, const float* D, const float* y, const uint8_t* mask, void* r,
+                                bool r_bf16, cudaStream_t st);
+cudaError_t launch_dps_update(const Geom& g, float* z, void* zb, const float* D, const float* dq, const float* dk,
+                              const float* dv, const float* eps, float sigma, float sigma_next, float lam,
+                              cudaStream_t st);
 // out <- gate[h] * out + (1 - gate[h]) * cross over [B, nh, N, d] (gated.cu)
 cudaError_t launch_gated_mix(const Geom& g, void* out, const void* cross, const float* gate, int out_dtype,
                              cudaStream_t st);

@@ -111,6 +111,10 @@ class gattn_desc(ctypes.Structure):
     ]
 
 
+class gattn_dps_params(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_float), ("sigma_next", ctypes.c_float), ("lam", ctypes.c_float)]
+
+
 class gattn_compress_desc(ctypes.Structure):
     _fields_ = [
         ("B", ctypes.c_int32),
@@ -160,6 +164,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         ),
         "gattn_serve_stats": ([P, ctypes.POINTER(gattn_serve_stats_t)], ctypes.c_int),
         "gattn_serve_destroy": ([P], None),
+        "gattn_dps_workspace_bytes": ([D], S),
+        "gattn_dps_step": ([D, ctypes.POINTER(gattn_dps_params), P, P, P, P, P, P, S, P], ctypes.c_int),
         "gattn_gated_workspace_bytes": ([D], S),
         "gattn_gated_fwd": ([D, P, P, P, P, P, P, P, P, S, P], ctypes.c_int),
         "gattn_compress_workspace_bytes": ([ctypes.POINTER(gattn_compress_desc)], S),
@@ -262,6 +268,17 @@ def gattn_fwd_noalloc(desc, q, k, v, out, stream=None) -> int:
 
 def gattn_stream_status(stream=None) -> int:
     return load_library().gattn_stream_status(_stream(stream))
+
+
+def gattn_dps_workspace_bytes(desc) -> int:
+    return load_library().gattn_dps_workspace_bytes(ctypes.byref(desc))
+
+
+def gattn_dps_step(desc, params, z, zb, y, mask, eps, ws, ws_bytes=None, stream=None) -> int:
+    return load_library().gattn_dps_step(
+        ctypes.byref(desc), ctypes.byref(params), _ptr(z), _ptr(zb), _ptr(y), _ptr(mask), _ptr(eps), _ptr(ws),
+        _nbytes(ws, ws_bytes), _stream(stream),
+    )
 
 
 def gattn_gated_workspace_bytes(desc) -> int:
@@ -546,3 +563,36 @@ def compress_forward(q, k, v, scale: float = 0.0, out_dtype=None, with_lse: bool
     ws = torch.empty(nws, dtype=torch.uint8, device=k.device) if nws else None
     check(gattn_compress_fwd(desc, q, k, v, out, lse, ws, stream=stream), "gattn_compress_fwd")
     return out, lse
+
+
+# ---------------------------------------------------------------- posterior sampling
+def sigma_schedule(n: int, sigma_max: float = 2.0, sigma_min: float = 0.02, rho: float = 7.0):
+    """n + 1 decreasing noise levels, sigma_max ... sigma_min, then 0 (the
+    rho-spaced schedule of Karras et al. 2022, whose diffusion model the paper
+    uses)."""
+    out = []
+    for i in range(n):
+        f = i / max(n - 1, 1)
+        out.append((sigma_max ** (1 / rho) + f * (sigma_min ** (1 / rho) - sigma_max ** (1 / rho))) ** rho)
+    return out + [0.0]
+
+
+class PosteriorSampler:
+    """Diffusion posterior sampling with the GPA denoiser (one gattn_dps_step
+    per noise level).  z: FP32 CUDA state [B, nh, N, d]; attention in
+    ``attn_dtype`` ("bf16": tensor-core form on a BF16 copy of z, "fp32")."""
+
+    def __init__(self, z, tiling: Tiling, attn_dtype="bf16"):
+        _require_cuda(z)
+        if z.dtype != torch.float32:
+            raise ValueError("the state is FP32")
+        self.z = z
+        self.zb = z.to(torch.bfloat16) if attn_dtype == "bf16" else None
+        self.desc = desc_for(self.zb if self.zb is not None else z, tiling, torch.float32)
+        self.ws = torch.empty(gattn_dps_workspace_bytes(self.desc), dtype=torch.uint8, device=z.device)
+
+    def step(self, y, mask, eps, sigma, sigma_next, lam, stream=None):
+        p = gattn_dps_params()
+        p.sigma, p.sigma_next, p.lam = float(sigma), float(sigma_next), float(lam)
+        check(gattn_dps_step(self.desc, p, self.z, self.zb, y, mask, eps, self.ws, stream=stream), "gattn_dps_step")
+        return self.z
