@@ -1,0 +1,61 @@
+"""FP64 CPU oracle of factorised (kernelised) linear attention.
+
+TEST INFRASTRUCTURE ONLY (same rule as the rest of ``oracle/``).
+
+This operator is not in the paper: it is the example of a linear-complexity
+global attention that the build's objective names (keys and values over all
+N tokens reduced into a fixed-size per-head summary and normaliser that every
+query then reads).  The feature map is not given there either; the reading
+taken is phi(x) = elu(x) + 1 (Katharopoulos et al., 2020, "Transformers are
+RNNs"), which is positive, so the normaliser never vanishes.  Per (b, h):
+
+    S      = sum_n phi(k_n) v_n^T          (d x d summary)
+    z      = sum_n phi(k_n)                (d normaliser)
+    out_i  = phi(q_i)^T S / (phi(q_i)^T z)
+
+The definition written out in that order (numpy float64); ``brute`` is the
+O(N^2) form with explicit weights w_ij = phi(q_i) . phi(k_j).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def phi(x) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(x > 0, x + 1.0, np.exp(np.minimum(x, 0.0)))
+
+
+def summary(k, v):
+    """(S [B, nh, d, d], z [B, nh, d]) from k, v [B, nh, N, d]."""
+    fk = phi(k)
+    S = np.einsum("bhnk,bhnv->bhkv", fk, np.asarray(v, dtype=np.float64))
+    z = fk.sum(axis=2)
+    return S, z
+
+
+def forward(q, k, v) -> np.ndarray:
+    """out [B, nh, N, d], float64."""
+    S, z = summary(k, v)
+    fq = phi(q)
+    num = np.einsum("bhnk,bhkv->bhnv", fq, S)
+    den = np.einsum("bhnk,bhk->bhn", fq, z)
+    return num / den[..., None]
+
+
+def forward_rows(q, k, v, rows, S=None, z=None):
+    """out at sampled (b, h, i) rows, [n, d]; S, z may be passed (from summary)."""
+    if S is None or z is None:
+        S, z = summary(k, v)
+    rows = np.asarray(rows, dtype=np.int64).reshape(-1, 3)
+    out = np.empty((rows.shape[0], S.shape[-1]))
+    for r, (b, h, i) in enumerate(rows):
+        fq = phi(q[b, h, i])
+        out[r] = (fq @ S[b, h]) / (fq @ z[b, h])
+    return out
+
+
+def brute(q, k, v) -> np.ndarray:
+    """O(N^2) evaluation: w_ij = phi(q_i) . phi(k_j); out_i = sum_j w_ij v_j / sum_j w_ij."""
+    w = np.einsum("bhid,bhjd->bhij", phi(q), phi(k))
+    return np.einsum("bhij,bhjd->bhid", w, np.asarray(v, dtype=np.float64)) / w.sum(axis=-1)[..., None]
