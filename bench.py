@@ -437,6 +437,55 @@ def run_dps(steps, warmup, dev, w, rank=0, n_prop=20):
     return res
 
 
+def run_linear(steps, warmup, dev, w, rank=0, peaks=None):
+    """Factorised linear attention (phi = elu + 1; not an operator of the paper)
+    on the bench workload's shape: B x heads x N tokens x d = 64, BF16 Q, K, V
+    N(0, 0.5) (4 x 2.15 GB moved per call, > L2, no flush)."""
+    import torch
+
+    from paper_2604_16590_gb300 import gattn
+    from paper_2604_16590_gb300.inputs import qkv
+    from paper_2604_16590_gb300.replicas import replica_seed
+
+    q, k, v = qkv(w.shape, replica_seed(w.seed + 91, rank), w.std, "bf16", device=dev)
+    desc = gattn.linear_desc(q)
+    out = torch.empty_like(q)
+    ws = torch.empty(gattn.gattn_linear_workspace_bytes(desc), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def call():
+        gattn.check(gattn.gattn_linear_fwd(desc, q, k, v, out, ws, stream=stream), "gattn_linear_fwd")
+
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    gattn.gattn_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = gattn.gattn_profile_read()
+    gattn.gattn_profile_enable(False)
+    gattn.check(gattn.gattn_stream_status(), "linear status")
+    ms = e0.elapsed_time(e1) / steps
+    alg = 4 * q.numel() * 2  # q, k, v read once, out written once
+    peak, src = (peaks[0], peaks[3]) if peaks else (6800.0, "fallback")
+    gbs = alg / (ms * 1e-3) / 1e9
+    res = {
+        "workload": f"{w.name} shape: B={w.B}, {w.nh} heads, N={w.N}, d={w.d}, BF16, phi = elu + 1",
+        "ms_per_call": ms, "calls": steps, "warmup": warmup, "tokens_per_s": w.B * w.N / (ms * 1e-3),
+        "kernels": {n: {"launches": c, "ms_per_launch": t / c} for n, (c, t) in prof.items()},
+        "roofline": {"kernel": "linear (summary + combine + query)", "bound": "hbm", "achieved": gbs, "peak": peak,
+                     "unit": "GB/s", "frac": gbs / peak, "peak_source": f"hbm_gbs of {src}",
+                     "algorithmic_bytes": alg, "traffic": None},
+    }
+    del q, k, v, out, ws
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args, w):
     import torch
 
@@ -481,6 +530,8 @@ def main():
     ap.add_argument("--compress-steps", type=int, default=10,
                     help="timed calls of the temporal compression (0 = skip)")
     ap.add_argument("--compress-workload", default="h3_2k")
+    ap.add_argument("--linear-steps", type=int, default=10,
+                    help="timed calls of the factorised linear attention (0 = skip)")
     ap.add_argument("--dps-steps", type=int, default=2,
                     help="timed posterior-sampling steps (0 = skip the posterior-sampling leg)")
     ap.add_argument("--gated-steps", type=int, default=2,
@@ -533,6 +584,9 @@ def main():
         compress = run_compress(args.compress_steps, 3, dev, rank, cpu=rank == 0 and world == 1 and not args.no_cpu,
                                 peaks=measured_peaks(), workload=args.compress_workload)
 
+    linear = None
+    if args.linear_steps > 0:
+        linear = run_linear(args.linear_steps, 3, dev, w, rank, peaks=measured_peaks())
     dps = None
     if args.dps_steps > 0:
         dps = run_dps(args.dps_steps, 1, dev, w, rank)
@@ -692,6 +746,7 @@ def main():
             "compress": compress,
             "gated": gated,
             "dps": dps,
+            "linear": linear,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

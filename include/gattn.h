@@ -267,6 +267,34 @@ gattn_status gattn_fwd_noalloc(const gattn_desc *desc, const void *q, const void
                                void *out, gattn_stream_t stream);
 
 /*
+ * Factorised linear attention.  Not an operator of the paper (its global
+ * attention is the tiled operator above): the example of a linear-complexity
+ * global attention in which keys and values over all N tokens are reduced
+ * into a fixed-size per-head summary and normaliser that every query reads.
+ * Feature map phi(x) = elu(x) + 1 (Katharopoulos et al., 2020):
+ *
+ *     S = sum_n phi(k_n) v_n^T,   z = sum_n phi(k_n),
+ *     out_i = phi(q_i)^T S / (phi(q_i)^T z).
+ *
+ * q, k, v, out: [B, nh, N, d] BF16 (device), d = 64, N < 2^31.  ws: device
+ * workspace of gattn_linear_workspace_bytes(desc) bytes (per-chunk FP32
+ * partial summaries, the combined summary).  Launches: a split-N summary
+ * kernel (TMA tiles, phi in shared memory, S accumulated by tcgen05 in TMEM,
+ * z in FP32 registers), a fixed-order compensated combine of the chunk
+ * partials, and a query pass (tcgen05 phi(Q) S with S split into BF16 high
+ * and low parts, FP32 denominator).  Deterministic.  Forward only.
+ */
+typedef struct {
+  int32_t B, nh, d;
+  int64_t N;
+  int32_t in_dtype, out_dtype;  /* GATTN_BF16 */
+} gattn_linear_desc;
+
+size_t gattn_linear_workspace_bytes(const gattn_linear_desc *desc);
+gattn_status gattn_linear_fwd(const gattn_linear_desc *desc, const void *q, const void *k, const void *v,
+                              void *out, void *ws, size_t ws_bytes, gattn_stream_t stream);
+
+/*
  * One diffusion posterior-sampling step with the GPA denoiser (arXiv
  * 2604.16590, Sec. III-A: the reverse SDE, the decomposition of the posterior
  * score into prior and likelihood scores, the DPS likelihood score, and the
@@ -393,7 +421,8 @@ gattn_status gattn_stream_status(gattn_stream_t stream);
  */
 typedef struct {
   char name[24];    /* "fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd",
-                       "compress", "compress_combine", "gated_mix", "dps_residual", "dps_update" */
+                       "compress", "compress_combine", "gated_mix", "dps_residual", "dps_update",
+                       "linear_summary", "linear_combine", "linear_query" */
   int64_t launches;
   double total_ms;
 } gattn_kernel_stat;

@@ -15,7 +15,7 @@ namespace gattn {
 namespace {
 const char* const kKernelNames[kKCount] = {"fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd",
                                            "compress", "compress_combine", "gated_mix", "dps_residual",
-                                           "dps_update"};
+                                           "dps_update", "linear_summary", "linear_combine", "linear_query"};
 struct ProfRecord {
   int kernel;
   cudaEvent_t start, stop;
@@ -287,6 +287,27 @@ gattn_status gattn_bwd(const gattn_desc* desc, const void* q, const void* k, con
   return from_cuda(e);
 }
 
+// Factorised linear attention (not an operator of the paper; see linear.cu).
+static bool linear_desc_ok(const gattn_linear_desc* l) {
+  return l && l->B >= 1 && l->nh >= 1 && l->d == 64 && l->N >= 1 && l->N < (1LL << 31) &&
+         l->in_dtype == GATTN_BF16 && l->out_dtype == GATTN_BF16 && (double)l->B * l->nh < 65536.0;
+}
+
+size_t gattn_linear_workspace_bytes(const gattn_linear_desc* l) {
+  if (!linear_desc_ok(l)) return 0;
+  return linear_ws_bytes(l->B, l->nh, l->N);
+}
+
+gattn_status gattn_linear_fwd(const gattn_linear_desc* l, const void* q, const void* k, const void* v, void* out,
+                              void* ws, size_t ws_bytes, gattn_stream_t stream) {
+  if (!linear_desc_ok(l)) return GATTN_ERR_INVALID_ARG;
+  const void* ptrs[] = {q, k, v, out, ws};
+  for (const void* p : ptrs)
+    if (!p || !aligned16(p)) return GATTN_ERR_INVALID_ARG;
+  if (ws_bytes < linear_ws_bytes(l->B, l->nh, l->N)) return GATTN_ERR_WORKSPACE;
+  return from_cuda(launch_linear(q, k, v, out, ws, l->B, l->nh, l->N, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 // Posterior-sampling step (Sec. III-A).  Workspace: attention saved state,
 // backward workspace, then D, dq, dk, dv (FP32) and the residual r (in_dtype).
 struct DpsLayout {
@@ -459,7 +480,7 @@ gattn_status gattn_stream_status(gattn_stream_t stream) {
   if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return GATTN_ERR_CUDA;
   uint32_t words[] = {fetch_status_simt(), fetch_status_merge(), fetch_status_sm103_fwd(), fetch_status_sm103_fwd64(), fetch_status_sm103_bwd(),
                       fetch_status_sm103_bwd64(),
-                      fetch_status_serve(), fetch_status_compress()};
+                      fetch_status_serve(), fetch_status_compress(), fetch_status_linear()};
   for (uint32_t w : words)
     if (w == ~0u) return GATTN_ERR_CUDA;
   for (uint32_t w : words)

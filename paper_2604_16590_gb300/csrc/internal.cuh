@@ -81,10 +81,12 @@ uint32_t fetch_status_sm103_bwd();
 uint32_t fetch_status_sm103_bwd64();
 uint32_t fetch_status_serve();
 uint32_t fetch_status_compress();
+uint32_t fetch_status_linear();
 
 // ---- per-kernel device timing (gattn_profile_*); no-ops unless enabled
 enum KernelId : int {
-  kKFwdTiles = 0, kKMergeFwd, kKBwdPrep, kKBwdDkdv, kKBwdDq, kKMergeBwd, kKCompress, kKCompressCombine, kKGatedMix, kKDpsResidual, kKDpsUpdate, kKCount
+  kKFwdTiles = 0, kKMergeFwd, kKBwdPrep, kKBwdDkdv, kKBwdDq, kKMergeBwd, kKCompress, kKCompressCombine, kKGatedMix, kKDpsResidual, kKDpsUpdate, kKLinearSummary, kKLinearCombine,
+  kKLinearQuery, kKCount
 };
 void prof_begin(int kernel, cudaStream_t st);
 void prof_end(int kernel, cudaStream_t st);
@@ -113,6 +115,15 @@ cudaError_t launch_simt_bwd(const Geom& g, const float* q, const float* k, const
                             void* dv, int out_dtype, float* dq_s, float* dk_s, float* dv_s,
                             cudaStream_t st);
 cudaError_t launch_merge_fwd(const Geom& g, const float* ot, void* out, int out_dtype, cudaStream_t st);
+// factorised linear attention (linear.cu): split-N summary over chunks of
+// 128-token tiles, fixed-order combine, query pass; BF16, d = 64.
+struct LinearPlan {
+  int ntiles, chunk_tiles, chunks, q_tiles_per_cta;
+};
+LinearPlan linear_plan(int B, int nh, int64_t N);
+size_t linear_ws_bytes(int B, int nh, int64_t N);
+cudaError_t launch_linear(const void* q, const void* k, const void* v, void* out, void* ws, int B, int nh, int64_t N,
+                          cudaStream_t st);
 // posterior-sampling step, elementwise parts (dps.cu)
 cudaError_t launch_dps_residual(const Geom& g, const float* D, const float* y, const uint8_t* mask, void* r,
                                 bool r_bf16, cudaStream_t st);

@@ -111,6 +111,17 @@ class gattn_desc(ctypes.Structure):
     ]
 
 
+class gattn_linear_desc(ctypes.Structure):
+    _fields_ = [
+        ("B", ctypes.c_int32),
+        ("nh", ctypes.c_int32),
+        ("d", ctypes.c_int32),
+        ("N", ctypes.c_int64),
+        ("in_dtype", ctypes.c_int32),
+        ("out_dtype", ctypes.c_int32),
+    ]
+
+
 class gattn_dps_params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_float), ("sigma_next", ctypes.c_float), ("lam", ctypes.c_float)]
 
@@ -164,6 +175,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         ),
         "gattn_serve_stats": ([P, ctypes.POINTER(gattn_serve_stats_t)], ctypes.c_int),
         "gattn_serve_destroy": ([P], None),
+        "gattn_linear_workspace_bytes": ([ctypes.POINTER(gattn_linear_desc)], S),
+        "gattn_linear_fwd": ([ctypes.POINTER(gattn_linear_desc), P, P, P, P, P, S, P], ctypes.c_int),
         "gattn_dps_workspace_bytes": ([D], S),
         "gattn_dps_step": ([D, ctypes.POINTER(gattn_dps_params), P, P, P, P, P, P, S, P], ctypes.c_int),
         "gattn_gated_workspace_bytes": ([D], S),
@@ -268,6 +281,36 @@ def gattn_fwd_noalloc(desc, q, k, v, out, stream=None) -> int:
 
 def gattn_stream_status(stream=None) -> int:
     return load_library().gattn_stream_status(_stream(stream))
+
+
+def gattn_linear_workspace_bytes(desc) -> int:
+    return load_library().gattn_linear_workspace_bytes(ctypes.byref(desc))
+
+
+def gattn_linear_fwd(desc, q, k, v, out, ws, ws_bytes=None, stream=None) -> int:
+    return load_library().gattn_linear_fwd(
+        ctypes.byref(desc), _ptr(q), _ptr(k), _ptr(v), _ptr(out), _ptr(ws), _nbytes(ws, ws_bytes), _stream(stream)
+    )
+
+
+def linear_desc(q):
+    B, nh, N, d = q.shape
+    desc = gattn_linear_desc()
+    desc.B, desc.nh, desc.d, desc.N = int(B), int(nh), int(d), int(N)
+    desc.in_dtype = desc.out_dtype = _DTYPES[q.dtype]
+    return desc
+
+
+def linear_forward(q, k, v, stream=None):
+    """Factorised linear attention (phi = elu + 1) of BF16 [B, heads, N, 64] tensors."""
+    _require_cuda(q, k, v)
+    if not (q.shape == k.shape == v.shape) or q.dtype != torch.bfloat16:
+        raise ValueError("q, k, v must be BF16 tensors of one shape [B, heads, N, 64]")
+    desc = linear_desc(q)
+    out = torch.empty_like(q)
+    ws = torch.empty(gattn_linear_workspace_bytes(desc), dtype=torch.uint8, device=q.device)
+    check(gattn_linear_fwd(desc, q, k, v, out, ws, stream=stream), "gattn_linear_fwd")
+    return out
 
 
 def gattn_dps_workspace_bytes(desc) -> int:
