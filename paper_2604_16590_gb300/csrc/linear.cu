@@ -269,7 +269,7 @@ struct QArgs {
 
 constexpr int kThreadsQ = 224;  // producer, issuer, 4 math warps, storer
 
-__global__ void __launch_bounds__(kThreadsQ) la_query_kernel(const __grid_constant__ CUtensorMap tq,
+__global__ void __launch_bounds__(kThreadsQ, 3) la_query_kernel(const __grid_constant__ CUtensorMap tq,
                                                              const __grid_constant__ CUtensorMap to, const QArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
