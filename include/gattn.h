@@ -56,7 +56,7 @@ typedef struct CUstream_st *gattn_stream_t;
 typedef enum {
   GATTN_OK = 0,
   GATTN_ERR_INVALID_ARG = 1,   /* NULL pointer, bad shape, misaligned pointer */
-  GATTN_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  GATTN_ERR_UNSUPPORTED = 2,   /* valid request this library does not implement */
   GATTN_ERR_WORKSPACE = 3,     /* saved/workspace buffer smaller than required */
   GATTN_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed */
   GATTN_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
@@ -268,7 +268,7 @@ gattn_status gattn_fwd_noalloc(const gattn_desc *desc, const void *q, const void
 
 /*
  * Factorised linear attention.  Not an operator of the paper (its global
- * attention is the tiled operator above): the example of a linear-complexity
+ * attention is the tiled operator above): the textbook linear-complexity
  * global attention in which keys and values over all N tokens are reduced
  * into a fixed-size per-head summary and normaliser that every query reads.
  * Feature map phi(x) = elu(x) + 1 (Katharopoulos et al., 2020):

@@ -2,12 +2,12 @@
 
 TEST INFRASTRUCTURE ONLY (same rule as the rest of ``oracle/``).
 
-This operator is not in the paper: it is the example of a linear-complexity
-global attention that the build's objective names (keys and values over all
-N tokens reduced into a fixed-size per-head summary and normaliser that every
-query then reads).  The feature map is not given there either; the reading
-taken is phi(x) = elu(x) + 1 (Katharopoulos et al., 2020, "Transformers are
-RNNs"), which is positive, so the normaliser never vanishes.  Per (b, h):
+This operator is not in the paper (whose global attention is the tiled GPA
+operator): it is the textbook linear-complexity global attention in which keys
+and values over all N tokens are reduced into a fixed-size per-head summary
+and normaliser that every query then reads.  The feature map is taken as
+phi(x) = elu(x) + 1 (Katharopoulos et al., 2020, "Transformers are RNNs"),
+which is positive, so the normaliser never vanishes.  Per (b, h):
 
     S      = sum_n phi(k_n) v_n^T          (d x d summary)
     z      = sum_n phi(k_n)                (d normaliser)

@@ -3,10 +3,10 @@
 //     S = sum_n phi(k_n) v_n^T (d x d),  z = sum_n phi(k_n),
 //     out_i = phi(q_i)^T S / (phi(q_i)^T z).
 //
-// Not an operator of the paper (whose global attention is the tiled GPA); it
-// is the example of a linear-complexity global attention with a fixed-size
-// per-head summary that the build's objective names.  The feature map is the
-// one of Katharopoulos et al. (2020).  BF16 inputs, d = 64.
+// Not an operator of the paper (whose global attention is the tiled GPA): the
+// textbook linear-complexity global attention with a fixed-size per-head
+// summary and normaliser.  The feature map is the one of Katharopoulos et al.
+// (2020).  BF16 inputs, d = 64.
 //
 // Three kernels, all HBM-bound:
 //   la_summary_kernel  split-N summary: each CTA streams a chunk of 128-token
