@@ -13,8 +13,17 @@ which is positive, so the normaliser never vanishes.  Per (b, h):
     z      = sum_n phi(k_n)                (d normaliser)
     out_i  = phi(q_i)^T S / (phi(q_i)^T z)
 
-The definition written out in that order (numpy float64); ``brute`` is the
-O(N^2) form with explicit weights w_ij = phi(q_i) . phi(k_j).
+and, for a loss with upstream gradient g_i = dL/dout_i (den_i = phi(q_i) . z):
+
+    dphi(q_i) = (S g_i - z (g_i . out_i)) / den_i,      dq_i = dphi(q_i) * phi'(q_i)
+    dS        = sum_i phi(q_i) (g_i / den_i)^T           (query-side gradient summary)
+    dz        = -sum_i phi(q_i) (g_i . out_i) / den_i
+    dphi(k_n) = dS v_n + dz,                             dk_n = dphi(k_n) * phi'(k_n)
+    dv_n      = dS^T phi(k_n)
+
+with phi'(x) = 1 for x > 0 and exp(x) otherwise.  The definition written out
+in that order (numpy float64); ``brute`` is the O(N^2) form with explicit
+weights w_ij = phi(q_i) . phi(k_j).
 """
 from __future__ import annotations
 
@@ -41,6 +50,27 @@ def forward(q, k, v) -> np.ndarray:
     num = np.einsum("bhnk,bhkv->bhnv", fq, S)
     den = np.einsum("bhnk,bhk->bhn", fq, z)
     return num / den[..., None]
+
+
+def dphi(x) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(x > 0, 1.0, np.exp(np.minimum(x, 0.0)))
+
+
+def backward(q, k, v, g):
+    """(dq, dk, dv) of the loss sum(out * g), float64."""
+    q, k, v, g = (np.asarray(t, dtype=np.float64) for t in (q, k, v, g))
+    S, z = summary(k, v)
+    fq, fk = phi(q), phi(k)
+    den = np.einsum("bhnk,bhk->bhn", fq, z)
+    out = np.einsum("bhnk,bhkv->bhnv", fq, S) / den[..., None]
+    go = np.einsum("bhnv,bhnv->bhn", g, out)
+    dfq = (np.einsum("bhkv,bhnv->bhnk", S, g) - z[:, :, None, :] * go[..., None]) / den[..., None]
+    dS = np.einsum("bhnk,bhnv->bhkv", fq, g / den[..., None])
+    dz = -np.einsum("bhnk,bhn->bhk", fq, go / den)
+    dfk = np.einsum("bhkv,bhnv->bhnk", dS, v) + dz[:, :, None, :]
+    dv = np.einsum("bhkv,bhnk->bhnv", dS, fk)
+    return dfq * dphi(q), dfk * dphi(k), dv
 
 
 def forward_rows(q, k, v, rows, S=None, z=None):

@@ -70,3 +70,36 @@ def test_forward_rows_matches_forward():
     got = ol.forward_rows(q, k, v, rows)
     for i, (b, h, n) in enumerate(rows):
         np.testing.assert_allclose(got[i], out[b, h, n], rtol=0, atol=1e-14)
+
+
+def test_backward_matches_torch_autograd_of_the_quadratic_form():
+    """Autograd through the O(N^2) form with torch's elu: an independent route."""
+    q, k, v = _qkv((2, 2, 40, 8), 7)
+    g = np.random.default_rng(8).standard_normal(q.shape)
+    dq, dk, dv = ol.backward(q, k, v, g)
+    tq, tk, tv = (torch.from_numpy(a).requires_grad_() for a in (q, k, v))
+    fq = torch.nn.functional.elu(tq) + 1
+    fk = torch.nn.functional.elu(tk) + 1
+    w = torch.einsum("bhid,bhjd->bhij", fq, fk)
+    out = torch.einsum("bhij,bhjd->bhid", w, tv) / w.sum(-1, keepdim=True)
+    (out * torch.from_numpy(g)).sum().backward()
+    np.testing.assert_allclose(dq, tq.grad.numpy(), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(dk, tk.grad.numpy(), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(dv, tv.grad.numpy(), rtol=1e-10, atol=1e-12)
+
+
+def test_backward_matches_finite_differences():
+    q, k, v = _qkv((1, 1, 12, 4), 9)
+    g = np.random.default_rng(10).standard_normal(q.shape)
+    grads = ol.backward(q, k, v, g)
+    h = 1e-6
+    for arr, grad in zip((q, k, v), grads):
+        flat, gf = arr.reshape(-1), grad.reshape(-1)
+        for i in range(0, flat.size, 5):
+            old = flat[i]
+            flat[i] = old + h
+            lp = float((ol.forward(q, k, v) * g).sum())
+            flat[i] = old - h
+            lm = float((ol.forward(q, k, v) * g).sum())
+            flat[i] = old
+            assert abs((lp - lm) / (2 * h) - gf[i]) < 1e-7
