@@ -113,3 +113,36 @@ def test_compress_validation_on_the_host(lib):
     # null or misaligned pointers
     assert gattn.gattn_compress_fwd(e, None, 16, 16, 16, None, None, stream=0) == 1
     assert gattn.gattn_compress_fwd(e, 16, 24, 16, 16, None, None, stream=0) == 1
+
+
+def test_gated_dps_linear_sizes_and_validation_on_the_host(lib):
+    """Workspace queries and argument checks of the gated, posterior-sampling
+    and linear-attention entry points, without a GPU."""
+    d = _desc()
+    saved = gattn.gattn_saved_bytes(d)
+    nd = 2 * 3 * 4 * 16 * 32 * 64
+    # gated: saved state (reused by both branches) + the cross branch's output
+    assert gattn.gattn_gated_workspace_bytes(d) >= saved + nd * 2
+    assert gattn.gattn_gated_fwd(d, None, 16, 16, 16, 16, 16, 16, 16, ws_bytes=1 << 30, stream=0) == 1
+    # posterior sampling needs FP32 outputs (D and the gradients)
+    assert gattn.gattn_dps_workspace_bytes(d) == 0
+    d32 = _desc(out_dtype="fp32")
+    need = gattn.gattn_dps_workspace_bytes(d32)
+    assert need >= saved + gattn.gattn_bwd_workspace_bytes(d32) + 4 * nd * 4 + nd * 2
+    p = gattn.gattn_dps_params()
+    p.sigma, p.sigma_next, p.lam = 1.0, 0.5, 1.0
+    assert gattn.gattn_dps_step(d32, p, None, 16, 16, 16, 16, 16, ws_bytes=need, stream=0) == 1
+    p.sigma_next = 2.0  # noise must not grow
+    assert gattn.gattn_dps_step(d32, p, 16, 16, 16, 16, 16, 16, ws_bytes=need, stream=0) == 1
+    # linear attention: BF16, d = 64 only; workspace grows with the chunks
+    ld = gattn.gattn_linear_desc()
+    ld.B, ld.nh, ld.d, ld.N, ld.in_dtype, ld.out_dtype = 1, 2, 64, 4096, gattn.GATTN_BF16, gattn.GATTN_BF16
+    small = gattn.gattn_linear_workspace_bytes(ld)
+    assert small >= 2 * 64 * 64 * 4
+    ld.N = 1 << 20
+    assert gattn.gattn_linear_workspace_bytes(ld) > small
+    ld.d = 128
+    assert gattn.gattn_linear_workspace_bytes(ld) == 0
+    assert gattn.gattn_linear_fwd(ld, 16, 16, 16, 16, 16, ws_bytes=1 << 30, stream=0) == 1
+    ld.d, ld.N = 64, 0
+    assert gattn.gattn_linear_fwd(ld, 16, 16, 16, 16, 16, ws_bytes=1 << 30, stream=0) == 1
