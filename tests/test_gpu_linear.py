@@ -16,8 +16,8 @@ from tests._parity import assert_close
 
 pytestmark = pytest.mark.gpu
 
-CASES = [("one_partial_tile", 1, 1, 100), ("ragged", 2, 3, 1000), ("n4096", 1, 1, 4096),
-         ("many_chunks", 1, 2, 65536 + 77)]
+CASES = [("one_partial_tile", 1, 1, 100), ("three_tiles_two_heads", 1, 2, 300), ("ragged", 2, 3, 1000),
+         ("n4096", 1, 1, 4096), ("many_chunks", 1, 2, 65536 + 77)]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
