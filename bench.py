@@ -31,12 +31,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "global-attn fwd+bwd Gtokens/s & HBM-roofline %, BF16 vs FP32; serve p50/p99"
 UNIT = "Gtokens/s"
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
-# from the ncu capture summarised in profiles/ (None until captured for the
-# kernel as built now).
-# dkdv64: 1535.0 MB in one ncu capture of the same geometry with 1/16 of the
-# (batch*head) units, times 16 (the units are independent)
-TRAFFIC_PER_LAUNCH = {"bwd_dkdv": 24.56e9}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a leg's dominant
+# kernel, from the ncu captures summarised in profiles/; None for a kernel
+# that changed since its counters were taken.
+TRAFFIC_PER_LAUNCH = {}
+# MUFU ex2 results per clock per SM (measured on GB300 with a micro-benchmark:
+# 32 per clock, i.e. 8 per SM sub-partition), the exponential-unit peak of the
+# attainable-time bound.
+EX2_PER_CLK_SM = 32
 
 
 def _extents(G, c, h):
@@ -51,17 +53,40 @@ def sum_L2(w):
     return out
 
 
-def kernel_flops(w):
-    """Algorithmic FLOPs per launch of each tile kernel (all batch*heads)."""
-    s = sum_L2(w) * w.B * w.nh * w.d
-    return {"fwd_tiles": 4 * s, "bwd_dkdv": 8 * s, "bwd_dq": 6 * s}
-
-
 def sum_L(w):
     out = 1
     for a in range(3):
         out *= sum(_extents(w.grid[a], w.core[a], w.halo[a]))
     return out
+
+
+def padded_pairs(w, box):
+    """Query-key pairs the tensor-core kernels execute per (batch, head): every
+    tile is cut into prod_a ceil(e_a / b_a) boxes of one 128-row MMA block
+    each, and all (query block, key block) pairs of a tile are computed."""
+    out = 128 * 128
+    for a in range(3):
+        out *= sum((-(-e // box[a])) ** 2 for e in _extents(w.grid[a], w.core[a], w.halo[a]))
+    return out
+
+
+def gpa_work(w, box):
+    """Algorithmic and executed work of one fwd+bwd step, whole batch.
+
+    Algorithmic (the method's own work): forward 4 d sum L^2 FLOP (S = Q K^T,
+    P V); backward 8 d sum L^2 (dV = P^T dO, dP = dO V^T, dK = dS^T Q in the
+    dK/dV kernel, dQ = dS K in the dQ kernel).  Executed: the MMA FLOPs the
+    kernels issue over padded 128-row blocks, including the recomputed S (dK/dV
+    kernel) and S, dP (dQ kernel) and, at d = 64, the K = 16 statistics step
+    of each score chain of the dK/dV kernel.  Exponentials: sum L^2 forward, 2
+    sum L^2 backward (P and its recompute)."""
+    bh, d = w.B * w.nh, w.d
+    L2, P = sum_L2(w) * bh, padded_pairs(w, box) * bh
+    stats = 2 * 2 * 16 * P if d == 64 else 0
+    alg = {"fwd_tiles": 4 * d * L2, "bwd_dkdv": 6 * d * L2, "bwd_dq": 2 * d * L2}
+    exe = {"fwd_tiles": 4 * d * P, "bwd_dkdv": 8 * d * P + stats, "bwd_dq": 6 * d * P}
+    return {"alg_flops": alg, "exec_flops": exe, "step_alg_flops": 12 * d * L2, "step_exps": 3 * L2,
+            "sum_L2": L2, "padded_pairs": P}
 
 
 def algorithmic_bytes(w, in_bytes=2, out_bytes=2):
@@ -74,6 +99,18 @@ def algorithmic_bytes(w, in_bytes=2, out_bytes=2):
     fwd = 3 * nd * in_bytes + nd * out_bytes + lse
     bwd = 4 * nd * in_bytes + nd * out_bytes + lse + 3 * nd * out_bytes
     return fwd + bwd
+
+
+def workload_config(w, world):
+    """The `config` object of both arms' JSON lines for a GPA workload."""
+    tiles = 1
+    for a in range(3):
+        tiles *= -(-w.grid[a] // w.core[a])
+    gb = w.B * w.nh * w.N * w.d * 2 / 1e9
+    return {"workload": w.name, "B": w.B, "heads": w.nh, "d": w.d, "grid": list(w.grid), "core": list(w.core),
+            "halo": list(w.halo), "tiles": tiles, "tokens_per_step": w.B * w.N * world, "in_dtype": "bf16",
+            "out_dtype": "bf16", "l2": f"inputs {3 * gb:.1f} GB per rank > L2, no flush",
+            "parallelism": f"replicas x{world} (independent batch*head units, no collective)"}
 
 
 def measured_peaks():
@@ -138,31 +175,46 @@ class ClockSampler:
 
 
 def oracle_sample(w, q, k, v, go, target_s=12.0):
-    """Time the FP64 oracle (as it stands) on a bounded sample: query rows of
-    one (batch*head, tile) unit, forward + backward.  Returns (Gtokens/s
-    extrapolated to the whole step, threads, description)."""
+    """Time the FP64 oracle (as it stands) on a bounded sample of one
+    (batch*head) slice, forward + backward: query rows of the largest tile, or
+    whole tiles in turn when one tile is quicker than the target.  Returns
+    (Gtokens/s extrapolated to the whole step by (query, key) pairs, threads,
+    description, seconds)."""
     import numpy as np
 
     import oracle
 
     geo = oracle.Geometry(1, 1, w.d, *w.grid, w.core, w.halo)
     f64 = [np.ascontiguousarray(t[0, 0].double().cpu().numpy())[None, None] for t in (q, k, v, go)]
-    # the largest tile: the middle one
     nt = geo.num_tiles()
     tile = max(range(nt), key=geo.tile_rows)
     L = geo.tile_rows(tile)
     t0 = time.perf_counter()
-    oracle.unit_fwd_bwd(geo, *f64, 0, tile, 0, 64)
+    oracle.unit_fwd_bwd(geo, *f64, 0, tile, 0, min(64, L))
     t64 = time.perf_counter() - t0
-    R = int(min(L, max(64, 64 * target_s / max(t64, 1e-6))))
-    t0 = time.perf_counter()
-    oracle.unit_fwd_bwd(geo, *f64, 0, tile, 0, R)
-    tR = time.perf_counter() - t0
+    if L > 64 and t64 * L / 64 > target_s:
+        # part of the largest tile: R query rows against all its L keys
+        R = int(min(L, max(64, 64 * target_s / max(t64, 1e-6))))
+        t0 = time.perf_counter()
+        oracle.unit_fwd_bwd(geo, *f64, 0, tile, 0, R)
+        tR = time.perf_counter() - t0
+        pairs, what = R * L, f"{R} query rows x {L} keys of one (batch*head, tile) unit"
+    else:
+        # whole tiles, in index order, until the target time is spent
+        pairs, n, tR = 0, 0, 0.0
+        while tR < target_s and n < nt:
+            Lt = geo.tile_rows(n)
+            t0 = time.perf_counter()
+            oracle.unit_fwd_bwd(geo, *f64, 0, n, 0, Lt)
+            tR += time.perf_counter() - t0
+            pairs += Lt * Lt
+            n += 1
+        what = f"{n} whole tiles ({pairs:.3e} query-key pairs) of one batch*head slice"
     pairs_total = sum_L2(w) * w.B * w.nh
-    step_s = tR * pairs_total / (R * L)
+    step_s = tR * pairs_total / pairs
     gtok = w.B * w.N / step_s / 1e9
-    desc = (f"{R} query rows x {L} keys of one (batch*head, tile) unit, forward + backward, "
-            f"{tR:.1f} s; scaled by (query, key) pairs to the full step ({pairs_total:.3e} pairs)")
+    desc = (f"{what}, forward + backward, {tR:.1f} s; scaled by (query, key) pairs to the full step "
+            f"({pairs_total:.3e} pairs)")
     return gtok, oracle.threads(), desc, tR
 
 
@@ -486,119 +538,29 @@ def run_linear(steps, warmup, dev, w, rank=0, peaks=None):
     return res
 
 
-def run_reference(args, w):
+def run_gpa(w, steps, warmup, dev, rank, world, peaks, cpu=True, e2e_steps=1, fp32_steps=0, clocks=False,
+            barrier=None):
+    """One GPA workload: `steps` timed fwd+bwd steps (gattn_fwd + gattn_bwd
+    through the C ABI) after `warmup` untimed ones, inputs device-resident
+    (larger than L2, no flush).  Reports the step time (max over ranks), the
+    per-kernel device times (CUDA events on the launch stream), the roofline of
+    the dominant kernel on its algorithmic FLOPs, the step's fraction of its
+    attainable time max(bytes / HBM, FLOPs / tensor peak, exps / exp-unit
+    peak), an end-to-end time with pinned host buffers (H2D of Q, K, V, dOut
+    and D2H of Out, dQ, dK, dV inside the timed region), the plain FP32 form
+    on the same values (fp32_steps > 0) and the oracle on a bounded sample."""
     import torch
 
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    # the oracle sample reads one (batch, head) slice: draw just that slice
+    from paper_2604_16590_gb300 import gattn, replicas
     from paper_2604_16590_gb300.inputs import qkv, upstream_grad
 
-    shape1 = (1, 1, w.N, w.d)
-    q, k, v = qkv(shape1, w.seed, w.std, w.dtype)
-    go = upstream_grad(shape1, w.seed, w.dtype)
-    vals, secs = [], []
-    for _ in range(args.warmup):
-        oracle_sample(w, q, k, v, go, target_s=2.0)
-    for _ in range(args.steps):
-        g, cores, desc, t = oracle_sample(w, q, k, v, go, target_s=8.0)
-        vals.append(g)
-        secs.append(t)
-    value = statistics.median(vals)
-    print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "B": w.B, "heads": w.nh, "d": w.d, "grid": list(w.grid),
-                   "core": list(w.core), "halo": list(w.halo)},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }), flush=True)
-    del torch
-
-
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gattn", choices=["gattn", "reference"])
-    ap.add_argument("--workload", default="c2_262k_p")
-    ap.add_argument("--fp32-steps", type=int, default=1, help="timed steps of the plain FP32 form (0 = skip)")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--compress-steps", type=int, default=10,
-                    help="timed calls of the temporal compression (0 = skip)")
-    ap.add_argument("--compress-workload", default="h3_2k")
-    ap.add_argument("--linear-steps", type=int, default=10,
-                    help="timed calls of the factorised linear attention (0 = skip)")
-    ap.add_argument("--dps-steps", type=int, default=2,
-                    help="timed posterior-sampling steps (0 = skip the posterior-sampling leg)")
-    ap.add_argument("--gated-steps", type=int, default=2,
-                    help="timed calls of the noise-gated self + cross attention (0 = skip)")
-    ap.add_argument("--serve-requests", type=int, default=256,
-                    help="requests of the serving run (Poisson 40/s, 20 steps; 0 = skip)")
-    args = ap.parse_args()
-
-    from paper_2604_16590_gb300.inputs import WORKLOADS
-
-    w = WORKLOADS[args.workload]
-    if args.impl == "reference":
-        run_reference(args, w)
-        return
-
-    import torch
-    import torch.distributed as dist
-
-    from paper_2604_16590_gb300 import build, gattn, replicas
-    from paper_2604_16590_gb300.inputs import qkv, upstream_grad
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    build.build()
-    gattn.load_library()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    # ---------------------------------------------------------------- serving: continuous batching (rank-local),
-    # run first so that its HBM budget does not compete with the step buffers
-    serve = None
-    if args.serve_requests > 0:
-        serve = run_serving(args.serve_requests, rank)
-        if world > 1:
-            t_srv = replicas.max_over_ranks(serve["wall_s"], device=dev)
-            serve["token_steps_per_s_all_ranks"] = replicas.sum_over_ranks(serve["token_steps"], device=dev) / t_srv
-
-    # ---------------------------------------------------------------- temporal compression (rank-local)
-    compress = None
-    if args.compress_steps > 0:
-        compress = run_compress(args.compress_steps, 3, dev, rank, cpu=rank == 0 and world == 1 and not args.no_cpu,
-                                peaks=measured_peaks(), workload=args.compress_workload)
-
-    linear = None
-    if args.linear_steps > 0:
-        linear = run_linear(args.linear_steps, 3, dev, w, rank, peaks=measured_peaks())
-    dps = None
-    if args.dps_steps > 0:
-        dps = run_dps(args.dps_steps, 1, dev, w, rank)
-    gated = None
-    if args.gated_steps > 0:
-        gated = run_gated(args.gated_steps, 1, dev, w, rank)
-
-    # ---------------------------------------------------------------- inputs (per rank)
+    barrier = barrier or (lambda: None)
     q, k, v = qkv(w.shape, replicas.replica_seed(w.seed, rank), w.std, "bf16", device=dev)
     go = upstream_grad(w.shape, replicas.replica_seed(w.seed, rank), "bf16", device=dev)
     tiling = gattn.Tiling(w.grid, w.core, w.halo)
     desc = gattn.desc_for(q, tiling, torch.bfloat16)
+    st_box, box = gattn.gattn_block_shape(desc)
+    gattn.check(st_box, "gattn_block_shape")
     out = torch.empty_like(q)
     dq, dk, dv = torch.empty_like(q), torch.empty_like(q), torch.empty_like(q)
     saved = torch.empty(gattn.gattn_saved_bytes(desc), dtype=torch.uint8, device=dev)
@@ -609,91 +571,111 @@ def main():
         gattn.check(gattn.gattn_fwd(d, qq, kk, vv, o, sv, stream=stream), "gattn_fwd")
         gattn.check(gattn.gattn_bwd(d, qq, kk, vv, o, gg, sv, a, b, c, wsp, stream=stream), "gattn_bwd")
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     st = gattn.gattn_stream_status(stream)
     if st != 0:
-        raise RuntimeError(f"device status after warm-up: {gattn.STATUS.get(st, st)}")
+        raise RuntimeError(f"{w.name}: device status after warm-up: {gattn.STATUS.get(st, st)}")
 
-    # ---------------------------------------------------------------- timed region (device-resident inputs)
-    clocks = ClockSampler(local)
-    time.sleep(0.3)
+    # ---- timed region (device-resident inputs)
+    sampler = ClockSampler(dev.index or 0) if clocks else None
+    if sampler:
+        time.sleep(0.3)
     gattn.gattn_profile_enable(True)
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    clk = clocks.stop()
+    clk = sampler.stop() if sampler else None
     kstats = gattn.gattn_profile_read()
     gattn.gattn_profile_enable(False)
     st = gattn.gattn_stream_status(stream)
     if st != 0:
-        raise RuntimeError(f"device status after timed steps: {gattn.STATUS.get(st, st)}")
-    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
-    tokens_per_step = w.B * w.N * world
+        raise RuntimeError(f"{w.name}: device status after timed steps: {gattn.STATUS.get(st, st)}")
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / steps, device=dev)
     value = replicas.weak_scaling_value(w.B * w.N, world, ms * 1e-3) / 1e9
-    launches = sum(n for n, _ in kstats.values())
 
-    # ---------------------------------------------------------------- roofline of the dominant kernel
-    hbm_peak, tc_peak, tc_sust, peak_src = measured_peaks()
-    flops = kernel_flops(w)
+    # ---- roofline: dominant kernel on its algorithmic FLOPs; the step against its attainable time
+    hbm_peak, tc_peak, tc_sust, peak_src = peaks
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = measured_sm_max_mhz()
+    ex2_peak = EX2_PER_CLK_SM * n_sms * sm_mhz * 1e6
+    work = gpa_work(w, box)
     kernels = {}
     for name, (n, tot) in kstats.items():
         per = tot / n
-        ent = {"launches": n, "ms_per_launch": per, "share": tot / (ms * args.steps)}
-        if name in flops:
-            ent["tflops"] = flops[name] / (per * 1e-3) / 1e12
+        ent = {"launches": n, "ms_per_launch": per, "share": tot / (ms * steps)}
+        if name in work["alg_flops"]:
+            ent["alg_tflops"] = work["alg_flops"][name] / (per * 1e-3) / 1e12
+            ent["exec_tflops"] = work["exec_flops"][name] / (per * 1e-3) / 1e12
+            ent["frac_of_sustained"] = ent["alg_tflops"] / tc_sust
         kernels[name] = ent
     dom = max(kstats, key=lambda nm: kstats[nm][1])
     dom_ms = kstats[dom][1] / kstats[dom][0]
-    achieved = flops.get(dom, 0) / (dom_ms * 1e-3) / 1e12
+    achieved = work["alg_flops"].get(dom, 0) / (dom_ms * 1e-3) / 1e12
     roofline = {
         "kernel": dom, "bound": "tensor", "achieved": achieved, "peak": tc_sust, "unit": "TFLOP/s",
         "frac": achieved / tc_sust, "peak_source": f"bf16_tflops_sustained of {peak_src}",
-        "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+        "traffic": TRAFFIC_PER_LAUNCH.get((w.name, dom)),
+        "algorithmic_flops": work["alg_flops"].get(dom), "executed_flops": work["exec_flops"].get(dom),
+        "executed_tflops": work["exec_flops"].get(dom, 0) / (dom_ms * 1e-3) / 1e12,
     }
     alg_bytes = algorithmic_bytes(w)
+    t_bytes = alg_bytes / (hbm_peak * 1e9)
+    t_flops = work["step_alg_flops"] / (tc_sust * 1e12)
+    t_exps = work["step_exps"] / ex2_peak
+    t_att = max(t_bytes, t_flops, t_exps)
+    attainable = {
+        "ms": 1e3 * t_att, "bound": ("hbm", "tensor", "exp")[[t_bytes, t_flops, t_exps].index(t_att)],
+        "ms_hbm": 1e3 * t_bytes, "ms_tensor": 1e3 * t_flops, "ms_exp": 1e3 * t_exps,
+        "frac_of_attainable": t_att / (ms * 1e-3),
+        "step_alg_flops": work["step_alg_flops"], "step_exec_flops": sum(work["exec_flops"].values()),
+        "executed_over_algorithmic": sum(work["exec_flops"].values()) / work["step_alg_flops"],
+        "padding": work["padded_pairs"] / work["sum_L2"], "block_shape": list(box),
+        "exp_peak": f"{EX2_PER_CLK_SM} ex2/clk/SM x {n_sms} SMs x {sm_mhz:.0f} MHz",
+    }
     hbm = {"algorithmic_bytes_per_step": alg_bytes, "gbs": alg_bytes / (ms * 1e-3) / 1e9,
            "frac_of_hbm": alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, "peak_gbs": hbm_peak, "peak_source": peak_src}
 
-    # ---------------------------------------------------------------- e2e through the public API with host buffers
-    host_in = [torch.empty(w.shape, dtype=torch.bfloat16, pin_memory=True) for _ in range(4)]
-    for h, t in zip(host_in, (q, k, v, go)):
-        h.copy_(t)
-    host_out = [torch.empty(w.shape, dtype=torch.bfloat16, pin_memory=True) for _ in range(4)]
-    dq_in, dk_in, dv_in, dgo_in = (torch.empty_like(q) for _ in range(4))
-    e2e_steps = max(1, min(args.steps, 3))
+    # ---- e2e through the public API with host buffers
+    e2e = None
+    if e2e_steps > 0:
+        host_in = [torch.empty(w.shape, dtype=torch.bfloat16, pin_memory=True) for _ in range(4)]
+        for h, t in zip(host_in, (q, k, v, go)):
+            h.copy_(t)
+        host_out = [torch.empty(w.shape, dtype=torch.bfloat16, pin_memory=True) for _ in range(4)]
 
-    def e2e_step():
-        for d_, h_ in zip((dq_in, dk_in, dv_in, dgo_in), host_in):
-            d_.copy_(h_, non_blocking=True)
-        step(qq=dq_in, kk=dk_in, vv=dv_in, gg=dgo_in)
-        for h_, d_ in zip(host_out, (out, dq, dk, dv)):
-            h_.copy_(d_, non_blocking=True)
+        def e2e_step():
+            for d_, h_ in zip((q, k, v, go), host_in):
+                d_.copy_(h_, non_blocking=True)
+            step()
+            for h_, d_ in zip(host_out, (out, dq, dk, dv)):
+                h_.copy_(d_, non_blocking=True)
 
-    e2e_step()
-    torch.cuda.synchronize()
-    barrier()
-    e2 = torch.cuda.Event(enable_timing=True)
-    e3 = torch.cuda.Event(enable_timing=True)
-    e2.record(stream)
-    for _ in range(e2e_steps):
         e2e_step()
-    e3.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = replicas.max_over_ranks(e2.elapsed_time(e3) / e2e_steps, device=dev)
-    bytes_io = 4 * q.numel() * q.element_size()
-    del dq_in, dk_in, dv_in, dgo_in, host_in, host_out
+        torch.cuda.synchronize()
+        barrier()
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        e3.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = replicas.max_over_ranks(e2.elapsed_time(e3) / e2e_steps, device=dev)
+        bytes_io = 4 * q.numel() * q.element_size()
+        e2e = {"value": w.B * w.N * world / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
+               "steps": e2e_steps, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io}
+        del host_in, host_out
 
-    # ---------------------------------------------------------------- the plain FP32 form on the same values
+    # ---- the plain FP32 form on the same values
     fp32 = None
-    if args.fp32_steps > 0:
+    if fp32_steps > 0:
         q32, k32, v32, g32 = (t.float() for t in (q, k, v, go))
         d32 = gattn.desc_for(q32, tiling, torch.float32)
         o32 = torch.empty_like(q32)
@@ -708,46 +690,231 @@ def main():
         torch.cuda.synchronize()
         e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e4.record(stream)
-        for _ in range(args.fp32_steps):
+        for _ in range(fp32_steps):
             step32()
         e5.record(stream)
         torch.cuda.synchronize()
-        ms32 = e4.elapsed_time(e5) / args.fp32_steps
+        ms32 = e4.elapsed_time(e5) / fp32_steps
         fp32 = {"value": w.B * w.N * world / (ms32 * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms32,
-                "steps": args.fp32_steps, "bf16_speedup": ms32 / ms}
+                "steps": fp32_steps, "bf16_speedup": ms32 / ms}
         del q32, k32, v32, g32, o32, a32, b32, c32, sv32, ws32
 
-    # ---------------------------------------------------------------- CPU oracle baseline (rank 0, N = 1)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    # ---- the oracle as it stands on a bounded sample (rank 0, N = 1)
+    cpu_res = None
+    if cpu and rank == 0 and world == 1:
         sl = (slice(0, 1), slice(0, 1))
         g, cores, desc_s, _ = oracle_sample(w, q[sl].cpu(), k[sl].cpu(), v[sl].cpu(), go[sl].cpu())
-        cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc_s}
+        cpu_res = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc_s}
+
+    res = {"workload": w.name, "config": workload_config(w, world), "value": value, "unit": UNIT,
+           "ms_per_step": ms, "steps": steps, "warmup": warmup, "roofline": roofline, "attainable": attainable,
+           "hbm": hbm, "kernels": kernels, "gpu_launches": sum(n for n, _ in kstats.values()), "e2e": e2e,
+           "fp32_form": fp32, "cpu_baseline": cpu_res, "clocks": clk}
+    del q, k, v, go, out, dq, dk, dv, saved, ws
+    torch.cuda.empty_cache()
+    return res
+
+
+def measured_sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
+def world_size(args):
+    """Ranks of this run: WORLD_SIZE under torchrun, else 1."""
+    return int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def self_launch(args):
+    """`--gpus N` (N > 1) without torchrun: start N ranks of this script under
+    torch.distributed.run (one process per GPU, rendezvous on 127.0.0.1) and
+    return their exit status; rank 0 prints the JSON line."""
+    import socket
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
+def run_reference(args, w):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on a
+    bounded sample of the same workload, scaled to one step (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    if world_size(args) > 1:
+        # torchrun pins every rank to one OpenMP thread; rank 0 alone runs the
+        # oracle here, on all host cores
+        os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
+    # the oracle sample reads one (batch, head) slice: draw just that slice
+    from paper_2604_16590_gb300.inputs import qkv, upstream_grad
+
+    shape1 = (1, 1, w.N, w.d)
+    q, k, v = qkv(shape1, w.seed, w.std, w.dtype)
+    go = upstream_grad(shape1, w.seed, w.dtype)
+    vals, secs = [], []
+    for _ in range(args.warmup):
+        oracle_sample(w, q, k, v, go, target_s=2.0)
+    for _ in range(args.steps):
+        g, cores, desc, t = oracle_sample(w, q, k, v, go, target_s=8.0)
+        vals.append(g)
+        secs.append(t)
+    value = statistics.median(vals)
+    world = world_size(args)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * w.B * w.N * world / (value * 1e9),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(w, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_dry(args):
+    """--dry-run: start the ranks (gloo, no GPU work) and have rank 0 print the
+    world size it sees; checks the multi-rank launch path on a CPU machine."""
+    import torch.distributed as dist
+
+    world, rank = world_size(args), int(os.environ.get("RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+        from paper_2604_16590_gb300 import replicas
+
+        ranks = replicas.sum_over_ranks(1.0)
+        dist.destroy_process_group()
+    else:
+        ranks = 1.0
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_gpus": world, "ranks_seen": int(ranks), "gpus_arg": args.gpus}),
+              flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gattn", choices=["gattn", "reference"])
+    ap.add_argument("--workload", default="c2_262k_p")
+    ap.add_argument("--legs", default="c2_262k_s,c4_1m_p,c3_4m_p",
+                    help="other GPA workloads timed as extra legs (comma list, '' = none)")
+    ap.add_argument("--leg-steps", type=int, default=0,
+                    help="timed steps of each extra leg (0 = by size: 10 below 0.1 s per step, else 2, C3 1)")
+    ap.add_argument("--fp32-steps", type=int, default=1, help="timed steps of the plain FP32 form (0 = skip)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baselines")
+    ap.add_argument("--compress-steps", type=int, default=10,
+                    help="timed calls of the temporal compression (0 = skip)")
+    ap.add_argument("--compress-workload", default="h3_2k")
+    ap.add_argument("--linear-steps", type=int, default=10,
+                    help="timed calls of the factorised linear attention (0 = skip)")
+    ap.add_argument("--dps-steps", type=int, default=2,
+                    help="timed posterior-sampling steps (0 = skip the posterior-sampling leg)")
+    ap.add_argument("--gated-steps", type=int, default=2,
+                    help="timed calls of the noise-gated self + cross attention (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=256,
+                    help="requests of the serving run (Poisson 40/s, 20 steps; 0 = skip)")
+    ap.add_argument("--dry-run", action="store_true", help="launch the ranks and report the world size only")
+    args = ap.parse_args()
+
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(self_launch(args))
+    if args.dry_run:
+        run_dry(args)
+        return
+
+    from paper_2604_16590_gb300.inputs import WORKLOADS
+
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2604_16590_gb300 import build, gattn, replicas
+
+    world = world_size(args)
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build()
+    gattn.load_library()
+    peaks = measured_peaks()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---------------------------------------------------------------- serving: continuous batching (rank-local),
+    # run first so that its HBM budget does not compete with the step buffers
+    serve = None
+    if args.serve_requests > 0:
+        serve = run_serving(args.serve_requests, rank)
+        if world > 1:
+            t_srv = replicas.max_over_ranks(serve["wall_s"], device=dev)
+            serve["token_steps_per_s_all_ranks"] = replicas.sum_over_ranks(serve["token_steps"], device=dev) / t_srv
+
+    # ---------------------------------------------------------------- other GPA workloads (each its own leg)
+    legs = {}
+    for name in [x for x in args.legs.split(",") if x]:
+        lw = WORKLOADS[name]
+        n = args.leg_steps or (1 if lw.name.startswith("c3") else 10 if lw.name.endswith("_s") else 2)
+        legs[name] = run_gpa(lw, n, 1, dev, rank, world, peaks, cpu=not args.no_cpu, e2e_steps=1,
+                             fp32_steps=0, barrier=barrier)
+
+    # ---------------------------------------------------------------- temporal compression (rank-local)
+    compress = None
+    if args.compress_steps > 0:
+        compress = run_compress(args.compress_steps, 3, dev, rank, cpu=rank == 0 and world == 1 and not args.no_cpu,
+                                peaks=peaks, workload=args.compress_workload)
+    linear = None
+    if args.linear_steps > 0:
+        linear = run_linear(args.linear_steps, 3, dev, w, rank, peaks=peaks)
+    dps = None
+    if args.dps_steps > 0:
+        dps = run_dps(args.dps_steps, 1, dev, w, rank)
+    gated = None
+    if args.gated_steps > 0:
+        gated = run_gated(args.gated_steps, 1, dev, w, rank)
+
+    # ---------------------------------------------------------------- the headline workload
+    head = run_gpa(w, args.steps, args.warmup, dev, rank, world, peaks, cpu=not args.no_cpu,
+                   e2e_steps=max(1, min(args.steps, 3)), fp32_steps=args.fp32_steps, clocks=True, barrier=barrier)
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": w.name, "B": w.B, "heads": w.nh, "d": w.d, "grid": list(w.grid),
-                       "core": list(w.core), "halo": list(w.halo), "tiles": gattn.gattn_num_tiles(desc),
-                       "tokens_per_step": tokens_per_step, "in_dtype": "bf16", "out_dtype": "bf16",
-                       "l2": "inputs 6.4 GB per rank > L2, no flush",
-                       "parallelism": f"replicas x{world} (independent batch*head units, no collective)"},
-            "clocks": clk,
-            "e2e": {"value": w.B * w.N * world / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
-            "gpu_launches": launches,
-            "roofline": roofline,
-            "hbm": hbm,
-            "kernels": kernels,
-            "fp32_form": fp32,
+            "config": head["config"],
+            "clocks": head["clocks"],
+            "e2e": head["e2e"],
+            "gpu_launches": head["gpu_launches"],
+            "roofline": head["roofline"],
+            "attainable": head["attainable"],
+            "hbm": head["hbm"],
+            "kernels": head["kernels"],
+            "fp32_form": head["fp32_form"],
+            "legs": legs,
             "serve": serve,
             "compress": compress,
             "gated": gated,
             "dps": dps,
             "linear": linear,
-            "cpu_baseline": cpu,
+            "cpu_baseline": head["cpu_baseline"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -59,3 +59,21 @@ def test_two_gloo_ranks_aggregate_like_the_benchmark():
 def test_single_process_reductions_are_identity():
     assert replicas.max_over_ranks(3.5) == 3.5
     assert replicas.sum_over_ranks(7.0) == 7.0
+
+
+def test_bench_gpus_flag_launches_that_many_ranks():
+    """`bench.py --gpus 2` started without torchrun launches two ranks itself
+    (torch.distributed.run, rendezvous on 127.0.0.1); rank 0 alone prints the
+    line and reports the real world size.  --dry-run does no GPU work."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--dry-run"],
+                       capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    assert lines[0]["n_gpus"] == 2 and lines[0]["ranks_seen"] == 2
