@@ -11,6 +11,10 @@
 // Device copy of the scratch, one per GPU that loads this library's module,
 // held until the process exits.  In host code `g_noalloc_scratch` is only a
 // host-side stand-in: its device address comes from cudaGetSymbolAddress.
+// Under lazy module loading (CUDA's default) the driver allocates this copy
+// when the module is first used on a device, which for a file without kernels
+// is the cudaGetSymbolAddress below, i.e. the first gattn_fwd_noalloc call on
+// that device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GATTN_NOALLOC_SCRATCH_BYTES];
 
 namespace {
@@ -26,7 +30,11 @@ void* scratch_on_current_device() {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_ptr[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+      // leave no sticky last-error behind for the next call of this library
+      (void)cudaGetLastError();
+      return nullptr;
+    }
     g_ptr[dev] = p;
   }
   return g_ptr[dev];
