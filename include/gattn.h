@@ -119,6 +119,14 @@ gattn_status gattn_validate(const gattn_desc *desc);
 /* Number of tiles, prod_a ceil(G_a / core_a). Negative on an invalid desc. */
 int64_t gattn_num_tiles(const gattn_desc *desc);
 
+/* Shape (bt, by, bx) of the token boxes the tensor-core kernels cut every
+ * extended tile into (bt * by * bx <= 128 tokens, one 128-row MMA block per
+ * box; rows past bt * by * bx and rows outside the tile are padding).  The
+ * attention work of a tile is (128 * boxes)^2 query-key pairs, so the padded
+ * (executed) work of a call follows from it.  GATTN_OK, or
+ * GATTN_ERR_INVALID_ARG on an invalid desc or a NULL shape. */
+gattn_status gattn_block_shape(const gattn_desc *desc, int32_t shape[3]);
+
 /*
  * Bytes of the saved-state buffer that gattn_fwd fills and gattn_bwd reads:
  * the per-(tile, row) log-sum-exp of every extended-tile row, and the FP32
@@ -255,7 +263,15 @@ void gattn_serve_destroy(gattn_server *s);
  *
  * The first call on a device looks up the array's device address on that
  * device (cudaGetSymbolAddress) and caches it; make that first call before
- * any stream capture.  All calls share the one array and it keeps the last
+ * any stream capture.  With CUDA's default lazy module loading the driver
+ * allocates the device copy of the array at that first lookup, not when the
+ * library is loaded: a caller whose memory manager takes all of HBM makes
+ * one call on each device before it does (a small problem is enough), or
+ * runs with CUDA_MODULE_LOADING=EAGER so that the array is placed when the
+ * context is created.  From then on calls allocate nothing.  The cached
+ * address belongs to the device's primary context: after cudaDeviceReset on
+ * that device it is stale, and this entry point must not be called again in
+ * that process.  All calls share the one array and it keeps the last
  * call's contents (no call depends on them: everything read is written
  * first in the same call).  Calls whose work overlaps on the GPU -- on
  * different streams, or from different host threads -- race on the array:

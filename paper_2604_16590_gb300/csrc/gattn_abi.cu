@@ -69,45 +69,81 @@ static int clipped_extent(const Geom& g, int a, int k) {
   return hi - lo;
 }
 
-// Box shape (bt, by, bx), bt*by*bx = 128, powers of two.  The attention work of
-// a tile grows with the square of its box count, so the shape minimising
-// sum_tiles NB_t^2 = prod_a sum_k ceil(e_a(k)/b_a)^2 (the sum factorises over
-// dimensions) wins; ties go to the longest contiguous x run.
+bool apply_box(Geom* g, const int b[3]);
+
+// Box shape (bt, by, bx) with R = bt*by*bx <= 128 rows.  Every box is one
+// 128-row MMA block, so the attention work of a tile grows with the square of
+// its box count and the shape minimising sum_tiles NB_t^2 =
+// prod_a sum_k ceil(e_a(k)/b_a)^2 (the sum factorises over dimensions) wins;
+// ties go to the fewest rows (least over-fetch), then to the longest
+// contiguous x run.  Non-power-of-two shapes matter for small tiles: a 24 x 24
+// extended tile takes five 5 x 24 boxes instead of six 4 x 32 boxes of which
+// a quarter is outside the tile.
 static void choose_box(Geom* g) {
+  // per dimension: the distinct clipped extents and how many tiles have each
+  double cost[3][129];
+  for (int a = 0; a < 3; ++a) {
+    int ext[8], cnt[8], nd = 0;
+    for (int k = 0; k < g->n[a]; ++k) {
+      const int e = clipped_extent(*g, a, k);
+      int i = 0;
+      while (i < nd && ext[i] != e) ++i;
+      if (i == nd) {
+        if (nd == 8) {  // cannot happen (at most first, interior, last two); be safe
+          ext[7] = e;
+          cnt[7] = 0;
+          i = 7;
+        } else {
+          ext[nd] = e;
+          cnt[nd++] = 0;
+        }
+      }
+      ++cnt[i];
+    }
+    for (int b = 1; b <= 128; ++b) {
+      double sum = 0.0;
+      for (int i = 0; i < nd; ++i) {
+        const double nb = (double)((ext[i] + b - 1) / b);
+        sum += cnt[i] * nb * nb;
+      }
+      cost[a][b] = sum;
+    }
+  }
   double best_cost = -1.0;
   int best[3] = {1, 1, 128};
-  for (int lt = 0; lt <= 7; ++lt)
-    for (int ly = 0; ly + lt <= 7; ++ly) {
-      const int lx = 7 - lt - ly;
-      const int b[3] = {1 << lt, 1 << ly, 1 << lx};
-      double cost = 1.0;
-      for (int a = 0; a < 3; ++a) {
-        double sum = 0.0;
-        for (int k = 0; k < g->n[a]; ++k) {
-          const double nb = (double)((clipped_extent(*g, a, k) + b[a] - 1) / b[a]);
-          sum += nb * nb;
+  for (int bt = 1; bt <= 128; ++bt)
+    for (int by = 1; bt * by <= 128; ++by)
+      for (int bx = 1; bt * by * bx <= 128; ++bx) {
+        const double c = cost[0][bt] * cost[1][by] * cost[2][bx];
+        const int R = bt * by * bx, Rb = best[0] * best[1] * best[2];
+        const bool tie = best_cost >= 0 && c <= best_cost * (1 + 1e-12) && c >= best_cost * (1 - 1e-12);
+        if (best_cost < 0 || c < best_cost * (1 - 1e-12) || (tie && (R < Rb || (R == Rb && bx > best[2])))) {
+          best_cost = c;
+          best[0] = bt;
+          best[1] = by;
+          best[2] = bx;
         }
-        cost *= sum;
       }
-      if (best_cost < 0 || cost < best_cost * (1 - 1e-12) || (cost <= best_cost * (1 + 1e-12) && b[2] > best[2])) {
-        best_cost = cost;
-        best[0] = b[0];
-        best[1] = b[1];
-        best[2] = b[2];
-      }
-    }
-  g->bt = best[0];
-  g->by = best[1];
-  g->bx = best[2];
-  g->lt = __builtin_ctz(best[0]);
-  g->ly = __builtin_ctz(best[1]);
-  g->lx = __builtin_ctz(best[2]);
-  g->nbmax_tot = 1;
+  apply_box(g, best);
+}
+
+bool apply_box(Geom* g, const int b[3]) {
+  if (b[0] < 1 || b[1] < 1 || b[2] < 1 || b[0] * b[1] * b[2] > 128) return false;
+  g->bt = b[0];
+  g->by = b[1];
+  g->bx = b[2];
+  g->R = b[0] * b[1] * b[2];
+  g->mdx = (65536u + (uint32_t)g->bx - 1) / (uint32_t)g->bx;
+  g->mdxy = (65536u + (uint32_t)(g->bx * g->by) - 1) / (uint32_t)(g->bx * g->by);
+  int64_t tot = 1;
   for (int a = 0; a < 3; ++a) {
-    g->nbmax[a] = (g->emax[a] + best[a] - 1) / best[a];
-    g->nbmax_tot *= g->nbmax[a];
+    g->nbmax[a] = (g->emax[a] + b[a] - 1) / b[a];
+    tot *= g->nbmax[a];
   }
+  if (tot * 128 >= (1LL << 31)) return false;
+  g->nbmax_tot = (int32_t)tot;
   g->per_tile = g->nbmax_tot * 128;
+  return true;
 }
 
 bool make_geom(const gattn_desc* desc, Geom* g) {
@@ -155,7 +191,7 @@ bool make_geom(const gattn_desc* desc, Geom* g) {
   g->scale = d.scale > 0.f ? d.scale : 1.0f / sqrtf((float)d.d);
   g->scale_log2 = g->scale * 1.4426950408889634f;
   choose_box(g);
-  if ((int64_t)g->nbmax_tot * 128 >= (1LL << 31)) return false;
+  if (g->R < 1 || (int64_t)g->nbmax_tot * 128 >= (1LL << 31)) return false;
   return true;
 }
 
@@ -202,6 +238,15 @@ gattn_status gattn_validate(const gattn_desc* desc) {
 int64_t gattn_num_tiles(const gattn_desc* desc) {
   Geom g;
   return make_geom(desc, &g) ? (int64_t)g.ntiles : -1;
+}
+
+gattn_status gattn_block_shape(const gattn_desc* desc, int32_t shape[3]) {
+  Geom g;
+  if (!shape || !make_geom(desc, &g)) return GATTN_ERR_INVALID_ARG;
+  shape[0] = g.bt;
+  shape[1] = g.by;
+  shape[2] = g.bx;
+  return GATTN_OK;
 }
 
 size_t gattn_saved_bytes(const gattn_desc* desc) {

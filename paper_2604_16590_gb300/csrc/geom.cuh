@@ -6,16 +6,17 @@
 // index is the fixed merge order).  Extended interval of tile k along a:
 // [max(k c - h, 0), min((k+1) c + h, G)).  Rows of an extended tile are
 // numbered r = (lt * e_y + ly) * e_x + lx over its clipped extents e[3].
-// Every extended tile is also covered by 3-D boxes of bt x by x bx = 128 tokens
-// (powers of two; the box shape is chosen per problem on the host).  Box j of
-// a tile with nb[3] boxes per dimension has origin ((j / (nb_y nb_x)) bt,
+// Every extended tile is also covered by 3-D boxes of bt x by x bx = R <= 128
+// tokens (the box shape is chosen per problem on the host); one box is one
+// 128-row MMA block whose rows R..127 are padding.  Box j of a tile with
+// nb[3] boxes per dimension has origin ((j / (nb_y nb_x)) bt,
 // ((j / nb_x) % nb_y) by, (j % nb_x) bx) in tile-local coordinates and its row
-// rho sits at box offset (rho >> (ly + lx), (rho >> lx) & (by - 1),
-// rho & (bx - 1)).  Per-(tile, row) state (log-sum-exp, per-tile outputs,
-// softmax statistics, per-tile gradients) lives at slot
+// rho < R sits at box offset (rho / (by bx), (rho / bx) % by, rho % bx).
+// Per-(tile, row) state (log-sum-exp, per-tile outputs, softmax statistics,
+// per-tile gradients) lives at slot
 //     ((bh * ntiles + tile) * per_tile + j * 128 + rho),  per_tile = nbmax * 128,
-// so the 128 rows of one box are contiguous -- the order the tensor-core
-// kernels process them in.
+// so the rows of one box are contiguous -- the order the tensor-core kernels
+// process them in.
 #pragma once
 
 #include <stdint.h>
@@ -41,8 +42,9 @@ struct Geom {
   int32_t ntiles;
   int32_t Lmax;
   int32_t window;   // gattn_window
-  int32_t bt, by, bx;   // 128-token box shape
-  int32_t lt, ly, lx;   // log2 of the box extents
+  int32_t bt, by, bx;   // box shape, R = bt * by * bx <= 128 tokens
+  int32_t R;            // rows of a box that hold tokens
+  uint32_t mdx, mdxy;   // ceil(2^16 / bx), ceil(2^16 / (bx by)): exact quotients of rho < 128
   int32_t nbmax[3];     // most boxes any tile needs per dimension
   int32_t nbmax_tot;    // nbmax[0] * nbmax[1] * nbmax[2]
   int32_t per_tile;     // slots per tile = nbmax_tot * 128
@@ -124,25 +126,41 @@ __host__ __device__ __forceinline__ void tile_local(const TileBox& tb, int r, in
   l[0] = rr / tb.e[1];
 }
 
+// offset (t, y, x) of row rho (0 <= rho < 128) inside a box; the quotients
+// are multiply-shifts, exact for rho < 128 and box extents <= 128
+__host__ __device__ __forceinline__ void box_offset(const Geom& g, int rho, int o[3]) {
+  const int rt = (int)(((uint32_t)rho * g.mdxy) >> 16);
+  const int rem = rho - rt * g.by * g.bx;
+  const int ry = (int)(((uint32_t)rem * g.mdx) >> 16);
+  o[0] = rt;
+  o[1] = ry;
+  o[2] = rem - ry * g.bx;
+}
+
 // slot of the token at tile-local coordinates l[3] of a tile with extents e[3]
 __host__ __device__ __forceinline__ int64_t slot_of(const Geom& g, int bh, int tile, const int e[3], const int l[3]) {
-  const int nby = (e[1] + g.by - 1) >> g.ly;
-  const int nbx = (e[2] + g.bx - 1) >> g.lx;
-  const int j = ((l[0] >> g.lt) * nby + (l[1] >> g.ly)) * nbx + (l[2] >> g.lx);
-  const int rho = ((l[0] & (g.bt - 1)) << (g.ly + g.lx)) | ((l[1] & (g.by - 1)) << g.lx) | (l[2] & (g.bx - 1));
+  const int nby = (e[1] + g.by - 1) / g.by;
+  const int nbx = (e[2] + g.bx - 1) / g.bx;
+  const int qt = l[0] / g.bt, qy = l[1] / g.by, qx = l[2] / g.bx;
+  const int j = (qt * nby + qy) * nbx + qx;
+  const int rho = ((l[0] - qt * g.bt) * g.by + (l[1] - qy * g.by)) * g.bx + (l[2] - qx * g.bx);
   return ((int64_t)bh * g.ntiles + tile) * g.per_tile + (int64_t)j * 128 + rho;
 }
 
 // inverse of slot_of within one tile: tile-local coordinates of row rho of
-// box j of a tile with extents e[3]; false if that row lies outside the tile
+// box j of a tile with extents e[3]; false if that row is padding (rho >= R)
+// or lies outside the tile
 __host__ __device__ __forceinline__ bool slot_local(const Geom& g, const int e[3], int j, int rho, int l[3]) {
-  const int nby = (e[1] + g.by - 1) >> g.ly;
-  const int nbx = (e[2] + g.bx - 1) >> g.lx;
+  if (rho >= g.R) return false;
+  const int nby = (e[1] + g.by - 1) / g.by;
+  const int nbx = (e[2] + g.bx - 1) / g.bx;
   const int jx = j % nbx, jr = j / nbx;
   const int jy = jr % nby, jt = jr / nby;
-  l[0] = (jt << g.lt) + (rho >> (g.ly + g.lx));
-  l[1] = (jy << g.ly) + ((rho >> g.lx) & (g.by - 1));
-  l[2] = (jx << g.lx) + (rho & (g.bx - 1));
+  int o[3];
+  box_offset(g, rho, o);
+  l[0] = jt * g.bt + o[0];
+  l[1] = jy * g.by + o[1];
+  l[2] = jx * g.bx + o[2];
   return l[0] < e[0] && l[1] < e[1] && l[2] < e[2];
 }
 
@@ -169,5 +187,9 @@ __device__ __forceinline__ float tile_weight(const Geom& g, const int p[3], cons
 
 // Host-side construction (including the box shape); false on an invalid descriptor.
 bool make_geom(const gattn_desc* desc, Geom* g);
+// Replace the box shape of a constructed geometry by b (bt, by, bx), R <= 128
+// (every shape is valid, only the padding differs); false if b is not a box
+// shape or the slot count overflows.
+bool apply_box(Geom* g, const int b[3]);
 
 }  // namespace gattn

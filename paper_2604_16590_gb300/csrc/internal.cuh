@@ -170,9 +170,12 @@ struct alignas(128) ReqDesc {
 // counts[0] = number of requests, counts[1] = total attention work items,
 // counts[2] = total (head, token) rows; read on the device so that one
 // captured launch serves any active set.
-cudaError_t launch_sm103_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, int d, cudaStream_t st);
+// box_rows: the rows R of the box shape every request of the launch uses
+// (items of a request with another shape are refused as bounds errors).
+cudaError_t launch_sm103_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, int d, int box_rows,
+                                    cudaStream_t st);
 // d = 64: the two-box kernel; its work items per (head, tile) are pairs of boxes
-cudaError_t launch_sm103_fwd64_ragged(const ReqDesc* reqs, const int64_t* counts, cudaStream_t st);
+cudaError_t launch_sm103_fwd64_ragged(const ReqDesc* reqs, const int64_t* counts, int box_rows, cudaStream_t st);
 int fwd64_ragged_items(const Geom& g);  // nh * ntiles * ceil(nbmax_tot / 2)
 cudaError_t launch_serve_update(const ReqDesc* reqs, const int64_t* counts, int d, float c, cudaStream_t st);
 

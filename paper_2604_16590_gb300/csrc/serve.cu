@@ -162,7 +162,16 @@ struct gattn_server {
   std::vector<double> latencies;
 };
 
-static bool serve_geom(const gattn_serve_cfg* cfg, int T, int nh, Geom* g) {
+// Geometry of a request with T frames and nh heads.  All requests of a server
+// share one box shape (the one chosen for a single temporal tile of one head),
+// because the ragged launch zeroes the padding rows of its operand blocks once.
+static bool serve_geom(const gattn_serve_cfg* cfg, int T, int nh, Geom* g, bool probe = false) {
+  if (!probe) {
+    Geom p;
+    if (!serve_geom(cfg, cfg->core[0], 1, &p, true)) return false;
+    const int box[3] = {p.bt, p.by, p.bx};
+    return serve_geom(cfg, T, nh, g, true) && apply_box(g, box);
+  }
   gattn_desc d;
   memset(&d, 0, sizeof(d));
   d.B = 1;
@@ -179,6 +188,12 @@ static bool serve_geom(const gattn_serve_cfg* cfg, int T, int nh, Geom* g) {
   d.in_dtype = GATTN_BF16;
   d.out_dtype = GATTN_BF16;
   return make_geom(&d, g);
+}
+
+// rows of the box shape every request of this server uses
+static int probe_rows(const gattn_server* s) {
+  Geom p;
+  return serve_geom(&s->cfg, s->cfg.core[0], 1, &p, true) ? p.R : 128;
 }
 
 static size_t request_bytes(const Geom& g) {
@@ -209,7 +224,7 @@ gattn_status gattn_serve_create(const gattn_serve_cfg* cfg, gattn_stream_t strea
   if (!cfg || !out || cfg->steps < 1 || cfg->max_active < 1 || cfg->max_active > 4096 || cfg->hbm_budget == 0)
     return GATTN_ERR_INVALID_ARG;
   Geom probe;
-  if (!serve_geom(cfg, cfg->core[0], 1, &probe)) return GATTN_ERR_INVALID_ARG;
+  if (!serve_geom(cfg, cfg->core[0], 1, &probe, true)) return GATTN_ERR_INVALID_ARG;
   gattn_server* s = new gattn_server();
   s->cfg = *cfg;
   s->stream = reinterpret_cast<cudaStream_t>(stream);
@@ -331,12 +346,12 @@ gattn_status gattn_serve_step(gattn_server* s, int32_t* n_active, int32_t* n_wai
         // the first iteration runs its two launches directly (which also sets the
         // kernels' attributes outside capture), then records the same two
         // launches into the graph that every later iteration replays
-        if (launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, s->stream) != cudaSuccess ||
+        if (launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, probe_rows(s), s->stream) != cudaSuccess ||
             launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->stream) != cudaSuccess)
           return GATTN_ERR_CUDA;
         cudaGraph_t gr;
         if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GATTN_ERR_CUDA;
-        cudaError_t e1 = launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, s->stream);
+        cudaError_t e1 = launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, probe_rows(s), s->stream);
         cudaError_t e2 = launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->stream);
         cudaError_t e3 = cudaStreamEndCapture(s->stream, &gr);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return GATTN_ERR_CUDA;
@@ -346,7 +361,7 @@ gattn_status gattn_serve_step(gattn_server* s, int32_t* n_active, int32_t* n_wai
         return GATTN_ERR_CUDA;
       }
     } else {
-      if (launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, s->stream) != cudaSuccess ||
+      if (launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, probe_rows(s), s->stream) != cudaSuccess ||
           launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->stream) != cudaSuccess)
         return GATTN_ERR_CUDA;
     }

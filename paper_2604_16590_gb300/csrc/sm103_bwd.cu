@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  zero_pad_rows(smem, (2 + 2 * C::kStages) * C::kHalves, a.g.R);  // K, V and the Q / dOut ring
   if (threadIdx.x == 0) {
     mbar_init(kv_full, 1);
     mbar_init(kv_empty, 1);
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int o[3];
         block_origin(g, tbk, kb, o);
         if (!(ok = WAIT(kv_empty, (W & 1) ^ 1))) break;
-        mbar_arrive_expect_tx(kv_full, 2 * C::kBlock);
+        mbar_arrive_expect_tx(kv_full, 2 * C::kHalves * g.R * 128);
         kv_arm = 1;
         kv_par = W & 1;
         for (int h = 0; h < C::kHalves; ++h) {
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t st = G % C::kStages, n = G / C::kStages;
           block_origin(g, tbk, i, o);
           if (!(ok = WAIT(qd_empty + st, (n & 1) ^ 1))) break;
-          mbar_arrive_expect_tx(qd_full + st, 2 * C::kBlock + 1024);
+          mbar_arrive_expect_tx(qd_full + st, 2 * C::kHalves * g.R * 128 + 1024);
           qd_arm |= 1u << st;
           qd_par = (qd_par & ~(1u << st)) | ((n & 1) << st);
           uint8_t* sq = smem + C::kQ + st * 2 * C::kBlock;
@@ -386,6 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  zero_pad_rows(smem, (2 + 2 * C::kStages) * C::kHalves, a.g.R);  // Q, dOut and the K / V ring
   if (threadIdx.x == 0) {
     mbar_init(qd_full, 1);
     mbar_init(qd_empty, 1);
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int o[3];
         block_origin(g, tbk, qb, o);
         if (!(ok = WAIT(qd_empty, (W & 1) ^ 1))) break;
-        mbar_arrive_expect_tx(qd_full, 2 * C::kBlock);
+        mbar_arrive_expect_tx(qd_full, 2 * C::kHalves * g.R * 128);
         qd_arm = 1;
         qd_par = W & 1;
         for (int h = 0; h < C::kHalves; ++h) {
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t st = G % C::kStages, n = G / C::kStages;
           block_origin(g, tbk, j, o);
           if (!(ok = WAIT(kv_empty + st, (n & 1) ^ 1))) break;
-          mbar_arrive_expect_tx(kv_full + st, 2 * C::kBlock);
+          mbar_arrive_expect_tx(kv_full + st, 2 * C::kHalves * g.R * 128);
           kv_arm |= 1u << st;
           kv_par = (kv_par & ~(1u << st)) | ((n & 1) << st);
           uint8_t* sk = smem + C::kK + st * 2 * C::kBlock;

@@ -68,43 +68,38 @@ constexpr int kMath0 = 3;                   // first math warp
 constexpr int kIssuerA = 2;                 // warp index of the gradient-product issuer
 constexpr int kThreads64 = 32 * (kMath0 + kMath64);
 
-// Epilogue of 16 FP32 TMEM columns of this thread's row, scaled by `mul`: to
-// `out` (OutT) if the row is covered by one tile, else to the FP32 slot `scr`,
-// nothing if the row lies outside the tile.  Every lane executes the TMEM load.
+// Stores 16 FP32 values of this thread's row (already in registers), scaled
+// by `mul`: to `out` (OutT) if the row is covered by one tile, else to the
+// FP32 slot `scr`, nothing if the row lies outside the tile.
 template <typename OutT>
-__device__ __forceinline__ void row_epilogue16(uint32_t taddr, float mul, bool valid, bool single, OutT* out,
-                                               float* scr) {
-  uint32_t r[16];
-  tmem_ld16(taddr, r);
-  tmem_wait_ld(r);
-  if (valid) {
+__device__ __forceinline__ void row_store16(const uint32_t (&r)[16], float mul, bool valid, bool single, OutT* out,
+                                            float* scr) {
+  if (!valid) return;
 #pragma unroll
-    for (int e = 0; e < 16; e += 4) {
-      const float4 v = make_float4(__uint_as_float(r[e]) * mul, __uint_as_float(r[e + 1]) * mul,
-                                   __uint_as_float(r[e + 2]) * mul, __uint_as_float(r[e + 3]) * mul);
-      if (single)
-        store4<OutT>(out + e, v);
-      else
-        store4<float>(scr + e, v);
-    }
+  for (int e = 0; e < 16; e += 4) {
+    const float4 v = make_float4(__uint_as_float(r[e]) * mul, __uint_as_float(r[e + 1]) * mul,
+                                 __uint_as_float(r[e + 2]) * mul, __uint_as_float(r[e + 3]) * mul);
+    if (single)
+      store4<OutT>(out + e, v);
+    else
+      store4<float>(scr + e, v);
   }
 }
-
 
 // =============================================================== dK / dV
 struct Kv64 {
   static constexpr int kStages = 4;  // (Q, dOut, statistics rows) ring
+  // two (K, V) buffers, items alternate: buffer b holds K at kK + 2 b kBox, V after it
   static constexpr int kK = 0;
-  static constexpr int kV = kBox;
-  static constexpr int kQ = 2 * kBox;  // stage s: Q at kQ + s*2*kBox, dOut after it
+  static constexpr int kQ = 4 * kBox;  // stage s: Q at kQ + s*2*kBox, dOut after it
   // Extension operands, K-major without swizzle: 128 rows x 16 B (K-columns
   // 0..7) followed by 2 KB of zeros (K-columns 8..15, lbo = 2048).
   static constexpr int kOnes = kQ + kStages * 2 * kBox;  // A: ones in K 0..2 at kOnes, ones in K 3..5 at kOnes+4096
   static constexpr int kExt = kOnes + 2 * 4096;            // B, stage s at kExt + s*4096: the 128 statistics rows
   static constexpr int kBar = kExt + kStages * 4096;
-  // kv_full, kv_empty, qd_full[S], qd_empty[S], s_full[2], s_empty[2], p_full[2], p_empty[2], acc_full,
-  // acc_empty, drain[2]   (s_*[0]: the S chain, s_*[1]: the dP chain)
-  static constexpr int kNumBars = 2 + 2 * kStages + 12;
+  // kv_full[2], kv_empty[2], qd_full[S], qd_empty[S], s_full[2], s_empty[2], p_full[2], p_empty[2],
+  // acc_full, acc_empty, drain[2]   (s_*[0]: the S chain, s_*[1]: the dP chain)
+  static constexpr int kNumBars = 4 + 2 * kStages + 12;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kSmem = kMisc + 16 + 1024;
   // TMEM: S'^T 0, dP'^T 128, P'^T (packed) 256, dS^T (packed) 320, dV 384, dK 448
@@ -143,9 +138,9 @@ __global__ void __launch_bounds__(kThreads64, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kBar);
-  uint64_t* kv_full = bars;
-  uint64_t* kv_empty = bars + 1;
-  uint64_t* qd_full = bars + 2;
+  uint64_t* kv_full = bars;       // [2]
+  uint64_t* kv_empty = bars + 2;  // [2]
+  uint64_t* qd_full = bars + 4;
   uint64_t* qd_empty = qd_full + C::kStages;
   uint64_t* s_full = qd_empty + C::kStages;
   uint64_t* s_empty = s_full + 2;
@@ -174,10 +169,13 @@ __global__ void __launch_bounds__(kThreads64, 1)
     }
     *reinterpret_cast<uint4*>(dst) = v;
   }
+  zero_pad_rows(smem, 4 + 2 * C::kStages, a.g.R);  // both K, V buffers and the Q / dOut ring
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
-    mbar_init(kv_full, 1);
-    mbar_init(kv_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(kv_full + b, 1);
+      mbar_init(kv_empty + b, 1);
+    }
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(qd_full + s, 1);
       mbar_init(qd_empty + s, 1);
@@ -225,17 +223,21 @@ __global__ void __launch_bounds__(kThreads64, 1)
         if (kb >= tbk.NB) continue;
         int o[3];
         block_origin(g, tbk, kb, o);
-        if (!(ok = WAIT(kv_empty, (W & 1) ^ 1))) break;
-        mbar_arrive_expect_tx(kv_full, 2 * kBox);
-        kv_arm = 1;
-        kv_par = W & 1;
-        tma_load_5d(smem + C::kK, &tk, kv_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
-        tma_load_5d(smem + C::kV, &tv, kv_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
+        // K, V of this item go to buffer W & 1 while the previous item still reads the other
+        const uint32_t kb2 = W & 1, kn = (W >> 1) & 1;
+        if (!(ok = WAIT(kv_empty + kb2, kn ^ 1))) break;
+        mbar_arrive_expect_tx(kv_full + kb2, 2 * g.R * 128);
+        kv_arm |= 1u << kb2;
+        kv_par = (kv_par & ~(1u << kb2)) | (kn << kb2);
+        uint8_t* skv = smem + C::kK + kb2 * 2 * kBox;
+        tma_load_5d(skv, &tk, kv_full + kb2, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
+        tma_load_5d(skv + kBox, &tv, kv_full + kb2, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0],
+                    bh);
         const int64_t slot0 = tile_slot0(g, bh, tile);
         int jt = 0, jy = 0, jx = 0;
         for (int i = 0; i < tbk.NB; ++i, ++G) {
           const uint32_t st = G % C::kStages, n = G / C::kStages;
-          const int c1 = tbk.tb.lo[2] + (jx << g.lx), c2 = tbk.tb.lo[1] + (jy << g.ly), c3 = tbk.tb.lo[0] + (jt << g.lt);
+          const int c1 = tbk.tb.lo[2] + (jx * g.bx), c2 = tbk.tb.lo[1] + (jy * g.by), c3 = tbk.tb.lo[0] + (jt * g.bt);
           if (++jx == tbk.nb[2]) {
             jx = 0;
             if (++jy == tbk.nb[1]) {
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(kThreads64, 1)
             }
           }
           if (!(ok = WAIT(qd_empty + st, (n & 1) ^ 1))) break;
-          mbar_arrive_expect_tx(qd_full + st, 2 * kBox + 2048);
+          mbar_arrive_expect_tx(qd_full + st, 2 * g.R * 128 + 2048);
           qd_arm |= 1u << st;
           qd_par = (qd_par & ~(1u << st)) | ((n & 1) << st);
           uint8_t* sq = smem + C::kQ + st * 2 * kBox;
@@ -255,7 +257,8 @@ __global__ void __launch_bounds__(kThreads64, 1)
         ++W;
       }
       if (!ok) {
-        if (kv_arm) mbar_wait<set_status_bwd64>(kv_full, kv_par, abort_flag, false);
+        for (int b = 0; b < 2; ++b)
+          if (kv_arm & (1u << b)) mbar_wait<set_status_bwd64>(kv_full + b, (kv_par >> b) & 1, abort_flag, false);
         for (int s = 0; s < C::kStages; ++s)
           if (qd_arm & (1u << s)) mbar_wait<set_status_bwd64>(qd_full + s, (qd_par >> s) & 1, abort_flag, false);
       }
@@ -264,8 +267,7 @@ __global__ void __launch_bounds__(kThreads64, 1)
     // ------------------------------------------------------------ issuer of S'^T, dP'^T
     if (lane == 0) {
       constexpr uint32_t idS = idesc_bf16(128, 128, 0);
-      const uint64_t dK = sw128_desc(smem_u32(smem + C::kK), 16, 1024);
-      const uint64_t dV = sw128_desc(smem_u32(smem + C::kV), 16, 1024);
+      const uint64_t dK0 = sw128_desc(smem_u32(smem + C::kK), 16, 1024);
       const uint64_t dQ0 = sw128_desc(smem_u32(smem + C::kQ), 16, 1024);
       const uint64_t dOnesS = noswz_desc(smem_u32(smem + C::kOnes), 2048, 128);
       const uint64_t dOnesD = dmove(dOnesS, 4096);
@@ -278,7 +280,9 @@ __global__ void __launch_bounds__(kThreads64, 1)
         TileBlocks tbk;
         tile_blocks(g, tile, tbk);
         if (kb >= tbk.NB) continue;
-        if (!(ok = WAIT(kv_full, W & 1))) break;
+        const uint32_t kb2 = W & 1;
+        if (!(ok = WAIT(kv_full + kb2, (W >> 1) & 1))) break;
+        const uint64_t dK = dmove(dK0, kb2 * 2 * kBox), dV = dmove(dK, kBox);
         for (int i = 0; i < tbk.NB; ++i, ++G) {
           const uint32_t st = G % C::kStages;
           if (!(ok = WAIT(qd_full + st, (G / C::kStages) & 1))) break;
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(kThreads64, 1)
             umma_bf16(tmem + C::kColDP, dmove(dV, ks * 32), dmove(ddo, ks * 32), idS, ks > 0);
           umma_bf16(tmem + C::kColDP, dOnesD, de, idS, 1u);
           umma_commit(s_full + 1);
-          if (i == tbk.NB - 1) umma_commit(kv_empty);  // K, V of this item no longer read
+          if (i == tbk.NB - 1) umma_commit(kv_empty + kb2);  // K, V of this item no longer read
         }
         ++W;
       }
@@ -402,13 +406,20 @@ __global__ void __launch_bounds__(kThreads64, 1)
       const bool single = kvalid && single_cover(g, p);
       const int64_t slot = tile_slot0(g, bh, tile) + kb * 128 + row;
       const int c0 = c4 * 16;
-      row_epilogue16<OutT>(tl + C::kColDK + c0, g.scale, kvalid, single,
-                           static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * kD + c0, a.dk_s + slot * kD + c0);
-      row_epilogue16<OutT>(tl + C::kColDV + c0, 1.f, kvalid, single,
-                           static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * kD + c0, a.dv_s + slot * kD + c0);
+      // both accumulators into registers, then they are released at once: the
+      // next item's first gradient products may overwrite them during the stores
+      uint32_t rk[16], rv[16];
+      tmem_ld16(tl + C::kColDK + c0, rk);
+      tmem_ld16(tl + C::kColDV + c0, rv);
+      tmem_wait_ld(rk);
+      tmem_wait_ld(rv);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
+      row_store16<OutT>(rk, g.scale, kvalid, single, static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * kD + c0,
+                        a.dk_s + slot * kD + c0);
+      row_store16<OutT>(rv, 1.f, kvalid, single, static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * kD + c0,
+                        a.dv_s + slot * kD + c0);
       ++W;
     }
   }
@@ -422,21 +433,15 @@ __global__ void __launch_bounds__(kThreads64, 1)
 
 // =============================================================== dQ
 // P' = exp2(s S log2e - lse') of 32 columns of this thread's query row, FP32
-// in place of the scores (keys outside the tile masked to 0)
-template <bool MASK>
-__device__ __forceinline__ void q_p(uint32_t (&s)[32], uint32_t mbits, float sl2, float nL) {
+// in place of the scores
+__device__ __forceinline__ void q_p(uint32_t (&s)[32], float sl2, float nL) {
   const uint64_t s2 = f2pack(sl2, sl2), nl2 = f2pack(nL, nL);
 #pragma unroll
   for (int c = 0; c < 32; c += 2) {
     float a0, a1;
     f2unpack(ffma2(u2pack(s[c], s[c + 1]), s2, nl2), a0, a1);
-    float p0 = ex2(a0), p1 = ex2(a1);
-    if (MASK) {
-      p0 = (mbits >> c) & 1u ? p0 : 0.f;
-      p1 = (mbits >> (c + 1)) & 1u ? p1 : 0.f;
-    }
-    s[c] = __float_as_uint(p0);
-    s[c + 1] = __float_as_uint(p1);
+    s[c] = __float_as_uint(ex2(a0));
+    s[c + 1] = __float_as_uint(ex2(a1));
   }
 }
 // dS = P' (dP - D) as BF16 pairs
@@ -455,7 +460,12 @@ struct Q64 {
   static constexpr int kQ = 0;
   static constexpr int kDO = kBox;
   static constexpr int kK = 2 * kBox;  // stage s: K at kK + s*2*kBox, V after it
-  static constexpr int kBar = kK + kStages * 2 * kBox;
+  // Key-mask extension operands (as in the forward): A = 1 in K-column 0 of
+  // 128 rows, and per stage the key block's bias row (0, or -1e30 for a
+  // padding key or a key outside the tile), each followed by 2 KB of zeros.
+  static constexpr int kOnes = kK + kStages * 2 * kBox;
+  static constexpr int kBias = kOnes + 4096;
+  static constexpr int kBar = kBias + kStages * 4096;
   // qd_full, qd_empty, qt_full, kv_full[S], kv_empty[S], s_full[2], s_empty[2], p_full[2], p_empty[2],
   // acc_full, acc_empty, drain[2]   (s_*[0]: the S chain, s_*[1]: the dP chain)
   static constexpr int kNumBars = 3 + 2 * kStages + 12;
@@ -490,6 +500,13 @@ __global__ void __launch_bounds__(kThreads64, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  zero_pad_rows(smem, 2 + 2 * C::kStages, a.g.R);  // Q, dOut and the K / V ring
+  for (int r = threadIdx.x; r < (1 + C::kStages) * 256; r += kThreads64) {
+    const int blk = r >> 8, rr = r & 255;
+    const uint4 v = (blk == 0 && rr < 128) ? make_uint4(0x00003F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+    if (blk == 0 || rr >= 128) *reinterpret_cast<uint4*>(smem + C::kOnes + blk * 4096 + rr * 16) = v;
+  }
+  fence_proxy_async_smem();
   if (threadIdx.x == 0) {
     mbar_init(qd_full, 1);
     mbar_init(qd_empty, kMath64);
@@ -528,58 +545,73 @@ __global__ void __launch_bounds__(kThreads64, 1)
   const Geom& g = a.g;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      uint32_t G = 0, W = 0;
-      uint32_t qd_arm = 0, qd_par = 0, kv_arm = 0, kv_par = 0;
-      bool ok = true;
-      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-        int bh, tile, qb;
-        decode_item(g, w, bh, tile, qb);
-        TileBlocks tbk;
-        tile_blocks(g, tile, tbk);
-        if (qb >= tbk.NB) continue;
-        int o[3];
-        block_origin(g, tbk, qb, o);
-        if (!(ok = WAIT(qd_empty, (W & 1) ^ 1))) break;
-        mbar_arrive_expect_tx(qd_full, 2 * kBox);
-        qd_arm = 1;
-        qd_par = W & 1;
-        tma_load_5d(smem + C::kQ, &tq, qd_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
-        tma_load_5d(smem + C::kDO, &tdo, qd_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0],
-                    bh);
-        int jt = 0, jy = 0, jx = 0;
-        for (int j = 0; j < tbk.NB; ++j, ++G) {
-          const uint32_t st = G % C::kStages, n = G / C::kStages;
-          const int c1 = tbk.tb.lo[2] + (jx << g.lx), c2 = tbk.tb.lo[1] + (jy << g.ly), c3 = tbk.tb.lo[0] + (jt << g.lt);
-          if (++jx == tbk.nb[2]) {
-            jx = 0;
-            if (++jy == tbk.nb[1]) {
-              jy = 0;
-              ++jt;
-            }
+    // ------------------------------------------------------------ TMA producer (lane 0) and
+    // key-mask rows (all lanes, for key blocks with padding rows or keys outside the tile)
+    const uint32_t neg = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(-1e30f));
+    uint32_t G = 0, W = 0;
+    uint32_t qd_arm = 0, qd_par = 0, kv_arm = 0, kv_par = 0;
+    bool ok = true;
+    for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
+      int bh, tile, qb;
+      decode_item(g, w, bh, tile, qb);
+      TileBlocks tbk;
+      tile_blocks(g, tile, tbk);
+      if (qb >= tbk.NB) continue;
+      int o[3];
+      block_origin(g, tbk, qb, o);
+      if (lane == 0) {
+        if ((ok = WAIT(qd_empty, (W & 1) ^ 1))) {
+          mbar_arrive_expect_tx(qd_full, 2 * g.R * 128);
+          qd_arm = 1;
+          qd_par = W & 1;
+          tma_load_5d(smem + C::kQ, &tq, qd_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0],
+                      bh);
+          tma_load_5d(smem + C::kDO, &tdo, qd_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
+                      tbk.tb.lo[0] + o[0], bh);
+        }
+      }
+      if (!(ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0)) break;
+      for (int j = 0; j < tbk.NB; ++j, ++G) {
+        const uint32_t st = G % C::kStages, n = G / C::kStages;
+        int ko[3];
+        block_origin(g, tbk, j, ko);
+        // the stage (K, V and its bias row) is free once box G - kStages is done
+        if (lane == 0) ok = WAIT(kv_empty + st, (n & 1) ^ 1);
+        if (!(ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0)) break;
+        if (!block_full(g, tbk, ko)) {
+          for (int r = lane; r < 128; r += 32) {
+            int kl[3];
+            block_row(g, ko, r, kl);
+            *reinterpret_cast<uint4*>(smem + C::kBias + st * 4096 + r * 16) =
+                make_uint4(inside(tbk, kl) ? 0u : neg, 0u, 0u, 0u);
           }
-          if (!(ok = WAIT(kv_empty + st, (n & 1) ^ 1))) break;
-          mbar_arrive_expect_tx(kv_full + st, 2 * kBox);
+          fence_proxy_async_smem();
+        }
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive_expect_tx(kv_full + st, 2 * g.R * 128);
           kv_arm |= 1u << st;
           kv_par = (kv_par & ~(1u << st)) | ((n & 1) << st);
           uint8_t* sk = smem + C::kK + st * 2 * kBox;
-          tma_load_5d(sk, &tk, kv_full + st, 0, c1, c2, c3, bh);
-          tma_load_5d(sk + kBox, &tv, kv_full + st, 0, c1, c2, c3, bh);
+          tma_load_5d(sk, &tk, kv_full + st, 0, tbk.tb.lo[2] + ko[2], tbk.tb.lo[1] + ko[1], tbk.tb.lo[0] + ko[0], bh);
+          tma_load_5d(sk + kBox, &tv, kv_full + st, 0, tbk.tb.lo[2] + ko[2], tbk.tb.lo[1] + ko[1],
+                      tbk.tb.lo[0] + ko[0], bh);
         }
-        ++W;
       }
-      if (!ok) {
-        if (qd_arm) mbar_wait<set_status_bwd64>(qd_full, qd_par, abort_flag, false);
-        for (int s = 0; s < C::kStages; ++s)
-          if (kv_arm & (1u << s)) mbar_wait<set_status_bwd64>(kv_full + s, (kv_par >> s) & 1, abort_flag, false);
-      }
+      ++W;
+    }
+    if (!ok && lane == 0) {
+      if (qd_arm) mbar_wait<set_status_bwd64>(qd_full, qd_par, abort_flag, false);
+      for (int s = 0; s < C::kStages; ++s)
+        if (kv_arm & (1u << s)) mbar_wait<set_status_bwd64>(kv_full + s, (kv_par >> s) & 1, abort_flag, false);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ issuer of S, dP
     if (lane == 0) {
       constexpr uint32_t idS = idesc_bf16(128, 128, 0);
       const uint64_t dK0 = sw128_desc(smem_u32(smem + C::kK), 16, 1024);
+      const uint64_t dOnes = noswz_desc(smem_u32(smem + C::kOnes), 2048, 128);
+      const uint64_t dBias0 = noswz_desc(smem_u32(smem + C::kBias), 2048, 128);
       uint32_t G = 0, W = 0;
       bool ok = true;
       for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
@@ -589,8 +621,12 @@ __global__ void __launch_bounds__(kThreads64, 1)
         tile_blocks(g, tile, tbk);
         if (qb >= tbk.NB) continue;
         if (!(ok = WAIT(qt_full, W & 1))) break;  // Q, dOut in TMEM
-        for (int j = 0; j < tbk.NB; ++j, ++G) {
+        const bool all_full = tile_all_full(g, tbk);
+        BlockWalk bw;
+        for (int j = 0; j < tbk.NB; ++j, ++G, bw.next(tbk)) {
           const uint32_t st = G % C::kStages;
+          // a masked block's bias row was filled by the producer warp
+          const bool masked = !all_full && !bw.full(g, tbk);
           if (!(ok = WAIT(kv_full + st, (G / C::kStages) & 1))) break;
           if (G > 0 && !(ok = WAIT(s_empty, (G - 1) & 1))) break;  // S of box G-1 read
           tc_fence_after();
@@ -598,6 +634,8 @@ __global__ void __launch_bounds__(kThreads64, 1)
 #pragma unroll
           for (int ks = 0; ks < kD / 16; ++ks)
             umma_bf16_ts(tmem + C::kColS, tmem + C::kColQ + ks * 8, dmove(dk, ks * 32), idS, ks > 0);
+          // masked keys get -1e30, so P' = 0 there and dS = 0 follows
+          if (masked) umma_bf16(tmem + C::kColS, dOnes, dmove(dBias0, st * 4096), idS, 1u);
           umma_commit(s_full);
           if (G > 0 && !(ok = WAIT(s_empty + 1, (G - 1) & 1))) break;  // dP of box G-1 read
           tc_fence_after();
@@ -684,23 +722,7 @@ __global__ void __launch_bounds__(kThreads64, 1)
           mbar_arrive(qt_full);
         }
       }
-      int jt = 0, jy = 0, jx = 0;
       for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
-        const int ko[3] = {jt << g.lt, jy << g.ly, jx << g.lx};
-        if (++jx == tbk.nb[2]) {
-          jx = 0;
-          if (++jy == tbk.nb[1]) {
-            jy = 0;
-            ++jt;
-          }
-        }
-        const bool full = block_full(g, tbk, ko);
-        uint32_t kmask = ~0u;
-        if (!full) {
-          int kl[3];
-          block_row(g, ko, c4 * 32 + lane, kl);
-          kmask = __ballot_sync(0xffffffffu, inside(tbk, kl));
-        }
         if (!(ok = WAIT(s_full, G & 1))) break;
         tc_fence_after();
         uint32_t sv[32], dv[32], pk[16];
@@ -709,10 +731,7 @@ __global__ void __launch_bounds__(kThreads64, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(s_empty);  // the next box's S may overwrite this one
-        if (full)
-          q_p<false>(sv, 0u, sl2, nL);  // sv <- P' (FP32)
-        else
-          q_p<true>(sv, kmask, sl2, nL);
+        q_p(sv, sl2, nL);  // sv <- P' (FP32); masked keys carry -1e30 from the extension step
         if (!(ok = WAIT(s_full + 1, G & 1))) break;
         tc_fence_after();
         tmem_ld32(tl + C::kColDP + c4 * 32, dv);
@@ -742,11 +761,14 @@ __global__ void __launch_bounds__(kThreads64, 1)
       const int64_t tok = qvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
       const bool single = qvalid && single_cover(g, p);
       const int c0 = c4 * 16;
-      row_epilogue16<OutT>(tl + C::kColDQ + c0, g.scale, qvalid, single,
-                           static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * kD + c0, a.dq_s + qslot * kD + c0);
+      uint32_t rq[16];
+      tmem_ld16(tl + C::kColDQ + c0, rq);
+      tmem_wait_ld(rq);
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
+      if (lane == 0) mbar_arrive(acc_empty);  // released before the stores
+      row_store16<OutT>(rq, g.scale, qvalid, single, static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * kD + c0,
+                        a.dq_s + qslot * kD + c0);
       ++W;
     }
   }

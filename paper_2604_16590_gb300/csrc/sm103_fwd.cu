@@ -73,6 +73,7 @@ struct FwdArgs {
   float* ot;
   int items;  // B*nh * ntiles * nbmax_tot
   uint32_t flags;  // GATTN_FLAG_*
+  int pad_R;  // box rows of every geometry of the launch (rows pad_R..127 of each block are zeroed once)
   // ragged mode (serving): per-request descriptors and device-side counts
   const ReqDesc* reqs;
   const int64_t* counts;
@@ -134,7 +135,7 @@ __device__ __forceinline__ bool resolve(const FwdArgs& a, const CUtensorMap* tq,
   it.tile = r % g.ntiles;
   it.bh = r / g.ntiles;
   it.req = req;
-  if (RAGGED && it.bh >= g.B * g.nh) {
+  if (RAGGED && (it.bh >= g.B * g.nh || g.R != a.pad_R)) {
     set_status(kStatusBounds);
     return false;
   }
@@ -347,6 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  zero_pad_rows(smem, (1 + 2 * C::kStages) * C::kHalves, a.pad_R);  // Q and the K and V rings
   if (threadIdx.x == 0) {
     mbar_init(q_full, 1);
     mbar_init(q_empty, kMathWarps);
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int o[3];
         block_origin(g, tbk, qb, o);
         if (!(ok = mbar_wait<set_status_fwd>(q_empty, (W & 1) ^ 1, abort_flag))) break;
-        mbar_arrive_expect_tx(q_full, C::kBlock);
+        mbar_arrive_expect_tx(q_full, C::kHalves * g.R * 128);
         q_arm = 1;
         q_par = W & 1;
         for (int h = 0; h < C::kHalves; ++h)
@@ -421,13 +423,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           block_origin(g, tbk, j, o);
           const int c1 = tbk.tb.lo[2] + o[2], c2 = tbk.tb.lo[1] + o[1], c3 = tbk.tb.lo[0] + o[0];
           if (!(ok = mbar_wait<set_status_fwd>(k_empty + st, (n & 1) ^ 1, abort_flag))) break;
-          mbar_arrive_expect_tx(k_full + st, C::kBlock);
+          mbar_arrive_expect_tx(k_full + st, C::kHalves * g.R * 128);
           k_arm |= 1u << st;
           k_par = (k_par & ~(1u << st)) | ((n & 1) << st);
           for (int h = 0; h < C::kHalves; ++h)
             tma_load_5d(smem + C::kK + st * C::kBlock + h * 16384, it.tk, k_full + st, 64 * h, c1, c2, c3, bh);
           if (!(ok = mbar_wait<set_status_fwd>(v_empty + st, (n & 1) ^ 1, abort_flag))) break;
-          mbar_arrive_expect_tx(v_full + st, C::kBlock);
+          mbar_arrive_expect_tx(v_full + st, C::kHalves * g.R * 128);
           v_arm |= 1u << st;
           v_par = (v_par & ~(1u << st)) | ((n & 1) << st);
           for (int h = 0; h < C::kHalves; ++h)
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int jt = 0, jy = 0, jx = 0;
       for (int j = 0; j < tbk.NB; ++j, ++G) {
         const uint32_t sb = G & 1, pb = G % C::kPBufs;
-        const int ko[3] = {jt << g.lt, jy << g.ly, jx << g.lx};
+        const int ko[3] = {jt * g.bt, jy * g.by, jx * g.bx};
         if (++jx == tbk.nb[2]) {
           jx = 0;
           if (++jy == tbk.nb[1]) {
@@ -663,6 +665,7 @@ cudaError_t run_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
   a.reqs = nullptr;
   a.counts = nullptr;
   a.flags = flags;
+  a.pad_R = g.R;
   const int64_t items = (int64_t)g.B * g.nh * g.ntiles * g.nbmax_tot;
   if (items >= (1LL << 31)) return cudaErrorNotSupported;
   a.items = (int)items;
@@ -681,12 +684,13 @@ cudaError_t run_fwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
 }
 
 template <int D>
-cudaError_t run_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, cudaStream_t st) {
+cudaError_t run_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, int pad_R, cudaStream_t st) {
   using C = FwdCfg<D>;
   FwdArgs a;
   memset(&a, 0, sizeof(a));
   a.reqs = reqs;
   a.counts = counts;
+  a.pad_R = pad_R;
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof(dummy));
   auto kern = sm103_fwd_kernel<D, __nv_bfloat16, true>;
@@ -698,9 +702,10 @@ cudaError_t run_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, cudaStrea
 
 }  // namespace
 
-cudaError_t launch_sm103_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, int d, cudaStream_t st) {
-  if (d == 64) return launch_sm103_fwd64_ragged(reqs, counts, st);
-  if (d == 128) return run_fwd_ragged<128>(reqs, counts, st);
+cudaError_t launch_sm103_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, int d, int box_rows,
+                                    cudaStream_t st) {
+  if (d == 64) return launch_sm103_fwd64_ragged(reqs, counts, box_rows, st);
+  if (d == 128) return run_fwd_ragged<128>(reqs, counts, box_rows, st);
   return cudaErrorNotSupported;
 }
 

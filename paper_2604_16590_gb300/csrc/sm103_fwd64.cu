@@ -24,7 +24,8 @@
 //   warp 2        issuer of the P V products (a thread's mbarrier waits stall
 //                 until its own issued MMAs drain, so the two product streams
 //                 come from two threads)
-//   warp 3        idle (completes the first warpgroup)
+//   warp 3        key-mask writer: for a key block with padding rows or rows
+//                 outside the tile, the bias row of its stage (see below)
 //   warps 4..7    softmax + epilogue of box A, warps 8..11 of box B: one warp
 //                 per TMEM lane quadrant, one thread per query row owning all
 //                 128 key columns (no cross-warp reduction)
@@ -32,6 +33,14 @@
 // softmax threads hold a whole row of scores: 128 x 72 + 2 x 128 x 216 =
 // 384 x 168, the launch's allocation.
 // TMEM (512 columns): S_x at 128 x, P_x at 256 + 64 x, O_x at 384 + 64 x.
+//
+// Key masking without a masked softmax: a key block that contains padding rows
+// or keys outside the tile gets one more K = 16 step in its S product, a
+// column of ones times the block's bias row (0 or -1e30 per key), so the
+// masked scores arrive as -1e30 and their probabilities are exactly 0.  The
+// softmax threads then run one branch-free form for every block (a second,
+// masked form of the exponential loop measured 19 % slower even where it was
+// never taken).
 //
 // Ragged mode (the serving engine): the work items of all active requests in
 // one launch; each item resolves through the request table in device memory
@@ -60,13 +69,20 @@ constexpr uint32_t kRegsLow = 72, kRegsHigh = 216;  // 128 x 72 + 256 x 216 = 38
 constexpr float kRescaleLog2 = 8.f;
 
 struct Cfg {
-  static constexpr int kQ = 0;  // Q_A at kQ, Q_B at kQ + kBox
-  static constexpr int kK = 2 * kBox;
+  // two Q buffers (items alternate): buffer b holds Q_A at kQ + 2 b kBox, Q_B after it
+  static constexpr int kQ = 0;
+  static constexpr int kK = 4 * kBox;
   static constexpr int kV = kK + kStages * kBox;
-  static constexpr int kBar = kV + kStages * kBox;
-  // q_full, q_empty, k_full[S], k_empty[S], v_full[S], v_empty[S],
+  // Key-mask extension operands, K-major without swizzle (128 rows x 16 B,
+  // then 2 KB of zeros for K-columns 8..15): the A operand has 1 in K-column 0
+  // of every row; stage s of the B operand holds the key block's bias
+  // (0 for a key of the tile, -1e30 for a padding row or a key outside it).
+  static constexpr int kOnes = kV + kStages * kBox;
+  static constexpr int kBias = kOnes + 4096;
+  static constexpr int kBar = kBias + kStages * 4096;
+  // q_full[2], q_empty[2], k_full[S], k_empty[S], v_full[S], v_empty[S],
   // per box: s_full, s_empty, p_full, p_empty, o_full, o_empty; drain[2], never
-  static constexpr int kNumBars = 2 + 4 * kStages + 2 * 6 + 3;
+  static constexpr int kNumBars = 4 + 4 * kStages + 2 * 6 + 3;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kSmem = kMisc + 16 + 1024;
 };
@@ -81,6 +97,7 @@ struct Fwd64Args {
   float* ot;
   int items;  // B*nh * ntiles * box pairs
   uint32_t flags;
+  int pad_R;  // box rows of every geometry of the launch (rows pad_R..127 of each block are zeroed once)
   // ragged mode (serving): per-request descriptors and device-side counts
   const ReqDesc* reqs;
   const int64_t* counts;
@@ -145,7 +162,7 @@ __device__ __forceinline__ bool resolve(const Fwd64Args& a, const CUtensorMap* t
   it.tile = r % g.ntiles;
   it.bh = r / g.ntiles;
   it.req = req;
-  if (RAGGED && (it.bh >= g.B * g.nh || g.d != kD)) {
+  if (RAGGED && (it.bh >= g.B * g.nh || g.d != kD || g.R != a.pad_R)) {
     set_status(kStatusBounds);
     return false;
   }
@@ -153,32 +170,20 @@ __device__ __forceinline__ bool resolve(const Fwd64Args& a, const CUtensorMap* t
 }
 
 // running max of 32 scores into 4 partial maxima (3-input max)
-template <bool MASK>
-__device__ __forceinline__ void chunk_max(const uint32_t* r, uint32_t mbits, float (&mx)[4]) {
+__device__ __forceinline__ void chunk_max(const uint32_t* r, float (&mx)[4]) {
 #pragma unroll
-  for (int i = 0; i < 32; i += 2) {
-    float x0 = __uint_as_float(r[i]), x1 = __uint_as_float(r[i + 1]);
-    if (MASK) {
-      x0 = (mbits >> i) & 1u ? x0 : -INFINITY;
-      x1 = (mbits >> (i + 1)) & 1u ? x1 : -INFINITY;
-    }
-    mx[(i >> 1) & 3] = fmax3(mx[(i >> 1) & 3], x0, x1);
-  }
+  for (int i = 0; i < 32; i += 2)
+    mx[(i >> 1) & 3] = fmax3(mx[(i >> 1) & 3], __uint_as_float(r[i]), __uint_as_float(r[i + 1]));
 }
 
 // exp2 of 32 scores -> 16 BF16 pairs, row sum in packed FP32 pairs
-template <bool MASK>
-__device__ __forceinline__ void exp_chunk(const uint32_t* r, uint32_t mbits, uint64_t s2, uint64_t nm2,
-                                          uint64_t (&acc)[4], uint32_t (&pk)[16]) {
+__device__ __forceinline__ void exp_chunk(const uint32_t* r, uint64_t s2, uint64_t nm2, uint64_t (&acc)[4],
+                                          uint32_t (&pk)[16]) {
 #pragma unroll
   for (int i = 0; i < 32; i += 2) {
     float a0, a1;
     f2unpack(ffma2(u2pack(r[i], r[i + 1]), s2, nm2), a0, a1);
-    float p0 = ex2(a0), p1 = ex2(a1);
-    if (MASK) {
-      p0 = (mbits >> i) & 1u ? p0 : 0.f;
-      p1 = (mbits >> (i + 1)) & 1u ? p1 : 0.f;
-    }
+    const float p0 = ex2(a0), p1 = ex2(a1);
     acc[(i >> 1) & 3] = fadd2(acc[(i >> 1) & 3], f2pack(p0, p1));
     pk[i >> 1] = pack_bf16(p0, p1);
   }
@@ -212,9 +217,9 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kBar);
-  uint64_t* q_full = bars;
-  uint64_t* q_empty = bars + 1;
-  uint64_t* k_full = bars + 2;
+  uint64_t* q_full = bars;       // [2]
+  uint64_t* q_empty = bars + 2;  // [2]
+  uint64_t* k_full = bars + 4;
   uint64_t* k_empty = k_full + kStages;
   uint64_t* v_full = k_empty + kStages;
   uint64_t* v_empty = v_full + kStages;
@@ -231,11 +236,22 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  zero_pad_rows(smem, 4 + 2 * kStages, a.pad_R);  // both Q buffers, the K and V rings
+  // the ones operand (1 in K-column 0 of each of its 128 rows) and the zero
+  // K-columns 8..15 of it and of every bias stage
+  for (int r = threadIdx.x; r < (1 + kStages) * 256; r += kThreadsF) {
+    const int blk = r >> 8, rr = r & 255;
+    const uint4 v = (blk == 0 && rr < 128) ? make_uint4(0x00003F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+    if (blk == 0 || rr >= 128) *reinterpret_cast<uint4*>(smem + C::kOnes + blk * 4096 + rr * 16) = v;
+  }
+  fence_proxy_async_smem();
   if (threadIdx.x == 0) {
-    mbar_init(q_full, 1);
-    mbar_init(q_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(q_full + b, 1);
+      mbar_init(q_empty + b, 1);
+    }
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(k_full + s, 1);
+      mbar_init(k_full + s, 2);  // the K load (producer) and the stage's bias row (mask writer)
       mbar_init(k_empty + s, 1);
       mbar_init(v_full + s, 1);
       mbar_init(v_empty + s, 1);
@@ -291,20 +307,23 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           tmap_acquire(it.tq);  // this launch's descriptor table may hold a new map here
           last_req = it.req;
         }
-        if (!(ok = WAIT(q_empty, (W & 1) ^ 1))) break;
-        mbar_arrive_expect_tx(q_full, nact * kBox);
-        q_arm = 1;
-        q_par = W & 1;
+        // Q of this item goes to buffer W & 1, so it loads while the previous
+        // item's score products still read the other buffer
+        const uint32_t qb = W & 1, qn = (W >> 1) & 1;
+        if (!(ok = WAIT(q_empty + qb, qn ^ 1))) break;
+        mbar_arrive_expect_tx(q_full + qb, nact * g.R * 128);
+        q_arm |= 1u << qb;
+        q_par = (q_par & ~(1u << qb)) | (qn << qb);
         for (int x = 0; x < nact; ++x) {
           int o[3];
           block_origin(g, tbk, qa + x, o);
-          tma_load_5d(smem + C::kQ + x * kBox, it.tq, q_full, 0, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
-                      tbk.tb.lo[0] + o[0], bh);
+          tma_load_5d(smem + C::kQ + (2 * qb + x) * kBox, it.tq, q_full + qb, 0, tbk.tb.lo[2] + o[2],
+                      tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
         }
         int jt = 0, jy = 0, jx = 0;
         for (int j = 0; j < tbk.NB; ++j, ++G) {
           const uint32_t st = G % kStages, n = G / kStages;
-          const int c1 = tbk.tb.lo[2] + (jx << g.lx), c2 = tbk.tb.lo[1] + (jy << g.ly), c3 = tbk.tb.lo[0] + (jt << g.lt);
+          const int c1 = tbk.tb.lo[2] + (jx * g.bx), c2 = tbk.tb.lo[1] + (jy * g.by), c3 = tbk.tb.lo[0] + (jt * g.bt);
           if (++jx == tbk.nb[2]) {
             jx = 0;
             if (++jy == tbk.nb[1]) {
@@ -313,12 +332,12 @@ __global__ void __launch_bounds__(kThreadsF, 1)
             }
           }
           if (!(ok = WAIT(k_empty + st, (n & 1) ^ 1))) break;
-          mbar_arrive_expect_tx(k_full + st, kBox);
+          mbar_arrive_expect_tx(k_full + st, g.R * 128);
           k_arm |= 1u << st;
           k_par = (k_par & ~(1u << st)) | ((n & 1) << st);
           tma_load_5d(smem + C::kK + st * kBox, it.tk, k_full + st, 0, c1, c2, c3, bh);
           if (!(ok = WAIT(v_empty + st, (n & 1) ^ 1))) break;
-          mbar_arrive_expect_tx(v_full + st, kBox);
+          mbar_arrive_expect_tx(v_full + st, g.R * 128);
           v_arm |= 1u << st;
           v_par = (v_par & ~(1u << st)) | ((n & 1) << st);
           tma_load_5d(smem + C::kV + st * kBox, it.tv, v_full + st, 0, c1, c2, c3, bh);
@@ -327,7 +346,8 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       }
       if (!ok) {
         // let every load this thread issued land before the CTA exits
-        if (q_arm) mbar_wait<set_status_f64>(q_full, q_par, abort_flag, false);
+        for (int b = 0; b < 2; ++b)
+          if (q_arm & (1u << b)) mbar_wait<set_status_f64>(q_full + b, (q_par >> b) & 1, abort_flag, false);
         for (int s = 0; s < kStages; ++s) {
           if (k_arm & (1u << s)) mbar_wait<set_status_f64>(k_full + s, (k_par >> s) & 1, abort_flag, false);
           if (v_arm & (1u << s)) mbar_wait<set_status_f64>(v_full + s, (v_par >> s) & 1, abort_flag, false);
@@ -338,6 +358,8 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       constexpr uint32_t idS = idesc_bf16(128, 128, 0);
       const uint64_t dQ0 = sw128_desc(smem_u32(smem + C::kQ), 16, 1024);
       const uint64_t dK0 = sw128_desc(smem_u32(smem + C::kK), 16, 1024);
+      const uint64_t dOnes = noswz_desc(smem_u32(smem + C::kOnes), 2048, 128);
+      const uint64_t dBias0 = noswz_desc(smem_u32(smem + C::kBias), 2048, 128);
       uint32_t G = 0, W = 0, GX0 = 0, GX1 = 0;
       bool ok = true;
       if (a.flags & GATTN_FLAG_TEST_STALL)  // failure-detection hook: a wait that cannot complete
@@ -345,16 +367,22 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
         Item it;
         if (!resolve<RAGGED>(a, &tq, &tk, &tv, w, it)) continue;
+        const Geom& g = *it.g;
         TileBlocks tbk;
-        tile_blocks(*it.g, it.tile, tbk);
+        tile_blocks(g, it.tile, tbk);
         const int qa = 2 * it.pair;
         if (qa >= tbk.NB) continue;
         const int nact = qa + 1 < tbk.NB ? 2 : 1;
-        if (!(ok = WAIT(q_full, W & 1))) break;  // Q_A, Q_B in shared memory
-        for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
+        const uint32_t qb = W & 1;
+        if (!(ok = WAIT(q_full + qb, (W >> 1) & 1))) break;  // Q_A, Q_B of this item in shared memory
+        const bool all_full = tile_all_full(g, tbk);
+        BlockWalk bw;
+        for (int j = 0; j < tbk.NB && ok; ++j, ++G, bw.next(tbk)) {
           const uint32_t st = G % kStages;
+          // a masked block's bias row was filled by the mask writer
+          const bool masked = !all_full && !bw.full(g, tbk);
           if (!(ok = WAIT(k_full + st, (G / kStages) & 1))) break;
-          const uint64_t dk = dmove(dK0, st * kBox);
+          const uint64_t dk = dmove(dK0, st * kBox), db = dmove(dBias0, st * 4096);
 #pragma unroll
           for (int x = 0; x < 2; ++x) {
             if (x >= nact) break;
@@ -362,10 +390,11 @@ __global__ void __launch_bounds__(kThreadsF, 1)
             // S_x is free once the softmax threads have read the previous scores
             if (gx > 0 && !(ok = WAIT(s_empty(x), (gx - 1) & 1))) break;
             tc_fence_after();
-            const uint64_t dq = dmove(dQ0, x * kBox);
+            const uint64_t dq = dmove(dQ0, (2 * qb + x) * kBox);
 #pragma unroll
             for (int ks = 0; ks < kD / 16; ++ks)
               umma_bf16(tmem + col_s(x), dmove(dq, ks * 32), dmove(dk, ks * 32), idS, ks > 0);
+            if (masked) umma_bf16(tmem + col_s(x), dOnes, db, idS, 1u);  // + bias of each key column
             umma_commit(s_full(x));
             ++gx;
           }
@@ -373,7 +402,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           umma_commit(k_empty + st);
         }
         if (!ok) break;
-        umma_commit(q_empty);  // Q_A, Q_B no longer read
+        umma_commit(q_empty + qb);  // Q_A, Q_B of this item no longer read
         ++W;
       }
       umma_commit(drain);
@@ -420,6 +449,41 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       }
       umma_commit(drain + 1);
       mbar_wait<set_status_f64>(drain + 1, 0, abort_flag, false);
+    } else if (warp == 3) {
+      // ---------------------------------------------------------- key-mask writer
+      // One arrival on k_full per stage use (the stage's second arrival), in
+      // the producer's order.  It first waits until the stage is free again,
+      // which also guarantees that the previous phase of k_full completed.
+      const uint32_t neg = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(-1e30f));
+      uint32_t G = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+        Item it;
+        if (!resolve<RAGGED>(a, &tq, &tk, &tv, w, it)) continue;
+        const Geom& g = *it.g;
+        TileBlocks tbk;
+        tile_blocks(g, it.tile, tbk);
+        if (2 * it.pair >= tbk.NB) continue;
+        for (int j = 0; j < tbk.NB; ++j, ++G) {
+          const uint32_t st = G % kStages, n = G / kStages;
+          int ko[3];
+          block_origin(g, tbk, j, ko);
+          if (lane == 0) ok = WAIT(k_empty + st, (n & 1) ^ 1);
+          ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+          if (!ok) break;
+          if (!block_full(g, tbk, ko)) {
+            for (int r = lane; r < 128; r += 32) {
+              int kl[3];
+              block_row(g, ko, r, kl);
+              *reinterpret_cast<uint4*>(smem + C::kBias + st * 4096 + r * 16) =
+                  make_uint4(inside(tbk, kl) ? 0u : neg, 0u, 0u, 0u);
+            }
+            fence_proxy_async_smem();  // the tensor core reads what these lanes wrote
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(k_full + st);
+        }
+      }
     }
   } else {
     setmaxnreg_inc<kRegsHigh>();
@@ -448,26 +512,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       block_row(g, qo, row, ql);
       const bool qvalid = inside(tbk, ql);
       float m = -INFINITY, l = 0.f;
-      int jt = 0, jy = 0, jx = 0;
       for (int j = 0; j < tbk.NB; ++j, ++GX) {
-        const int ko[3] = {jt << g.lt, jy << g.ly, jx << g.lx};
-        if (++jx == tbk.nb[2]) {
-          jx = 0;
-          if (++jy == tbk.nb[1]) {
-            jy = 0;
-            ++jt;
-          }
-        }
-        uint32_t km[4] = {~0u, ~0u, ~0u, ~0u};
-        const bool full = block_full(g, tbk, ko);
-        if (!full) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            int kl[3];
-            block_row(g, ko, c * 32 + lane, kl);
-            km[c] = __ballot_sync(0xffffffffu, inside(tbk, kl));
-          }
-        }
         if (!(ok = WAIT(s_full(x), GX & 1))) break;
         tc_fence_after();
         // the row's 128 scores into registers, then S_x is released
@@ -484,17 +529,11 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(s_empty(x));
         float mx[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
-        if (full) {
-          chunk_max<false>(s0, 0u, mx);
-          chunk_max<false>(s1, 0u, mx);
-          chunk_max<false>(s2r, 0u, mx);
-          chunk_max<false>(s3, 0u, mx);
-        } else {
-          chunk_max<true>(s0, km[0], mx);
-          chunk_max<true>(s1, km[1], mx);
-          chunk_max<true>(s2r, km[2], mx);
-          chunk_max<true>(s3, km[3], mx);
-        }
+        // masked keys carry -1e30 from the extension step: no mask here
+        chunk_max(s0, mx);
+        chunk_max(s1, mx);
+        chunk_max(s2r, mx);
+        chunk_max(s3, mx);
         const float mblk = fmaxf(fmaxf(mx[0], mx[1]), fmaxf(mx[2], mx[3])) * sl2;
         float f = 1.f;
         bool any_grow = false;
@@ -515,17 +554,10 @@ __global__ void __launch_bounds__(kThreadsF, 1)
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[i] = f2pack(0.f, 0.f);
         uint32_t pk0[16], pk1[16], pk2[16], pk3[16];
-        if (full) {
-          exp_chunk<false>(s0, 0u, s2, nm2, acc, pk0);
-          exp_chunk<false>(s1, 0u, s2, nm2, acc, pk1);
-          exp_chunk<false>(s2r, 0u, s2, nm2, acc, pk2);
-          exp_chunk<false>(s3, 0u, s2, nm2, acc, pk3);
-        } else {
-          exp_chunk<true>(s0, km[0], s2, nm2, acc, pk0);
-          exp_chunk<true>(s1, km[1], s2, nm2, acc, pk1);
-          exp_chunk<true>(s2r, km[2], s2, nm2, acc, pk2);
-          exp_chunk<true>(s3, km[3], s2, nm2, acc, pk3);
-        }
+        exp_chunk(s0, s2, nm2, acc, pk0);
+        exp_chunk(s1, s2, nm2, acc, pk1);
+        exp_chunk(s2r, s2, nm2, acc, pk2);
+        exp_chunk(s3, s2, nm2, acc, pk3);
         float lsum = 0.f;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -563,12 +595,20 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       const bool single = qvalid && single_cover(g, p);
       OutT* dst_out = static_cast<OutT*>(it.out) + ((int64_t)bh * g.N + tok) * kD;
       float* dst_scr = it.ot + slot * kD;
-      uint32_t r[32];
+      // the whole O row into registers, then O_x is released at once: the next
+      // item's first P V may overwrite it while this row is scaled and stored
+      uint32_t r0[32], r1[32];
+      tmem_ld32(tO, r0);
+      tmem_ld32(tO + 32, r1);
+      tmem_wait_ld(r0);
+      tmem_wait_ld(r1);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(o_empty(x));
+      if (qvalid) {
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        tmem_ld32(tO + c * 32, r);
-        tmem_wait_ld(r);
-        if (qvalid) {
+        for (int c = 0; c < 2; ++c) {
+          const uint32_t* r = c == 0 ? r0 : r1;
 #pragma unroll
           for (int e = 0; e < 32; e += 4) {
             const float4 v4 = make_float4(__uint_as_float(r[e]) * inv, __uint_as_float(r[e + 1]) * inv,
@@ -580,9 +620,6 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           }
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(o_empty(x));
     }
   }
   tc_fence_before();
@@ -603,6 +640,7 @@ cudaError_t run_fwd64(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16
   a.lse2 = lse2;
   a.ot = ot;
   a.flags = flags;
+  a.pad_R = g.R;
   const int64_t items = (int64_t)g.B * g.nh * g.ntiles * box_pairs(g);
   if (items >= (1LL << 31)) return cudaErrorNotSupported;
   a.items = (int)items;
@@ -631,11 +669,12 @@ cudaError_t launch_sm103_fwd64(const Geom& g, const __nv_bfloat16* q, const __nv
 
 int fwd64_ragged_items(const Geom& g) { return g.nh * g.ntiles * box_pairs(g); }
 
-cudaError_t launch_sm103_fwd64_ragged(const ReqDesc* reqs, const int64_t* counts, cudaStream_t st) {
+cudaError_t launch_sm103_fwd64_ragged(const ReqDesc* reqs, const int64_t* counts, int box_rows, cudaStream_t st) {
   Fwd64Args a;
   memset(&a, 0, sizeof(a));
   a.reqs = reqs;
   a.counts = counts;
+  a.pad_R = box_rows;
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof(dummy));
   auto kern = fwd64_kernel<__nv_bfloat16, true>;

@@ -159,6 +159,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gattn_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "gattn_validate": ([D], ctypes.c_int),
         "gattn_num_tiles": ([D], ctypes.c_int64),
+        "gattn_block_shape": ([D, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "gattn_saved_bytes": ([D], S),
         "gattn_bwd_workspace_bytes": ([D], S),
         "gattn_fwd": ([D, P, P, P, P, P, S, P], ctypes.c_int),
@@ -247,6 +248,13 @@ def gattn_validate(desc) -> int:
 
 def gattn_num_tiles(desc) -> int:
     return load_library().gattn_num_tiles(ctypes.byref(desc))
+
+
+def gattn_block_shape(desc):
+    """(status, (bt, by, bx)): the token box the tensor-core kernels use."""
+    arr = (ctypes.c_int32 * 3)()
+    st = load_library().gattn_block_shape(ctypes.byref(desc), arr)
+    return st, (int(arr[0]), int(arr[1]), int(arr[2]))
 
 
 def gattn_saved_bytes(desc) -> int:

@@ -52,6 +52,8 @@ WORKLOADS = {
     "c2_262k_p1": Workload("c2_262k_p1", 1, 4, 64, (32, 64, 128), (32, 16, 32), (0, 4, 8), 0.5, 20262, "bf16"),
     # same grid, small tiles near the HBM/tensor ridge: core 1 x 16 x 16, halo 0/4/4
     "c2_262k_s": Workload("c2_262k_s", 4, 16, 64, (32, 64, 128), (1, 16, 16), (0, 4, 4), 0.5, 20262, "bf16"),
+    # the small-tile geometry with 1 x 4 heads (1/16 of the units, each tensor 134 MB > L2): profiling case
+    "c2_262k_s1": Workload("c2_262k_s1", 1, 4, 64, (32, 64, 128), (1, 16, 16), (0, 4, 4), 0.5, 20262, "bf16"),
     # long temporal context: 2048 frames x 32 x 64, d = 128, Tiles = 16 along time, halo 8 frames
     "c3_4m_p": Workload("c3_4m_p", 1, 8, 128, (2048, 32, 64), (128, 32, 64), (8, 0, 0), 0.5, 20263, "bf16"),
     # gradient check size: 32 x 32, 2 heads, d = 32

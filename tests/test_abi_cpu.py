@@ -146,3 +146,43 @@ def test_gated_dps_linear_sizes_and_validation_on_the_host(lib):
     assert gattn.gattn_linear_fwd(ld, 16, 16, 16, 16, 16, ws_bytes=1 << 30, stream=0) == 1
     ld.d, ld.N = 64, 0
     assert gattn.gattn_linear_fwd(ld, 16, 16, 16, 16, 16, ws_bytes=1 << 30, stream=0) == 1
+
+
+def _extents(G, c, h):
+    return [min((k + 1) * c + h, G) - max(k * c - h, 0) for k in range(-(-G // c))]
+
+
+@pytest.mark.parametrize(
+    "grid,core,halo",
+    [((32, 64, 128), (32, 16, 32), (0, 4, 8)), ((32, 64, 128), (1, 16, 16), (0, 4, 4)),
+     ((2048, 32, 64), (128, 32, 64), (8, 0, 0)), ((7, 32, 64), (1, 16, 16), (0, 4, 4)),
+     ((3, 10, 13), (2, 4, 5), (1, 2, 2)), ((16, 256, 256), (16, 64, 64), (0, 8, 8))],
+)
+def test_block_shape_minimises_padded_work(lib, grid, core, halo):
+    """The tensor-core kernels cut every extended tile into boxes of at most 128
+    tokens, one 128-row MMA block each; the library's shape must minimise the
+    padded work sum_tiles (number of boxes)^2 over every such shape."""
+    d = gattn.make_desc(1, 1, 64, grid, core, halo, in_dtype="bf16")
+    st, box = gattn.gattn_block_shape(d)
+    assert st == 0 and all(b >= 1 for b in box) and box[0] * box[1] * box[2] <= 128
+    ext = [_extents(grid[a], core[a], halo[a]) for a in range(3)]
+
+    def cost(b):
+        out = 1
+        for a in range(3):
+            out *= sum((-(-e // b[a])) ** 2 for e in ext[a])
+        return out
+
+    best = min(cost((bt, by, bx)) for bt in range(1, 129) for by in range(1, 128 // bt + 1)
+               for bx in range(1, 128 // (bt * by) + 1))
+    assert cost(box) == best
+
+
+def test_block_shape_of_the_paper_and_small_tile_regimes(lib):
+    # Tiles = 16 on 32 x 64 x 128: 4 x 4 x 8 boxes tile every extended tile exactly
+    st, box = gattn.gattn_block_shape(gattn.make_desc(4, 16, 64, (32, 64, 128), (32, 16, 32), (0, 4, 8)))
+    assert st == 0 and box == (4, 4, 8)
+    # 16 x 16 cores with a 4-token halo: 24 x 24 extended tiles in five 5 x 24 boxes
+    st, box = gattn.gattn_block_shape(gattn.make_desc(4, 16, 64, (32, 64, 128), (1, 16, 16), (0, 4, 4)))
+    assert st == 0 and box == (1, 5, 24)
+    assert gattn.gattn_block_shape(_desc(d=48))[0] == 1
