@@ -492,7 +492,10 @@ def run_dps(steps, warmup, dev, w, rank=0, n_prop=20):
 def run_linear(steps, warmup, dev, w, rank=0, peaks=None):
     """Factorised linear attention (phi = elu + 1; not an operator of the paper)
     on the bench workload's shape: B x heads x N tokens x d = 64, BF16 Q, K, V
-    N(0, 0.5) (4 x 2.15 GB moved per call, > L2, no flush)."""
+    N(0, 0.5), upstream gradient N(0, 1).  Forward: 4 x 2.15 GB moved per call
+    (q, k, v read, out written); backward: 7 x 2.15 GB (q, k, v, dout read;
+    dq, dk, dv written); both > L2, no flush.  Device time from CUDA events on
+    the launching stream."""
     import torch
 
     from paper_2604_16590_gb300 import gattn
@@ -500,40 +503,57 @@ def run_linear(steps, warmup, dev, w, rank=0, peaks=None):
     from paper_2604_16590_gb300.replicas import replica_seed
 
     q, k, v = qkv(w.shape, replica_seed(w.seed + 91, rank), w.std, "bf16", device=dev)
+    (g,) = qkv(w.shape, replica_seed(w.seed + 93, rank), 1.0, "bf16", device=dev, n=1)
     desc = gattn.linear_desc(q)
     out = torch.empty_like(q)
+    dq, dk, dv = torch.empty_like(q), torch.empty_like(q), torch.empty_like(q)
     ws = torch.empty(gattn.gattn_linear_workspace_bytes(desc), dtype=torch.uint8, device=dev)
+    wsb = torch.empty(gattn.gattn_linear_bwd_workspace_bytes(desc), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def call():
+    def fwd():
         gattn.check(gattn.gattn_linear_fwd(desc, q, k, v, out, ws, stream=stream), "gattn_linear_fwd")
 
-    for _ in range(warmup):
-        call()
-    torch.cuda.synchronize()
-    gattn.gattn_profile_enable(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        call()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    prof = gattn.gattn_profile_read()
-    gattn.gattn_profile_enable(False)
-    gattn.check(gattn.gattn_stream_status(), "linear status")
-    ms = e0.elapsed_time(e1) / steps
-    alg = 4 * q.numel() * 2  # q, k, v read once, out written once
+    def bwd():
+        gattn.check(gattn.gattn_linear_bwd(desc, q, k, v, g, ws, dq, dk, dv, wsb, stream=stream), "gattn_linear_bwd")
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        gattn.gattn_profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = gattn.gattn_profile_read()
+        gattn.gattn_profile_enable(False)
+        gattn.check(gattn.gattn_stream_status(), "linear status")
+        return e0.elapsed_time(e1) / steps, prof
+
+    ms_f, prof_f = timed(fwd)
+    ms_b, prof_b = timed(bwd)
+    nd2 = q.numel() * 2
     peak, src = (peaks[0], peaks[3]) if peaks else (6800.0, "fallback")
-    gbs = alg / (ms * 1e-3) / 1e9
+    gbs_f, gbs_b = 4 * nd2 / (ms_f * 1e-3) / 1e9, 7 * nd2 / (ms_b * 1e-3) / 1e9
+    gbs_fb = 11 * nd2 / ((ms_f + ms_b) * 1e-3) / 1e9
+    kernels = {n: {"launches": c, "ms_per_launch": t / c} for n, (c, t) in {**prof_f, **prof_b}.items()}
     res = {
         "workload": f"{w.name} shape: B={w.B}, {w.nh} heads, N={w.N}, d={w.d}, BF16, phi = elu + 1",
-        "ms_per_call": ms, "calls": steps, "warmup": warmup, "tokens_per_s": w.B * w.N / (ms * 1e-3),
-        "kernels": {n: {"launches": c, "ms_per_launch": t / c} for n, (c, t) in prof.items()},
-        "roofline": {"kernel": "linear (summary + combine + query)", "bound": "hbm", "achieved": gbs, "peak": peak,
-                     "unit": "GB/s", "frac": gbs / peak, "peak_source": f"hbm_gbs of {src}",
-                     "algorithmic_bytes": alg, "traffic": None},
+        "ms_per_call": ms_f, "ms_backward": ms_b, "calls": steps, "warmup": warmup,
+        "tokens_per_s": w.B * w.N / (ms_f * 1e-3), "fwd_bwd_tokens_per_s": w.B * w.N / ((ms_f + ms_b) * 1e-3),
+        "kernels": kernels,
+        "roofline": {"kernel": "linear forward (summary + combine + query)", "bound": "hbm", "achieved": gbs_f,
+                     "peak": peak, "unit": "GB/s", "frac": gbs_f / peak, "peak_source": f"hbm_gbs of {src}",
+                     "algorithmic_bytes": 4 * nd2, "traffic": None},
+        "roofline_backward": {"kernel": "linear backward (query pass + combine + key pass)", "bound": "hbm",
+                              "achieved": gbs_b, "peak": peak, "unit": "GB/s", "frac": gbs_b / peak,
+                              "peak_source": f"hbm_gbs of {src}", "algorithmic_bytes": 7 * nd2, "traffic": None},
+        "fwd_bwd_gbs": gbs_fb, "fwd_bwd_frac": gbs_fb / peak,
     }
-    del q, k, v, out, ws
+    del q, k, v, g, out, dq, dk, dv, ws, wsb
     torch.cuda.empty_cache()
     return res
 

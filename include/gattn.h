@@ -298,7 +298,8 @@ gattn_status gattn_fwd_noalloc(const gattn_desc *desc, const void *q, const void
  * kernel (TMA tiles, phi in shared memory, S accumulated by tcgen05 in TMEM,
  * z in FP32 registers), a fixed-order compensated combine of the chunk
  * partials, and a query pass (tcgen05 phi(Q) S with S split into BF16 high
- * and low parts, FP32 denominator).  Deterministic.  Forward only.
+ * and low parts, FP32 denominator).  Deterministic.  The workspace keeps the
+ * combined summary (S^T as BF16 high and low parts, z) for the backward.
  */
 typedef struct {
   int32_t B, nh, d;
@@ -309,6 +310,38 @@ typedef struct {
 size_t gattn_linear_workspace_bytes(const gattn_linear_desc *desc);
 gattn_status gattn_linear_fwd(const gattn_linear_desc *desc, const void *q, const void *k, const void *v,
                               void *out, void *ws, size_t ws_bytes, gattn_stream_t stream);
+
+/*
+ * Backward of the loss sum(out * dout) of the factorised linear attention,
+ * with den_i = phi(q_i) . z and phi'(x) = 1 (x > 0), exp(x) (x <= 0):
+ *
+ *     dq_i = (S^T dout_i - z (dout_i . out_i)) / den_i * phi'(q_i)
+ *     dS   = sum_i phi(q_i) (dout_i / den_i)^T       (query-side gradient summary)
+ *     dz   = -sum_i phi(q_i) (dout_i . out_i) / den_i
+ *     dk_n = (dS v_n + dz) * phi'(k_n),   dv_n = dS^T phi(k_n)
+ *
+ * (dout_i . out_i is recomputed as phi(q_i) . S^T dout_i / den_i; out is not
+ * read).  Not an operator of the paper, like the forward.
+ *   q, k, v, dout  [B, nh, N, d] BF16 (device), d = 64.
+ *   saved          the workspace gattn_linear_fwd filled for these q, k, v,
+ *                  unchanged since (its combined S and z are read);
+ *                  saved_bytes >= gattn_linear_workspace_bytes(desc).
+ *   dq, dk, dv     [B, nh, N, d] BF16 (device), fully overwritten.
+ *   ws             device workspace of gattn_linear_bwd_workspace_bytes(desc)
+ *                  bytes (per-chunk FP32 partials of dS and dz, the combined
+ *                  dS as BF16 high and low parts).
+ * Launches: a query pass (tcgen05 products S^T dout and phi(Q)^T (dout / den)
+ * with BF16 high and low parts of both factors; dq; split-N partials of dS and
+ * dz), a fixed-order compensated combine, and a key pass (tcgen05 products
+ * V dS^T and phi(K) dS; dk, dv).  Deterministic.  All pointers 16-byte
+ * aligned.  GATTN_ERR_INVALID_ARG on a bad desc or pointer,
+ * GATTN_ERR_WORKSPACE when saved or ws is short, GATTN_ERR_CUDA when a launch
+ * fails.
+ */
+size_t gattn_linear_bwd_workspace_bytes(const gattn_linear_desc *desc);
+gattn_status gattn_linear_bwd(const gattn_linear_desc *desc, const void *q, const void *k, const void *v,
+                              const void *dout, const void *saved, size_t saved_bytes, void *dq, void *dk,
+                              void *dv, void *ws, size_t ws_bytes, gattn_stream_t stream);
 
 /*
  * One diffusion posterior-sampling step with the GPA denoiser (arXiv
@@ -438,7 +471,8 @@ gattn_status gattn_stream_status(gattn_stream_t stream);
 typedef struct {
   char name[24];    /* "fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd",
                        "compress", "compress_combine", "gated_mix", "dps_residual", "dps_update",
-                       "linear_summary", "linear_combine", "linear_query" */
+                       "linear_summary", "linear_combine", "linear_query", "linear_bwd_query",
+                       "linear_bwd_combine", "linear_bwd_key" */
   int64_t launches;
   double total_ms;
 } gattn_kernel_stat;

@@ -15,7 +15,8 @@ namespace gattn {
 namespace {
 const char* const kKernelNames[kKCount] = {"fwd_tiles", "merge_fwd", "bwd_prep", "bwd_dkdv", "bwd_dq", "merge_bwd",
                                            "compress", "compress_combine", "gated_mix", "dps_residual",
-                                           "dps_update", "linear_summary", "linear_combine", "linear_query"};
+                                           "dps_update", "linear_summary", "linear_combine", "linear_query",
+                                           "linear_bwd_query", "linear_bwd_combine", "linear_bwd_key"};
 struct ProfRecord {
   int kernel;
   cudaEvent_t start, stop;
@@ -351,6 +352,24 @@ gattn_status gattn_linear_fwd(const gattn_linear_desc* l, const void* q, const v
     if (!p || !aligned16(p)) return GATTN_ERR_INVALID_ARG;
   if (ws_bytes < linear_ws_bytes(l->B, l->nh, l->N)) return GATTN_ERR_WORKSPACE;
   return from_cuda(launch_linear(q, k, v, out, ws, l->B, l->nh, l->N, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t gattn_linear_bwd_workspace_bytes(const gattn_linear_desc* l) {
+  if (!linear_desc_ok(l)) return 0;
+  return linear_bwd_layout(l->B, l->nh, l->N).bytes;
+}
+
+gattn_status gattn_linear_bwd(const gattn_linear_desc* l, const void* q, const void* k, const void* v,
+                              const void* dout, const void* saved, size_t saved_bytes, void* dq, void* dk, void* dv,
+                              void* ws, size_t ws_bytes, gattn_stream_t stream) {
+  if (!linear_desc_ok(l)) return GATTN_ERR_INVALID_ARG;
+  const void* ptrs[] = {q, k, v, dout, saved, dq, dk, dv, ws};
+  for (const void* p : ptrs)
+    if (!p || !aligned16(p)) return GATTN_ERR_INVALID_ARG;
+  if (saved_bytes < linear_ws_bytes(l->B, l->nh, l->N) || ws_bytes < linear_bwd_layout(l->B, l->nh, l->N).bytes)
+    return GATTN_ERR_WORKSPACE;
+  return from_cuda(launch_linear_bwd(q, k, v, dout, saved, dq, dk, dv, ws, l->B, l->nh, l->N,
+                                     reinterpret_cast<cudaStream_t>(stream)));
 }
 
 // Posterior-sampling step (Sec. III-A).  Workspace: attention saved state,

@@ -86,7 +86,7 @@ uint32_t fetch_status_linear();
 // ---- per-kernel device timing (gattn_profile_*); no-ops unless enabled
 enum KernelId : int {
   kKFwdTiles = 0, kKMergeFwd, kKBwdPrep, kKBwdDkdv, kKBwdDq, kKMergeBwd, kKCompress, kKCompressCombine, kKGatedMix, kKDpsResidual, kKDpsUpdate, kKLinearSummary, kKLinearCombine,
-  kKLinearQuery, kKCount
+  kKLinearQuery, kKLinearBwdQuery, kKLinearBwdCombine, kKLinearBwdKey, kKCount
 };
 void prof_begin(int kernel, cudaStream_t st);
 void prof_end(int kernel, cudaStream_t st);
@@ -121,9 +121,25 @@ struct LinearPlan {
   int ntiles, chunk_tiles, chunks, q_tiles_per_cta;
 };
 LinearPlan linear_plan(int B, int nh, int64_t N);
+// Forward workspace: per-chunk FP32 partials of S and z, then the combined
+// S^T as BF16 high and low parts ([BH, 64 (v), 64 (k)] each) and z (FP32
+// [BH, 64]); the backward reads the last three.
+struct LinearLayout {
+  size_t part_S, part_z, sth, stl, z, bytes;
+};
+LinearLayout linear_layout(int B, int nh, int64_t N);
 size_t linear_ws_bytes(int B, int nh, int64_t N);
 cudaError_t launch_linear(const void* q, const void* k, const void* v, void* out, void* ws, int B, int nh, int64_t N,
                           cudaStream_t st);
+// Backward workspace: per-chunk FP32 partials of the query-side gradient
+// summary dS (64 x 64) and dz (64), then dS and dS^T as BF16 high and low
+// parts and dz (FP32).
+struct LinearBwdLayout {
+  size_t part_dS, part_dz, dsh, dsl, dsth, dstl, dz, bytes;
+};
+LinearBwdLayout linear_bwd_layout(int B, int nh, int64_t N);
+cudaError_t launch_linear_bwd(const void* q, const void* k, const void* v, const void* dout, const void* saved,
+                              void* dq, void* dk, void* dv, void* ws, int B, int nh, int64_t N, cudaStream_t st);
 // posterior-sampling step, elementwise parts (dps.cu)
 cudaError_t launch_dps_residual(const Geom& g, const float* D, const float* y, const uint8_t* mask, void* r,
                                 bool r_bf16, cudaStream_t st);

@@ -12,11 +12,16 @@
 //   la_summary_kernel  split-N summary: each CTA streams a chunk of 128-token
 //                      K and V tiles (TMA, 128-byte swizzle) through a ring of
 //                      shared-memory stages; four warps apply phi to the K tile
-//                      in place (BF16, rows past N zeroed) and accumulate z in
-//                      FP32; one thread issues S += phi(K)^T V on tcgen05
-//                      (M = N = 64, both operands MN-major, K = 128 tokens)
-//                      with the accumulator in TMEM; the CTA writes its FP32
-//                      partial S and z.
+//                      (rows past N zeroed) and write it as BF16 high parts in
+//                      place and low parts (phi - hi) in the stage's third
+//                      tile, and accumulate z in FP32 from the unrounded phi;
+//                      one thread issues S += phi_hi(K)^T V + phi_lo(K)^T V on
+//                      tcgen05 (M = N = 64, both operands MN-major, K = 128
+//                      tokens) with the accumulator in TMEM; the CTA writes its
+//                      FP32 partial S and z.  (With phi(K) rounded to BF16, S
+//                      and z would carry independent 2^-9 per-term errors that
+//                      the centred sum of the query gradient amplifies to
+//                      ~5e-3 RMS.)
 //   la_combine_kernel  per (b, h), the chunk partials summed in fixed order
 //                      with Kahan compensation; S^T split into BF16 high and
 //                      low parts (S = hi + lo to ~2^-17) for the query pass.
@@ -38,7 +43,8 @@ using namespace sm103;
 constexpr int kD = 64;
 constexpr int kTile = 128;                 // tokens per tile
 constexpr int kTileBytes = kTile * kD * 2;  // 16 KB, one TMA box
-constexpr int kStagesS = 3;                 // summary ring: K + V per stage
+constexpr int kStagesS = 2;                 // summary ring: K (phi hi) + V + phi lo per stage
+constexpr int kSumStage = 3 * kTileBytes;
 constexpr int kThreadsL = 192;              // producer, issuer, 4 math warps
 constexpr int kQStages = 2;
 
@@ -78,6 +84,36 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // byte offset of 16-byte chunk c of row r in a 128-byte-swizzled tile
 __device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
+// phi of eight BF16 values (unrounded, FP32)
+__device__ __forceinline__ void phi8(uint4 u, bool valid, float (&f)[8]) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f[2 * i] = valid ? phi_f(__uint_as_float(w[i] << 16)) : 0.f;
+    f[2 * i + 1] = valid ? phi_f(__uint_as_float(w[i] & 0xffff0000u)) : 0.f;
+  }
+}
+// BF16 high parts of eight floats and the BF16 low parts (x - hi)
+__device__ __forceinline__ void split8(const float (&f)[8], uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    h[i] = pack_bf16(f[2 * i], f[2 * i + 1]);
+    l[i] = pack_bf16(f[2 * i] - __uint_as_float(h[i] << 16), f[2 * i + 1] - __uint_as_float(h[i] & 0xffff0000u));
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+// hi + lo of eight BF16 pairs
+__device__ __forceinline__ void join8(uint4 hi, uint4 lo, float (&f)[8]) {
+  const uint32_t h[4] = {hi.x, hi.y, hi.z, hi.w}, l[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f[2 * i] = __uint_as_float(h[i] << 16) + __uint_as_float(l[i] << 16);
+    f[2 * i + 1] = __uint_as_float(h[i] & 0xffff0000u) + __uint_as_float(l[i] & 0xffff0000u);
+  }
+}
+
 struct SumArgs {
   int N, BH, ntiles, chunk_tiles;
   float* ws_S;  // [chunks, BH, 64, 64]
@@ -89,7 +125,7 @@ __global__ void __launch_bounds__(kThreadsL) la_summary_kernel(const __grid_cons
                                                                const SumArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStagesS * 2 * kTileBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStagesS * kSumStage);
   uint64_t* kready = full + kStagesS;
   uint64_t* empty = kready + kStagesS;
   uint64_t* done = empty + kStagesS;
@@ -129,7 +165,7 @@ __global__ void __launch_bounds__(kThreadsL) la_summary_kernel(const __grid_cons
         mbar_arrive_expect_tx(full + st, 2 * kTileBytes);
         armed |= 1u << st;
         par = (par & ~(1u << st)) | ((n & 1) << st);
-        uint8_t* dst = smem + st * 2 * kTileBytes;
+        uint8_t* dst = smem + st * kSumStage;
         tma_load_5d(dst, &tk, full + st, 0, t * kTile, 0, 0, bh);
         tma_load_5d(dst + kTileBytes, &tv, full + st, 0, t * kTile, 0, 0, bh);
       }
@@ -147,11 +183,14 @@ __global__ void __launch_bounds__(kThreadsL) la_summary_kernel(const __grid_cons
         const int st = G % kStagesS, n = G / kStagesS;
         if (!(ok = LWAIT(kready + st, n & 1))) break;
         tc_fence_after();
-        const uint32_t base = smem_u32(smem + st * 2 * kTileBytes);
+        const uint32_t base = smem_u32(smem + st * kSumStage);
         const uint64_t dA = sw128_desc(base, 16384, 1024), dB = sw128_desc(base + kTileBytes, 16384, 1024);
+        const uint64_t dAl = sw128_desc(base + 2 * kTileBytes, 16384, 1024);
 #pragma unroll
         for (int ks = 0; ks < kTile / 16; ++ks)
           umma_bf16(tmem, dmove(dA, ks * 2048), dmove(dB, ks * 2048), idS, (G > 0 || ks > 0) ? 1u : 0u);
+#pragma unroll
+        for (int ks = 0; ks < kTile / 16; ++ks) umma_bf16(tmem, dmove(dAl, ks * 2048), dmove(dB, ks * 2048), idS, 1u);
         umma_commit(empty + st);
       }
       umma_commit(done);
@@ -168,13 +207,17 @@ __global__ void __launch_bounds__(kThreadsL) la_summary_kernel(const __grid_cons
     for (int t = t0, G = 0; t < t1; ++t, ++G) {
       const int st = G % kStagesS, n = G / kStagesS;
       if (!(ok = LWAIT(full + st, n & 1))) break;
-      uint8_t* kt = smem + st * 2 * kTileBytes;
+      uint8_t* kt = smem + st * kSumStage;
       const bool valid = t * kTile + r < a.N;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         uint4* p = reinterpret_cast<uint4*>(kt + swz(r, c));
         float f[8];
-        *p = phi_chunk(*p, valid, f);
+        phi8(*p, valid, f);
+        uint4 hi, lo;
+        split8(f, hi, lo);
+        *p = hi;
+        *reinterpret_cast<uint4*>(kt + 2 * kTileBytes + swz(r, c)) = lo;
 #pragma unroll
         for (int e = 0; e < 8; ++e) zacc[c * 8 + e] += f[e];
       }
@@ -451,7 +494,537 @@ __global__ void __launch_bounds__(kThreadsQ, 3) la_query_kernel(const __grid_con
   }
 }
 
-constexpr int kSumSmem = kStagesS * 2 * kTileBytes + 1024 + 256;
+// =================================================================== backward
+// For the loss sum(out * g) (g = dOut) with den_i = phi(q_i) . z:
+//   U_i     = S^T g_i (d-vector, u_k = sum_v S[k][v] g_i[v])
+//   go_i    = phi(q_i) . U_i / den_i                      (= g_i . out_i)
+//   dq_i    = (U_i - z go_i) / den_i * phi'(q_i)
+//   dS      = sum_i phi(q_i) (g_i / den_i)^T,  dz = -sum_i phi(q_i) go_i / den_i
+//   dk_n    = (dS v_n + dz) * phi'(k_n),       dv_n = dS^T phi(k_n)
+// with phi'(x) = 1 for x > 0 and exp(x) = phi(x) otherwise, so phi' follows
+// from phi alone (phi > 1 exactly when x > 0).  Three kernels, HBM-bound: a
+// query pass (dq, split-N partials of dS and dz), a fixed-order compensated
+// combine, and a key pass (dk, dv).  Products whose accuracy matters for the
+// cancellation in dq (U) and for the N-long sums (dS) use BF16 high and low
+// parts of both factors (S, phi(q), g / den), so the rounding of the tensor
+// core's BF16 operands stays below 2^-16; phi(k) and dS in the key pass are
+// split the same way.
+
+constexpr int kThreadsB = 192;               // producer, issuer, 4 math warps
+constexpr int kBQStage = 4 * kTileBytes;     // q -> phi hi, g -> g/den hi, phi lo, g/den lo
+constexpr int kBQStages = 2;
+constexpr int kBQBase = 16384 + 1024;        // S^T hi, lo (8 KB each), then z and padding
+constexpr int kBQSmem = kBQBase + kBQStages * kBQStage + 1024 + 256;
+constexpr int kBKStage = 3 * kTileBytes;     // k -> phi hi, v, phi lo
+constexpr int kBKStages = 2;
+constexpr int kBKBase = 32768 + 1024;        // dS hi, lo, dS^T hi, lo, then dz and padding
+constexpr int kBKSmem = kBKBase + kBKStages * kBKStage + 1024 + 256;
+
+// 64 x 64 BF16 matrices (rows of 128 bytes) from global memory into 128-byte-
+// swizzled shared memory, n of them; every math thread (tid 0..127) takes part
+__device__ __forceinline__ void load_mats(int tid, int n, const __nv_bfloat16* const* src, uint8_t* const* dst) {
+  for (int i = tid; i < n * 64 * 8; i += 128) {
+    const int m = i >> 9, row = (i >> 3) & 63, c = i & 7;
+    *reinterpret_cast<uint4*>(dst[m] + swz(row, c)) = *reinterpret_cast<const uint4*>(src[m] + row * kD + c * 8);
+  }
+}
+
+struct BQArgs {
+  int N, BH, ntiles, chunk_tiles;
+  const __nv_bfloat16* sth;  // forward summary S^T, high and low parts [BH, 64 (v), 64 (k)]
+  const __nv_bfloat16* stl;
+  const float* zt;           // [BH, 64]
+  __nv_bfloat16* dq;
+  float* part_dS;            // [chunks, BH, 64 (k), 64 (v)]
+  float* part_dz;            // [chunks, BH, 64]
+};
+
+// Query pass, grid (chunks, BH): every CTA streams a chunk of 128-token query
+// tiles (q and g by TMA through two stages).
+//   issuer: U = G S (A = g tile K-major, B = S^T parts MN-major), into one of
+//           two TMEM buffers; then dS += phi(Q)^T (G / den) over the tile's 128
+//           tokens (both operands MN-major; chains hi.hi, hi.lo, lo.hi)
+//   math:   per row, phi(q) and den in FP32, phi's parts over the q tile and a
+//           side buffer; with U: go, dq (stored), dz; g / den's parts over the
+//           g tile and a side buffer
+// At the end the CTA writes its dS and dz partials.
+__global__ void __launch_bounds__(kThreadsB, 1) la_bwd_query_kernel(const __grid_constant__ CUtensorMap tq,
+                                                                    const __grid_constant__ CUtensorMap tg,
+                                                                    const BQArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sHi = smem;
+  uint8_t* sLo = smem + 8192;
+  float* zs = reinterpret_cast<float*>(smem + 16384);
+  auto stq = [&](int st) { return smem + kBQBase + st * kBQStage; };  // q, then phi hi
+  auto stg = [&](int st) { return stq(st) + kTileBytes; };              // g, then g/den hi
+  auto stpl = [&](int st) { return stq(st) + 2 * kTileBytes; };         // phi lo
+  auto stgl = [&](int st) { return stq(st) + 3 * kTileBytes; };         // g/den lo
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kBQBase + kBQStages * kBQStage);
+  uint64_t* empty = full + kBQStages;
+  uint64_t* ufull = empty + kBQStages;
+  uint64_t* ufree = ufull + kBQStages;
+  uint64_t* dsready = ufree + kBQStages;
+  uint64_t* sready = dsready + kBQStages;
+  uint64_t* done = sready + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int chunk = blockIdx.x, bh = blockIdx.y;
+  const int t0 = chunk * a.chunk_tiles, t1 = min(a.ntiles, t0 + a.chunk_tiles);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kBQStages; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
+      mbar_init(ufull + i, 1);
+      mbar_init(ufree + i, 4);
+      mbar_init(dsready + i, 4);
+    }
+    mbar_init(sready, 4);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    prefetch_tmap(&tq);
+    prefetch_tmap(&tg);
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, 256);  // U buffers at columns 0 and 64, dS (M = 64) at 128
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ------------------------------------------------ TMA producer
+      uint32_t armed = 0, par = 0;
+      bool ok = true;
+      for (int t = t0, G = 0; t < t1; ++t, ++G) {
+        const int st = G % kBQStages, n = G / kBQStages;
+        if (!(ok = LWAIT(empty + st, (n & 1) ^ 1))) break;
+        mbar_arrive_expect_tx(full + st, 2 * kTileBytes);
+        armed |= 1u << st;
+        par = (par & ~(1u << st)) | ((n & 1) << st);
+        tma_load_5d(stq(st), &tq, full + st, 0, t * kTile, 0, 0, bh);
+        tma_load_5d(stg(st), &tg, full + st, 0, t * kTile, 0, 0, bh);
+      }
+      if (!ok)
+        for (int s2 = 0; s2 < kBQStages; ++s2)
+          if (armed & (1u << s2)) mbar_wait<set_status_l>(full + s2, (par >> s2) & 1, abort_flag, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ------------------------------------------------ MMA issuer
+      constexpr uint32_t idU = idesc_bf16(128, 64, 1);                 // B = S^T rows, MN-major
+      constexpr uint32_t idDS = idesc_bf16(64, 64, 1) | (1u << 15);    // A and B MN-major
+      const uint64_t dSh = sw128_desc(smem_u32(sHi), 16384, 1024), dSl = sw128_desc(smem_u32(sLo), 16384, 1024);
+      bool ok = LWAIT(sready, 0);
+      for (int t = t0, G = 0; t < t1 && ok; ++t, ++G) {
+        const int st = G % kBQStages, n = G / kBQStages, b = G & 1;
+        if (!(ok = LWAIT(full + st, n & 1))) break;
+        if (G >= 2 && !(ok = LWAIT(ufree + b, ((G >> 1) - 1) & 1))) break;
+        tc_fence_after();
+        const uint32_t tU = tmem + 64 * b;
+        const uint64_t dG = sw128_desc(smem_u32(stg(st)), 16, 1024);
+#pragma unroll
+        for (int ks = 0; ks < kD / 16; ++ks) umma_bf16(tU, dmove(dG, ks * 32), dmove(dSh, ks * 2048), idU, ks > 0);
+#pragma unroll
+        for (int ks = 0; ks < kD / 16; ++ks) umma_bf16(tU, dmove(dG, ks * 32), dmove(dSl, ks * 2048), idU, 1u);
+        umma_commit(ufull + b);
+        // dS += phi(Q)^T (G / den) once the math warps wrote both operands' parts
+        if (!(ok = LWAIT(dsready + st, n & 1))) break;
+        tc_fence_after();
+        const uint64_t pH = sw128_desc(smem_u32(stq(st)), 16384, 1024), pL = sw128_desc(smem_u32(stpl(st)), 16384, 1024);
+        const uint64_t gH = sw128_desc(smem_u32(stg(st)), 16384, 1024), gL = sw128_desc(smem_u32(stgl(st)), 16384, 1024);
+#pragma unroll
+        for (int ks = 0; ks < kTile / 16; ++ks)
+          umma_bf16(tmem + 128, dmove(pH, ks * 2048), dmove(gH, ks * 2048), idDS, (G > 0 || ks > 0) ? 1u : 0u);
+#pragma unroll
+        for (int ks = 0; ks < kTile / 16; ++ks) umma_bf16(tmem + 128, dmove(pH, ks * 2048), dmove(gL, ks * 2048), idDS, 1u);
+#pragma unroll
+        for (int ks = 0; ks < kTile / 16; ++ks) umma_bf16(tmem + 128, dmove(pL, ks * 2048), dmove(gH, ks * 2048), idDS, 1u);
+        umma_commit(empty + st);
+      }
+      umma_commit(done);
+      if (!ok) *abort_flag = 1;
+    }
+  } else {
+    // ------------------------------------------------------------------ math warps
+    const int quad = warp & 3;
+    const int r = quad * 32 + lane;  // tile row = TMEM lane
+    const int tid = threadIdx.x - 64;
+    {
+      const __nv_bfloat16* src[2] = {a.sth + (size_t)bh * kD * kD, a.stl + (size_t)bh * kD * kD};
+      uint8_t* dst[2] = {sHi, sLo};
+      load_mats(tid, 2, src, dst);
+      if (tid < kD) zs[tid] = a.zt[(size_t)bh * kD + tid];
+      fence_proxy_async_smem();
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // z visible to all four math warps
+      __syncwarp();
+      if (lane == 0) mbar_arrive(sready);
+    }
+    float dz[kD];
+#pragma unroll
+    for (int i = 0; i < kD; ++i) dz[i] = 0.f;
+    bool ok = true;
+    for (int t = t0, G = 0; t < t1; ++t, ++G) {
+      const int st = G % kBQStages, n = G / kBQStages, b = G & 1;
+      const bool valid = (int64_t)t * kTile + r < a.N;
+      if (!(ok = LWAIT(full + st, n & 1))) break;
+      // phi(q) in FP32, den, and phi's parts (hi over q, lo in its own tile)
+      float den = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        uint4* pq = reinterpret_cast<uint4*>(stq(st) + swz(r, c));
+        float f[8];
+        phi8(*pq, valid, f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) den = fmaf(f[e], zs[c * 8 + e], den);
+        uint4 hi, lo;
+        split8(f, hi, lo);
+        *pq = hi;
+        *reinterpret_cast<uint4*>(stpl(st) + swz(r, c)) = lo;
+      }
+      const float inv = valid ? 1.f / den : 0.f;
+      // U row (the U product is done: the g tile may be overwritten below)
+      if (!(ok = LWAIT(ufull + b, n & 1))) break;
+      tc_fence_after();
+      uint32_t u0[32], u1[32];
+      const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + 64 * b;
+      tmem_ld32(tl, u0);
+      tmem_ld32(tl + 32, u1);
+      tmem_wait_ld(u0);
+      tmem_wait_ld(u1);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ufree + b);
+      float go = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float f[8];
+        join8(*reinterpret_cast<const uint4*>(stq(st) + swz(r, c)), *reinterpret_cast<const uint4*>(stpl(st) + swz(r, c)),
+              f);
+        const uint32_t* u = c < 4 ? u0 + 8 * c : u1 + 8 * (c - 4);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) go = fmaf(f[e], __uint_as_float(u[e]), go);
+      }
+      go *= inv;
+      // dq = (U - z go) / den * phi'(q); dz -= phi(q) go / den
+      __nv_bfloat16* dst = a.dq + ((size_t)bh * a.N + (size_t)t * kTile + r) * kD;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float f[8];
+        join8(*reinterpret_cast<const uint4*>(stq(st) + swz(r, c)), *reinterpret_cast<const uint4*>(stpl(st) + swz(r, c)),
+              f);
+        const uint32_t* u = c < 4 ? u0 + 8 * c : u1 + 8 * (c - 4);
+        uint32_t pk[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+          const float d0 = (__uint_as_float(u[e]) - zs[c * 8 + e] * go) * inv * (f[e] > 1.f ? 1.f : f[e]);
+          const float d1 = (__uint_as_float(u[e + 1]) - zs[c * 8 + e + 1] * go) * inv * (f[e + 1] > 1.f ? 1.f : f[e + 1]);
+          pk[e >> 1] = pack_bf16(d0, d1);
+          dz[c * 8 + e] = fmaf(-f[e], go * inv, dz[c * 8 + e]);
+          dz[c * 8 + e + 1] = fmaf(-f[e + 1], go * inv, dz[c * 8 + e + 1]);
+        }
+        if (valid) *reinterpret_cast<uint4*>(dst + c * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+      // g / den: hi over the g tile, lo in its own tile
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        uint4* pg = reinterpret_cast<uint4*>(stg(st) + swz(r, c));
+        const uint4 u = *pg;
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+        float f[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          f[2 * i] = __uint_as_float(w[i] << 16) * inv;
+          f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u) * inv;
+        }
+        uint4 hi, lo;
+        split8(f, hi, lo);
+        *pg = hi;
+        *reinterpret_cast<uint4*>(stgl(st) + swz(r, c)) = lo;
+      }
+      fence_proxy_async_smem();  // the tensor core reads what these threads wrote
+      __syncwarp();
+      if (lane == 0) mbar_arrive(dsready + st);
+    }
+    // epilogue: dS partial (M = 64: rows 16q .. 16q+15 in lanes 0..15 of lane
+    // quadrant q) and dz reduced over the 128 rows in fixed order
+    const bool got = ok && LWAIT(done, 0);
+    tc_fence_after();
+    uint32_t s0[32], s1[32];
+    const uint32_t tq4 = tmem + ((uint32_t)(quad * 32) << 16) + 128;
+    tmem_ld32(tq4, s0);
+    tmem_ld32(tq4 + 32, s1);
+    tmem_wait_ld(s0);
+    tmem_wait_ld(s1);
+    const size_t part = (size_t)chunk * a.BH + bh;
+    if (got && lane < 16) {
+      float* dst = a.part_dS + (part * kD + quad * 16 + lane) * kD;
+#pragma unroll
+      for (int j = 0; j < 32; j += 4) {
+        *reinterpret_cast<float4*>(dst + j) = make_float4(__uint_as_float(s0[j]), __uint_as_float(s0[j + 1]),
+                                                          __uint_as_float(s0[j + 2]), __uint_as_float(s0[j + 3]));
+        *reinterpret_cast<float4*>(dst + 32 + j) = make_float4(
+            __uint_as_float(s1[j]), __uint_as_float(s1[j + 1]), __uint_as_float(s1[j + 2]), __uint_as_float(s1[j + 3]));
+      }
+    }
+    // the stages are idle once `done` completed: reuse them for the dz rows
+    float* zbuf = reinterpret_cast<float*>(smem + kBQBase);
+    if (got) {
+#pragma unroll
+      for (int i = 0; i < kD; ++i) zbuf[r * kD + i] = dz[i];
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (got && tid < kD) {
+      float sum = 0.f;
+      for (int i = 0; i < kTile; ++i) sum += zbuf[i * kD + tid];
+      a.part_dz[part * kD + tid] = sum;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
+struct BCombArgs {
+  int BH, chunks;
+  const float* part_dS;
+  const float* part_dz;
+  __nv_bfloat16 *dsh, *dsl;    // dS [BH, 64 (k), 64 (v)], high and low parts
+  __nv_bfloat16 *dsth, *dstl;  // dS^T [BH, 64 (v), 64 (k)]
+  float* dz;                   // [BH, 64]
+};
+
+// grid (BH, ceil((64 * 64 + 64) / 256)): one entry per thread, chunk
+// partials summed in ascending chunk order with Kahan compensation
+__global__ void __launch_bounds__(256) la_bwd_combine_kernel(const BCombArgs a) {
+  const int bh = blockIdx.x;
+  for (int e = blockIdx.y * 256 + threadIdx.x; e < kD * kD + kD; e += 256 * gridDim.y) {
+    const bool is_z = e >= kD * kD;
+    float sum = 0.f, comp = 0.f;
+    for (int c = 0; c < a.chunks; ++c) {
+      const size_t part = (size_t)c * a.BH + bh;
+      const float x = is_z ? a.part_dz[part * kD + (e - kD * kD)] : a.part_dS[part * kD * kD + e];
+      const float y = x - comp;
+      const float t = sum + y;
+      comp = (t - sum) - y;
+      sum = t;
+    }
+    if (is_z) {
+      a.dz[(size_t)bh * kD + (e - kD * kD)] = sum;
+    } else {
+      const int k = e / kD, v = e % kD;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(sum);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(sum - __bfloat162float(hi));
+      const size_t m = (size_t)bh * kD * kD;
+      a.dsh[m + k * kD + v] = hi;
+      a.dsl[m + k * kD + v] = lo;
+      a.dsth[m + v * kD + k] = hi;
+      a.dstl[m + v * kD + k] = lo;
+    }
+  }
+}
+
+struct BKArgs {
+  int N, BH, ntiles, tiles_per_cta;
+  const __nv_bfloat16 *dsh, *dsl, *dsth, *dstl;
+  const float* dz;
+  __nv_bfloat16* dk;
+  __nv_bfloat16* dv;
+};
+
+// Key pass, grid (ceil(ntiles / tiles_per_cta), BH): per 128-token key tile
+// (k and v by TMA through two stages)
+//   math:   phi(k)'s parts (hi over the k tile, lo in its own tile)
+//   issuer: P1 = V dS^T (A = v tile, B = dS rows; hi and lo) and P2 = phi(K) dS
+//           (A = phi parts, B = dS^T rows; chains hi.hi, hi.lo, lo.hi), into
+//           one of two TMEM buffer pairs
+//   math:   dk = (P1 + dz) * phi'(k), dv = P2, stored row by row
+// A stage is released by the issuer's commit and the four math warps together
+// (phi' is recomputed from phi's parts in the epilogue).
+__global__ void __launch_bounds__(kThreadsB, 1) la_bwd_key_kernel(const __grid_constant__ CUtensorMap tk,
+                                                                  const __grid_constant__ CUtensorMap tv,
+                                                                  const BKArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* mDh = smem;          // dS rows (k), hi
+  uint8_t* mDl = smem + 8192;   // dS rows, lo
+  uint8_t* mTh = smem + 16384;  // dS^T rows (v), hi
+  uint8_t* mTl = smem + 24576;  // dS^T rows, lo
+  float* dzs = reinterpret_cast<float*>(smem + 32768);
+  auto stk = [&](int st) { return smem + kBKBase + st * kBKStage; };  // k, then phi hi
+  auto stv = [&](int st) { return stk(st) + kTileBytes; };
+  auto stpl = [&](int st) { return stk(st) + 2 * kTileBytes; };        // phi lo
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kBKBase + kBKStages * kBKStage);
+  uint64_t* empty = full + kBKStages;
+  uint64_t* kready = empty + kBKStages;
+  uint64_t* pfull = kready + kBKStages;
+  uint64_t* pfree = pfull + kBKStages;
+  uint64_t* sready = pfree + kBKStages;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sready + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bh = blockIdx.y;
+  const int t0 = blockIdx.x * a.tiles_per_cta, t1 = min(a.ntiles, t0 + a.tiles_per_cta);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kBKStages; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 5);  // the issuer's commit and the four math warps
+      mbar_init(kready + i, 4);
+      mbar_init(pfull + i, 1);
+      mbar_init(pfree + i, 4);
+    }
+    mbar_init(sready, 4);
+    *abort_flag = 0;
+    fence_mbar_init();
+    prefetch_tmap(&tk);
+    prefetch_tmap(&tv);
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, 256);  // buffer b: P1 at 128 b, P2 at 128 b + 64
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ------------------------------------------------ TMA producer
+      uint32_t armed = 0, par = 0;
+      bool ok = true;
+      for (int t = t0, G = 0; t < t1; ++t, ++G) {
+        const int st = G % kBKStages, n = G / kBKStages;
+        if (!(ok = LWAIT(empty + st, (n & 1) ^ 1))) break;
+        mbar_arrive_expect_tx(full + st, 2 * kTileBytes);
+        armed |= 1u << st;
+        par = (par & ~(1u << st)) | ((n & 1) << st);
+        tma_load_5d(stk(st), &tk, full + st, 0, t * kTile, 0, 0, bh);
+        tma_load_5d(stv(st), &tv, full + st, 0, t * kTile, 0, 0, bh);
+      }
+      if (!ok)
+        for (int s2 = 0; s2 < kBKStages; ++s2)
+          if (armed & (1u << s2)) mbar_wait<set_status_l>(full + s2, (par >> s2) & 1, abort_flag, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ------------------------------------------------ MMA issuer
+      constexpr uint32_t idP = idesc_bf16(128, 64, 0);  // A, B K-major
+      const uint64_t bDh = sw128_desc(smem_u32(mDh), 16, 1024), bDl = sw128_desc(smem_u32(mDl), 16, 1024);
+      const uint64_t bTh = sw128_desc(smem_u32(mTh), 16, 1024), bTl = sw128_desc(smem_u32(mTl), 16, 1024);
+      bool ok = LWAIT(sready, 0);
+      for (int t = t0, G = 0; t < t1 && ok; ++t, ++G) {
+        const int st = G % kBKStages, n = G / kBKStages, b = G & 1;
+        if (!(ok = LWAIT(full + st, n & 1))) break;
+        if (!(ok = LWAIT(kready + st, n & 1))) break;
+        if (G >= 2 && !(ok = LWAIT(pfree + b, ((G >> 1) - 1) & 1))) break;
+        tc_fence_after();
+        const uint32_t tP1 = tmem + 128 * b, tP2 = tP1 + 64;
+        const uint64_t aV = sw128_desc(smem_u32(stv(st)), 16, 1024);
+        const uint64_t aH = sw128_desc(smem_u32(stk(st)), 16, 1024), aL = sw128_desc(smem_u32(stpl(st)), 16, 1024);
+#pragma unroll
+        for (int ks = 0; ks < kD / 16; ++ks) umma_bf16(tP1, dmove(aV, ks * 32), dmove(bDh, ks * 32), idP, ks > 0);
+#pragma unroll
+        for (int ks = 0; ks < kD / 16; ++ks) umma_bf16(tP1, dmove(aV, ks * 32), dmove(bDl, ks * 32), idP, 1u);
+#pragma unroll
+        for (int ks = 0; ks < kD / 16; ++ks) umma_bf16(tP2, dmove(aH, ks * 32), dmove(bTh, ks * 32), idP, ks > 0);
+#pragma unroll
+        for (int ks = 0; ks < kD / 16; ++ks) umma_bf16(tP2, dmove(aH, ks * 32), dmove(bTl, ks * 32), idP, 1u);
+#pragma unroll
+        for (int ks = 0; ks < kD / 16; ++ks) umma_bf16(tP2, dmove(aL, ks * 32), dmove(bTh, ks * 32), idP, 1u);
+        umma_commit(pfull + b);
+        umma_commit(empty + st);
+      }
+      if (!ok) *abort_flag = 1;
+    }
+  } else {
+    // ------------------------------------------------------------------ math warps
+    const int quad = warp & 3;
+    const int r = quad * 32 + lane;
+    const int tid = threadIdx.x - 64;
+    {
+      const size_t m = (size_t)bh * kD * kD;
+      const __nv_bfloat16* src[4] = {a.dsh + m, a.dsl + m, a.dsth + m, a.dstl + m};
+      uint8_t* dst[4] = {mDh, mDl, mTh, mTl};
+      load_mats(tid, 4, src, dst);
+      if (tid < kD) dzs[tid] = a.dz[(size_t)bh * kD + tid];
+      fence_proxy_async_smem();
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(sready);
+    }
+    bool ok = true;
+    for (int t = t0, G = 0; t < t1; ++t, ++G) {
+      const int st = G % kBKStages, n = G / kBKStages, b = G & 1;
+      const bool valid = (int64_t)t * kTile + r < a.N;
+      if (!(ok = LWAIT(full + st, n & 1))) break;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        uint4* pk = reinterpret_cast<uint4*>(stk(st) + swz(r, c));
+        float f[8];
+        phi8(*pk, true, f);
+        uint4 hi, lo;
+        split8(f, hi, lo);
+        *pk = hi;
+        *reinterpret_cast<uint4*>(stpl(st) + swz(r, c)) = lo;
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(kready + st);
+      if (!(ok = LWAIT(pfull + b, n & 1))) break;
+      tc_fence_after();
+      uint32_t p1a[32], p1b[32], p2a[32], p2b[32];
+      const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + 128 * b;
+      tmem_ld32(tl, p1a);
+      tmem_ld32(tl + 32, p1b);
+      tmem_ld32(tl + 64, p2a);
+      tmem_ld32(tl + 96, p2b);
+      tmem_wait_ld(p1a);
+      tmem_wait_ld(p1b);
+      tmem_wait_ld(p2a);
+      tmem_wait_ld(p2b);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(pfree + b);
+      const size_t row = ((size_t)bh * a.N + (size_t)t * kTile + r) * kD;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float f[8];
+        join8(*reinterpret_cast<const uint4*>(stk(st) + swz(r, c)), *reinterpret_cast<const uint4*>(stpl(st) + swz(r, c)),
+              f);
+        const uint32_t* p1 = c < 4 ? p1a + 8 * c : p1b + 8 * (c - 4);
+        const uint32_t* p2 = c < 4 ? p2a + 8 * c : p2b + 8 * (c - 4);
+        uint32_t ok4[4], ov4[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+          const float k0 = (__uint_as_float(p1[e]) + dzs[c * 8 + e]) * (f[e] > 1.f ? 1.f : f[e]);
+          const float k1 = (__uint_as_float(p1[e + 1]) + dzs[c * 8 + e + 1]) * (f[e + 1] > 1.f ? 1.f : f[e + 1]);
+          ok4[e >> 1] = pack_bf16(k0, k1);
+          ov4[e >> 1] = pack_bf16(__uint_as_float(p2[e]), __uint_as_float(p2[e + 1]));
+        }
+        if (valid) {
+          *reinterpret_cast<uint4*>(a.dk + row + c * 8) = make_uint4(ok4[0], ok4[1], ok4[2], ok4[3]);
+          *reinterpret_cast<uint4*>(a.dv + row + c * 8) = make_uint4(ov4[0], ov4[1], ov4[2], ov4[3]);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty + st);  // phi's parts read: the stage may be refilled
+    }
+    (void)ok;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
+constexpr int kSumSmem = kStagesS * kSumStage + 1024 + 256;
 constexpr int kQSmem = 16384 + (kQStages + 1) * kTileBytes + 1024 + 512;
 
 }  // namespace
@@ -468,16 +1041,25 @@ LinearPlan linear_plan(int B, int nh, int64_t N) {
   return p;
 }
 
-size_t linear_ws_bytes(int B, int nh, int64_t N) {
+LinearLayout linear_layout(int B, int nh, int64_t N) {
   const LinearPlan p = linear_plan(B, nh, N);
   const size_t BH = (size_t)B * nh;
-  return align_up((size_t)p.chunks * BH * kD * kD * 4) + align_up((size_t)p.chunks * BH * kD * 4) +
-         2 * align_up(BH * kD * kD * 2) + align_up(BH * kD * 4);
+  LinearLayout l;
+  l.part_S = 0;
+  l.part_z = l.part_S + align_up((size_t)p.chunks * BH * kD * kD * 4);
+  l.sth = l.part_z + align_up((size_t)p.chunks * BH * kD * 4);
+  l.stl = l.sth + align_up(BH * kD * kD * 2);
+  l.z = l.stl + align_up(BH * kD * kD * 2);
+  l.bytes = l.z + align_up(BH * kD * 4);
+  return l;
 }
+
+size_t linear_ws_bytes(int B, int nh, int64_t N) { return linear_layout(B, nh, N).bytes; }
 
 cudaError_t launch_linear(const void* q, const void* k, const void* v, void* out, void* ws, int B, int nh, int64_t N,
                           cudaStream_t st) {
   const LinearPlan p = linear_plan(B, nh, N);
+  const LinearLayout lay = linear_layout(B, nh, N);
   const int BH = B * nh;
   char* w = static_cast<char*>(ws);
   SumArgs sa;
@@ -485,20 +1067,16 @@ cudaError_t launch_linear(const void* q, const void* k, const void* v, void* out
   sa.BH = BH;
   sa.ntiles = p.ntiles;
   sa.chunk_tiles = p.chunk_tiles;
-  sa.ws_S = reinterpret_cast<float*>(w);
-  w += align_up((size_t)p.chunks * BH * kD * kD * 4);
-  sa.ws_z = reinterpret_cast<float*>(w);
-  w += align_up((size_t)p.chunks * BH * kD * 4);
+  sa.ws_S = reinterpret_cast<float*>(w + lay.part_S);
+  sa.ws_z = reinterpret_cast<float*>(w + lay.part_z);
   CombArgs ca;
   ca.BH = BH;
   ca.chunks = p.chunks;
   ca.ws_S = sa.ws_S;
   ca.ws_z = sa.ws_z;
-  ca.sth = reinterpret_cast<__nv_bfloat16*>(w);
-  w += align_up((size_t)BH * kD * kD * 2);
-  ca.stl = reinterpret_cast<__nv_bfloat16*>(w);
-  w += align_up((size_t)BH * kD * kD * 2);
-  ca.zt = reinterpret_cast<float*>(w);
+  ca.sth = reinterpret_cast<__nv_bfloat16*>(w + lay.sth);
+  ca.stl = reinterpret_cast<__nv_bfloat16*>(w + lay.stl);
+  ca.zt = reinterpret_cast<float*>(w + lay.z);
   QArgs qa;
   qa.N = (int)N;
   qa.BH = BH;
@@ -534,6 +1112,91 @@ cudaError_t launch_linear(const void* q, const void* k, const void* v, void* out
                                                                                                              qa);
   e = cudaGetLastError();
   prof_end(kKLinearQuery, st);
+  return e;
+}
+
+LinearBwdLayout linear_bwd_layout(int B, int nh, int64_t N) {
+  const LinearPlan p = linear_plan(B, nh, N);
+  const size_t BH = (size_t)B * nh;
+  LinearBwdLayout l;
+  l.part_dS = 0;
+  l.part_dz = l.part_dS + align_up((size_t)p.chunks * BH * kD * kD * 4);
+  l.dsh = l.part_dz + align_up((size_t)p.chunks * BH * kD * 4);
+  l.dsl = l.dsh + align_up(BH * kD * kD * 2);
+  l.dsth = l.dsl + align_up(BH * kD * kD * 2);
+  l.dstl = l.dsth + align_up(BH * kD * kD * 2);
+  l.dz = l.dstl + align_up(BH * kD * kD * 2);
+  l.bytes = l.dz + align_up(BH * kD * 4);
+  return l;
+}
+
+cudaError_t launch_linear_bwd(const void* q, const void* k, const void* v, const void* dout, const void* saved,
+                              void* dq, void* dk, void* dv, void* ws, int B, int nh, int64_t N, cudaStream_t st) {
+  const LinearPlan p = linear_plan(B, nh, N);
+  const LinearLayout fl = linear_layout(B, nh, N);
+  const LinearBwdLayout bl = linear_bwd_layout(B, nh, N);
+  const int BH = B * nh;
+  const char* sv = static_cast<const char*>(saved);
+  char* w = static_cast<char*>(ws);
+  BQArgs qa;
+  qa.N = (int)N;
+  qa.BH = BH;
+  qa.ntiles = p.ntiles;
+  qa.chunk_tiles = p.chunk_tiles;
+  qa.sth = reinterpret_cast<const __nv_bfloat16*>(sv + fl.sth);
+  qa.stl = reinterpret_cast<const __nv_bfloat16*>(sv + fl.stl);
+  qa.zt = reinterpret_cast<const float*>(sv + fl.z);
+  qa.dq = static_cast<__nv_bfloat16*>(dq);
+  qa.part_dS = reinterpret_cast<float*>(w + bl.part_dS);
+  qa.part_dz = reinterpret_cast<float*>(w + bl.part_dz);
+  BCombArgs ca;
+  ca.BH = BH;
+  ca.chunks = p.chunks;
+  ca.part_dS = qa.part_dS;
+  ca.part_dz = qa.part_dz;
+  ca.dsh = reinterpret_cast<__nv_bfloat16*>(w + bl.dsh);
+  ca.dsl = reinterpret_cast<__nv_bfloat16*>(w + bl.dsl);
+  ca.dsth = reinterpret_cast<__nv_bfloat16*>(w + bl.dsth);
+  ca.dstl = reinterpret_cast<__nv_bfloat16*>(w + bl.dstl);
+  ca.dz = reinterpret_cast<float*>(w + bl.dz);
+  BKArgs ka;
+  ka.N = (int)N;
+  ka.BH = BH;
+  ka.ntiles = p.ntiles;
+  ka.tiles_per_cta = p.q_tiles_per_cta;
+  ka.dsh = ca.dsh;
+  ka.dsl = ca.dsl;
+  ka.dsth = ca.dsth;
+  ka.dstl = ca.dstl;
+  ka.dz = ca.dz;
+  ka.dk = static_cast<__nv_bfloat16*>(dk);
+  ka.dv = static_cast<__nv_bfloat16*>(dv);
+
+  CUtensorMap mq, mg, mk, mv;
+  if (!make_tmap_5d(&mq, q, kD, (int)N, 1, 1, BH, kTile, 1, 1) || !make_tmap_5d(&mg, dout, kD, (int)N, 1, 1, BH, kTile, 1, 1) ||
+      !make_tmap_5d(&mk, k, kD, (int)N, 1, 1, BH, kTile, 1, 1) || !make_tmap_5d(&mv, v, kD, (int)N, 1, 1, BH, kTile, 1, 1))
+    return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(la_bwd_query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBQSmem)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(la_bwd_key_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBKSmem)) !=
+          cudaSuccess)
+    return e;
+  prof_begin(kKLinearBwdQuery, st);
+  la_bwd_query_kernel<<<dim3(p.chunks, BH), kThreadsB, kBQSmem, st>>>(mq, mg, qa);
+  e = cudaGetLastError();
+  prof_end(kKLinearBwdQuery, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(kKLinearBwdCombine, st);
+  la_bwd_combine_kernel<<<dim3(BH, (kD * kD + kD + 255) / 256), 256, 0, st>>>(ca);
+  e = cudaGetLastError();
+  prof_end(kKLinearBwdCombine, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(kKLinearBwdKey, st);
+  la_bwd_key_kernel<<<dim3((p.ntiles + p.q_tiles_per_cta - 1) / p.q_tiles_per_cta, BH), kThreadsB, kBKSmem, st>>>(
+      mk, mv, ka);
+  e = cudaGetLastError();
+  prof_end(kKLinearBwdKey, st);
   return e;
 }
 

@@ -8,6 +8,7 @@
 // visiting their covering tiles in ascending tile order (fixed order, no
 // atomics: bitwise reproducible run to run).
 #include "internal.cuh"
+#include "merge_common.cuh"
 
 GATTN_DEFINE_STATUS(merge)
 
@@ -83,6 +84,121 @@ __global__ void __launch_bounds__(kThreads) merge_fwd_kernel(Geom g, const float
   }
 }
 
+// The same merge, one warp per 32 consecutive tokens: each lane lists its
+// token's covering slots and weights (token_covers), then the half-warps take
+// the tokens in pairs, lane f of a half reading 16 bytes f of every covering
+// slot's row (contiguous 256-byte runs at d = 64) with the slot and the weight
+// broadcast from the owner lane.  Used when no token has more than kMaxCover
+// covering tiles.
+template <typename OutT>
+__global__ void __launch_bounds__(kThreads, 4) merge_fwd_warp_kernel(Geom g, const float* __restrict__ ot,
+                                                                  OutT* __restrict__ out) {
+  __shared__ float win[kWinMax];
+  const WinTable tbl = build_win_table(g, win);
+  const int lane = threadIdx.x & 31;
+  const int64_t total = (int64_t)g.B * g.nh * g.N;
+  const int F4 = g.d / 4;  // 8, 16 or 32
+  const int64_t stride = (int64_t)gridDim.x * (kThreads / 32) * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32; base < total;
+       base += stride) {
+    const int64_t idx = base + lane;
+    int64_t slot[kMaxCover];
+    float w[kMaxCover];
+    int n = 0;
+    float wsum = 0.f;
+    if (idx < total) {
+      n = token_covers(g, tbl, (int)(idx / g.N), idx % g.N, slot, w);
+#pragma unroll
+      for (int c = 0; c < kMaxCover; ++c)
+        if (c < n) wsum += w[c];
+    }
+    for (int q = 0; q < 16; ++q) {
+      const int owner = 2 * q + (lane >> 4);
+      const int nc = __shfl_sync(0xffffffffu, n, owner);
+      const int ncmax = max(nc, __shfl_xor_sync(0xffffffffu, nc, 16));
+      if (ncmax == 0) continue;  // both tokens written by their tile kernel
+      const float inv = 1.f / __shfl_sync(0xffffffffu, wsum, owner);
+      const int f0 = lane & 15;
+      float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+#pragma unroll
+      for (int c = 0; c < kMaxCover; ++c) {
+        if (c >= ncmax) break;
+        const int64_t sc = __shfl_sync(0xffffffffu, slot[c], owner);
+        const float wc = __shfl_sync(0xffffffffu, w[c], owner);
+        if (c < nc) {
+          const float4* row = reinterpret_cast<const float4*>(ot + sc * g.d);
+          if (f0 < F4) {
+            const float4 o = __ldg(row + f0);
+            acc0 = make_float4(fmaf(wc, o.x, acc0.x), fmaf(wc, o.y, acc0.y), fmaf(wc, o.z, acc0.z),
+                               fmaf(wc, o.w, acc0.w));
+          }
+          if (f0 + 16 < F4) {
+            const float4 o = __ldg(row + f0 + 16);
+            acc1 = make_float4(fmaf(wc, o.x, acc1.x), fmaf(wc, o.y, acc1.y), fmaf(wc, o.z, acc1.z),
+                               fmaf(wc, o.w, acc1.w));
+          }
+        }
+      }
+      if (nc > 0) {
+        OutT* dst = out + (base + owner) * g.d;
+        if (f0 < F4) store4<OutT>(dst + 4 * f0, make_float4(acc0.x * inv, acc0.y * inv, acc0.z * inv, acc0.w * inv));
+        if (f0 + 16 < F4)
+          store4<OutT>(dst + 4 * (f0 + 16), make_float4(acc1.x * inv, acc1.y * inv, acc1.z * inv, acc1.w * inv));
+      }
+    }
+  }
+}
+
+// Input gradients of multiply-covered tokens, organised like
+// merge_fwd_warp_kernel: ascending-tile sums of the FP32 per-tile gradients.
+template <typename OutT>
+__global__ void __launch_bounds__(kThreads, 4) merge_bwd_warp_kernel(Geom g, const float* __restrict__ dq_s,
+                                                                  const float* __restrict__ dk_s,
+                                                                  const float* __restrict__ dv_s, OutT* __restrict__ dq,
+                                                                  OutT* __restrict__ dk, OutT* __restrict__ dv) {
+  __shared__ float win[kWinMax];
+  const WinTable tbl = build_win_table(g, win);
+  const int lane = threadIdx.x & 31;
+  const int64_t total = (int64_t)g.B * g.nh * g.N;
+  const int F4 = g.d / 4;
+  const int64_t stride = (int64_t)gridDim.x * (kThreads / 32) * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32; base < total;
+       base += stride) {
+    const int64_t idx = base + lane;
+    int64_t slot[kMaxCover];
+    float w[kMaxCover];
+    const int n = idx < total ? token_covers(g, tbl, (int)(idx / g.N), idx % g.N, slot, w) : 0;
+    for (int q = 0; q < 16; ++q) {
+      const int owner = 2 * q + (lane >> 4);
+      const int nc = __shfl_sync(0xffffffffu, n, owner);
+      const int ncmax = max(nc, __shfl_xor_sync(0xffffffffu, nc, 16));
+      if (ncmax == 0) continue;
+      for (int f = lane & 15; f - (lane & 15) < F4; f += 16) {  // one or two 16-byte columns per lane
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, e = a;
+#pragma unroll
+        for (int c = 0; c < kMaxCover; ++c) {
+          if (c >= ncmax) break;
+          const int64_t off = __shfl_sync(0xffffffffu, slot[c], owner) * g.d;
+          if (c < nc && f < F4) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(dq_s + off) + f);
+            const float4 y = __ldg(reinterpret_cast<const float4*>(dk_s + off) + f);
+            const float4 z = __ldg(reinterpret_cast<const float4*>(dv_s + off) + f);
+            a.x += x.x; a.y += x.y; a.z += x.z; a.w += x.w;
+            b.x += y.x; b.y += y.y; b.z += y.z; b.w += y.w;
+            e.x += z.x; e.y += z.y; e.z += z.z; e.w += z.w;
+          }
+        }
+        if (nc > 0 && f < F4) {
+          const int64_t o = (base + owner) * g.d + 4 * f;
+          store4<OutT>(dq + o, a);
+          store4<OutT>(dk + o, b);
+          store4<OutT>(dv + o, e);
+        }
+      }
+    }
+  }
+}
+
 // x as the sum of three BF16 terms (each the rounding of what the previous ones
 // leave), exact to about 2^-24 |x|.
 __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
@@ -147,6 +263,8 @@ __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* 
                                                             const float* __restrict__ ot,
                                                             float* __restrict__ lse2c, float* __restrict__ dd,
                                                             uint4* __restrict__ ext) {
+  __shared__ float win[kWinMax];
+  const WinTable tbl = build_win_table(g, win);
   const int64_t S = (int64_t)g.B * g.nh * g.ntiles * g.per_tile;
   for (int64_t slot = (int64_t)blockIdx.x * kThreads + threadIdx.x; slot < S; slot += (int64_t)gridDim.x * kThreads) {
     const int64_t ut = slot / g.per_tile;
@@ -198,11 +316,11 @@ __global__ void __launch_bounds__(kThreads) bwd_prep_kernel(Geom g, const OutT* 
       kt[0] = tile / (g.n[1] * g.n[2]);
       kt[1] = (tile / g.n[2]) % g.n[1];
       kt[2] = tile % g.n[2];
-      float wt = tile_weight(g, p, kt), ws = 0.f;
+      float wt = table_weight(g, tbl, p, kt), ws = 0.f;
       int k[3];
       for (k[0] = c.k0[0]; k[0] <= c.k1[0]; ++k[0])
         for (k[1] = c.k0[1]; k[1] <= c.k1[1]; ++k[1])
-          for (k[2] = c.k0[2]; k[2] <= c.k1[2]; ++k[2]) ws += tile_weight(g, p, k);
+          for (k[2] = c.k0[2]; k[2] <= c.k1[2]; ++k[2]) ws += table_weight(g, tbl, p, k);
       lc -= log2f(wt / ws);
     }
     lse2c[slot] = -lc;
@@ -255,7 +373,22 @@ inline unsigned grid_for(int64_t total) {
 
 }  // namespace
 
+// grid of the warp-per-32-tokens kernels
+inline unsigned grid_warp(int64_t tokens) {
+  const int64_t blocks = (tokens + kThreads - 1) / kThreads;
+  const int64_t cap = 152LL * 8;
+  return (unsigned)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
+}
+
 cudaError_t launch_merge_fwd(const Geom& g, const float* ot, void* out, int out_dtype, cudaStream_t st) {
+  if (max_covers(g) <= kMaxCover) {
+    const unsigned grid = grid_warp((int64_t)g.B * g.nh * g.N);
+    if (out_dtype == GATTN_BF16)
+      merge_fwd_warp_kernel<__nv_bfloat16><<<grid, kThreads, 0, st>>>(g, ot, static_cast<__nv_bfloat16*>(out));
+    else
+      merge_fwd_warp_kernel<float><<<grid, kThreads, 0, st>>>(g, ot, static_cast<float*>(out));
+    return cudaGetLastError();
+  }
   const int64_t total = (int64_t)g.B * g.nh * g.N * (g.d / 4);
   if (out_dtype == GATTN_BF16)
     merge_fwd_kernel<__nv_bfloat16><<<grid_for(total), kThreads, 0, st>>>(g, ot, static_cast<__nv_bfloat16*>(out));
@@ -284,8 +417,16 @@ cudaError_t launch_bwd_prep(const Geom& g, const void* out, int out_dtype, const
 
 cudaError_t launch_merge_bwd(const Geom& g, const float* dq_s, const float* dk_s, const float* dv_s, void* dq,
                              void* dk, void* dv, int out_dtype, cudaStream_t st) {
-  const int64_t total = (int64_t)g.B * g.nh * g.N * (g.d / 4);
   using bf = __nv_bfloat16;
+  if (max_covers(g) <= kMaxCover) {
+    const unsigned grid = grid_warp((int64_t)g.B * g.nh * g.N);
+    if (out_dtype == GATTN_BF16)
+      merge_bwd_warp_kernel<bf><<<grid, kThreads, 0, st>>>(g, dq_s, dk_s, dv_s, (bf*)dq, (bf*)dk, (bf*)dv);
+    else
+      merge_bwd_warp_kernel<float><<<grid, kThreads, 0, st>>>(g, dq_s, dk_s, dv_s, (float*)dq, (float*)dk, (float*)dv);
+    return cudaGetLastError();
+  }
+  const int64_t total = (int64_t)g.B * g.nh * g.N * (g.d / 4);
   if (out_dtype == GATTN_BF16)
     merge_bwd_kernel<bf><<<grid_for(total), kThreads, 0, st>>>(g, dq_s, dk_s, dv_s, (bf*)dq, (bf*)dk, (bf*)dv);
   else

@@ -178,6 +178,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gattn_serve_destroy": ([P], None),
         "gattn_linear_workspace_bytes": ([ctypes.POINTER(gattn_linear_desc)], S),
         "gattn_linear_fwd": ([ctypes.POINTER(gattn_linear_desc), P, P, P, P, P, S, P], ctypes.c_int),
+        "gattn_linear_bwd_workspace_bytes": ([ctypes.POINTER(gattn_linear_desc)], S),
+        "gattn_linear_bwd": ([ctypes.POINTER(gattn_linear_desc), P, P, P, P, P, S, P, P, P, P, S, P], ctypes.c_int),
         "gattn_dps_workspace_bytes": ([D], S),
         "gattn_dps_step": ([D, ctypes.POINTER(gattn_dps_params), P, P, P, P, P, P, S, P], ctypes.c_int),
         "gattn_gated_workspace_bytes": ([D], S),
@@ -301,6 +303,17 @@ def gattn_linear_fwd(desc, q, k, v, out, ws, ws_bytes=None, stream=None) -> int:
     )
 
 
+def gattn_linear_bwd_workspace_bytes(desc) -> int:
+    return load_library().gattn_linear_bwd_workspace_bytes(ctypes.byref(desc))
+
+
+def gattn_linear_bwd(desc, q, k, v, dout, saved, dq, dk, dv, ws, saved_bytes=None, ws_bytes=None, stream=None) -> int:
+    return load_library().gattn_linear_bwd(
+        ctypes.byref(desc), _ptr(q), _ptr(k), _ptr(v), _ptr(dout), _ptr(saved), _nbytes(saved, saved_bytes),
+        _ptr(dq), _ptr(dk), _ptr(dv), _ptr(ws), _nbytes(ws, ws_bytes), _stream(stream),
+    )
+
+
 def linear_desc(q):
     B, nh, N, d = q.shape
     desc = gattn_linear_desc()
@@ -309,8 +322,10 @@ def linear_desc(q):
     return desc
 
 
-def linear_forward(q, k, v, stream=None):
-    """Factorised linear attention (phi = elu + 1) of BF16 [B, heads, N, 64] tensors."""
+def linear_forward(q, k, v, stream=None, keep_summary=False):
+    """Factorised linear attention (phi = elu + 1) of BF16 [B, heads, N, 64]
+    tensors; with keep_summary, also the workspace that holds the summary the
+    backward reads."""
     _require_cuda(q, k, v)
     if not (q.shape == k.shape == v.shape) or q.dtype != torch.bfloat16:
         raise ValueError("q, k, v must be BF16 tensors of one shape [B, heads, N, 64]")
@@ -318,7 +333,41 @@ def linear_forward(q, k, v, stream=None):
     out = torch.empty_like(q)
     ws = torch.empty(gattn_linear_workspace_bytes(desc), dtype=torch.uint8, device=q.device)
     check(gattn_linear_fwd(desc, q, k, v, out, ws, stream=stream), "gattn_linear_fwd")
-    return out
+    return (out, ws) if keep_summary else out
+
+
+def linear_backward(q, k, v, dout, saved, stream=None):
+    """(dq, dk, dv) of sum(out * dout) for the factorised linear attention;
+    `saved` is the workspace linear_forward(..., keep_summary=True) returned."""
+    _require_cuda(q, k, v, dout, saved)
+    if dout.shape != q.shape or dout.dtype != torch.bfloat16:
+        raise ValueError("dout must be BF16 of the shape of q")
+    desc = linear_desc(q)
+    dq, dk, dv = torch.empty_like(q), torch.empty_like(q), torch.empty_like(q)
+    ws = torch.empty(gattn_linear_bwd_workspace_bytes(desc), dtype=torch.uint8, device=q.device)
+    check(gattn_linear_bwd(desc, q, k, v, dout, saved, dq, dk, dv, ws, stream=stream), "gattn_linear_bwd")
+    return dq, dk, dv
+
+
+class LinearAttention(torch.autograd.Function):
+    """Factorised linear attention as an autograd op: forward and hand-written
+    backward in CUDA (the summary is kept from the forward, feature maps are
+    recomputed)."""
+
+    @staticmethod
+    def forward(ctx, q, k, v):
+        out, saved = linear_forward(q, k, v, keep_summary=True)
+        ctx.save_for_backward(q, k, v, saved)
+        return out
+
+    @staticmethod
+    def backward(ctx, dout):
+        q, k, v, saved = ctx.saved_tensors
+        return linear_backward(q, k, v, dout.contiguous().to(torch.bfloat16), saved)
+
+
+def linear_attention(q, k, v):
+    return LinearAttention.apply(q, k, v)
 
 
 def gattn_dps_workspace_bytes(desc) -> int:
@@ -360,11 +409,11 @@ def gattn_profile_enable(enable: bool) -> int:
 
 def gattn_profile_read() -> dict:
     """{kernel name: (launches, total device ms)} since the last enable."""
-    arr = (gattn_kernel_stat * 16)()
-    n = load_library().gattn_profile_read(arr, 16)
+    arr = (gattn_kernel_stat * 32)()
+    n = load_library().gattn_profile_read(arr, 32)
     if n < 0:
         raise GattnError(-n, "gattn_profile_read")
-    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n, 16))}
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n, 32))}
 
 
 # ---------------------------------------------------------------- serving ABI, one to one
