@@ -83,3 +83,25 @@ def forward(T, Y, X, core, halo, q, k, v, scale=None, window="hann") -> np.ndarr
             A = effective_matrix(T, Y, X, core, halo, q[b, h], k[b, h], scale, window)
             out[b, h] = A @ v[b, h]
     return out
+
+
+def tile_lse(T, Y, X, core, halo, q2, k2, scale, tile, rows) -> np.ndarray:
+    """log sum_{j in E_t} exp(scale q_i . k_j) for query rows i of one extended
+    tile (the softmax normaliser of Sec. III-C's per-tile attention), FP64.
+    tile: per-dimension tile indices (k_t, k_y, k_x); rows: global token
+    indices inside that extended tile; q2, k2: [N, d] of one (batch, head)."""
+    grid = np.arange(T * Y * X).reshape(T, Y, X)
+    dims = [(T, core[0], halo[0]), (Y, core[1], halo[1]), (X, core[2], halo[2])]
+    sl = []
+    for a, (G, c, h) in enumerate(dims):
+        _, lo, hi = _dim_tiles(G, c, h)[tile[a]]
+        sl.append(slice(lo, hi))
+    idx = grid[tuple(sl)].reshape(-1)
+    assert set(int(i) for i in rows) <= set(int(i) for i in idx)
+    kk = np.asarray(k2, dtype=np.float64)[idx]
+    out = np.empty(len(rows))
+    for r, i in enumerate(rows):
+        s = scale * (kk @ np.asarray(q2[i], dtype=np.float64))
+        m = s.max()
+        out[r] = m + np.log(np.exp(s - m).sum())
+    return out

@@ -163,8 +163,9 @@ constexpr int kIssuerPV = 2 + kMathWarps;  // warp index of the P V issuer
 // are rescaled once); O itself accumulates in TMEM across the key blocks.
 constexpr float kRescaleLog2 = 8.f;
 struct RowState {
-  float m;  // reference max (log2 domain, scaled), same in both threads of the row
-  float l;  // this thread's half of the row sum, relative to m
+  float m;   // reference max (log2 domain, scaled), same in both threads of the row
+  float l;   // this thread's half of the row sum, relative to m
+  float lc;  // Kahan compensation of l (the sum runs over every key block of the tile)
 };
 
 template <int N>
@@ -298,6 +299,7 @@ __device__ __forceinline__ bool softmax_block(RowState& rs, uint32_t tS, uint32_
       const float f = grow ? ex2(rs.m - mblk) : 1.f;
       rescale_o<D>(tO, f);
       rs.l *= f;
+      rs.lc *= f;
       if (grow) rs.m = mblk;
     }
   }
@@ -317,7 +319,12 @@ __device__ __forceinline__ bool softmax_block(RowState& rs, uint32_t tS, uint32_
     f2unpack(acc[i], x, y);
     lsum += x + y;
   }
-  rs.l += lsum;
+  {  // compensated: tiles of the long temporal context span thousands of key blocks
+    const float y = lsum - rs.lc;
+    const float t = rs.l + y;
+    rs.lc = (t - rs.l) - y;
+    rs.l = t;
+  }
   tmem_wait_st();
   return true;
 }
@@ -562,6 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       RowState rs;
       rs.m = -INFINITY;
       rs.l = 0.f;
+      rs.lc = 0.f;
       // key-block coordinates stepped incrementally (no divisions in the loop)
       int jt = 0, jy = 0, jx = 0;
       for (int j = 0; j < tbk.NB; ++j, ++G) {

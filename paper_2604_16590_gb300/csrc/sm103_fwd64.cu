@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       block_origin(g, tbk, qb, qo);
       block_row(g, qo, row, ql);
       const bool qvalid = inside(tbk, ql);
-      float m = -INFINITY, l = 0.f;
+      float m = -INFINITY, l = 0.f, lc = 0.f;  // lc: Kahan compensation of the row sum l
       for (int j = 0; j < tbk.NB; ++j, ++GX) {
         if (!(ok = WAIT(s_full(x), GX & 1))) break;
         tc_fence_after();
@@ -571,8 +571,14 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         if (any_grow) {
           rescale_o(tO, f);
           l *= f;
+          lc *= f;
         }
-        l += lsum;
+        {  // compensated sum over the tile's key blocks
+          const float y = lsum - lc;
+          const float t = l + y;
+          lc = (t - l) - y;
+          l = t;
+        }
         tmem_st16(tP, pk0);
         tmem_st16(tP + 16, pk1);
         tmem_st16(tP + 32, pk2);

@@ -4,7 +4,7 @@ BF16 inputs and outputs, the same seeded inputs as bench.py.
 
 The oracle cannot evaluate the whole operator at this size, so the test checks
 (a) sampled rows of Out and dQ, which the oracle computes row by row, (b) dK
-and dV of sampled keys of one tile, and (c) two exact identities of the
+and dV of sampled keys of one tile and of keys two tiles share, and (c) two exact identities of the
 operator at every size: per (batch, head) the dV rows sum to the dOut rows
 (each softmax row and each set of merge weights sums to one) and the dK rows
 sum to zero (each row of dS sums to zero)."""
@@ -72,10 +72,15 @@ def test_sampled_keys_of_dk_dv(run):
     T, Y, X = w.grid
     geo1 = oracle.Geometry(1, 1, w.d, T, Y, X, w.core, w.halo)
     b, h = 2, 5
-    # keys inside the core of tile (0, 1, 1) away from its halos: one tile's backward
+    # keys inside the core of tile (0, 1, 1) away from its halos (one tile's
+    # backward), and keys in the overlap of tiles (0, 1, 1) and (0, 1, 2)
+    # (x in [56, 72) is in both extended tiles, y in [20, 28) in one tile row):
+    # their dK, dV are the fixed-order sums of two tiles' gradients (merge path)
     rng = np.random.default_rng(6)
     keys = [((int(t) * Y + int(y)) * X + int(x)) for t, y, x in zip(rng.integers(0, T, 12), rng.integers(20, 28, 12),
                                                                    rng.integers(40, 56, 12))]
+    keys += [((int(t) * Y + int(y)) * X + int(x)) for t, y, x in zip(rng.integers(0, T, 8), rng.integers(20, 28, 8),
+                                                                    rng.integers(56, 72, 8))]
     qs, ks, vs, gs = (_slice64(t, b, h) for t in (q, k, v, go))
     dk_r, dv_r = oracle.key_rows(geo1, qs, ks, vs, gs, [(0, 0, j) for j in keys])
     for name, got, ref in (("dk", dk[b, h, keys], dk_r), ("dv", dv[b, h, keys], dv_r)):

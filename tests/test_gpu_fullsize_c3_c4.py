@@ -32,6 +32,60 @@ def _errs(got, ref):
     return np.abs(got - ref).max() / np.abs(ref).max(), np.linalg.norm(got - ref) / np.linalg.norm(ref)
 
 
+def _slot(w, box, bh, tile, p):
+    """Slot of token position p in extended tile `tile` (per-dimension indices):
+    box j of the tile at offset (p - lo) // box, row rho inside the box, boxes of
+    a tile contiguous (128 slots each) and tiles laid out per batch*head."""
+    n = [-(-w.grid[a] // w.core[a]) for a in range(3)]
+    lo, e, emax = [], [], []
+    for a in range(3):
+        ext = [min((kk + 1) * w.core[a] + w.halo[a], w.grid[a]) - max(kk * w.core[a] - w.halo[a], 0)
+               for kk in range(n[a])]
+        lo.append(max(tile[a] * w.core[a] - w.halo[a], 0))
+        e.append(ext[tile[a]])
+        emax.append(max(ext))
+    l = [p[a] - lo[a] for a in range(3)]
+    nb = [-(-e[a] // box[a]) for a in range(3)]
+    per_tile = 128
+    for a in range(3):
+        per_tile *= -(-emax[a] // box[a])
+    j = ((l[0] // box[0]) * nb[1] + l[1] // box[1]) * nb[2] + l[2] // box[2]
+    rho = ((l[0] % box[0]) * box[1] + l[1] % box[1]) * box[2] + l[2] % box[2]
+    t = (tile[0] * n[1] + tile[1]) * n[2] + tile[2]
+    return ((bh * n[0] * n[1] * n[2] + t) * per_tile + j * 128 + rho)
+
+
+def _check_row_normalisers(w, q, k, saved, desc):
+    """The per-tile row normalisers the forward saves (log2 of the compensated
+    FP32 row sum plus the reference max) against the oracle's per-tile
+    log-sum-exp at sampled rows of tiles that span 2304 key boxes (144 frames
+    of 32 x 64 tokens; Tab. III(a)'s long temporal context): the Kahan-
+    compensated sum keeps the normaliser's relative error near FP32 rounding."""
+    from oracle import brute
+
+    st, box = gattn.gattn_block_shape(desc)
+    assert st == 0
+    lse2 = saved[: saved.numel() // 4 * 4].view(torch.float32)
+    T, Y, X = w.grid
+    b, h = 0, w.nh - 1
+    q2 = q[b, h].double().cpu().numpy()
+    k2 = k[b, h].double().cpu().numpy()
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for kt in (0, 7, 15):
+        t_lo = max(kt * w.core[0] - w.halo[0], 0)
+        t_hi = min((kt + 1) * w.core[0] + w.halo[0], T)
+        ts = rng.integers(t_lo, t_hi, 6)
+        ps = [(int(t_), int(rng.integers(0, Y)), int(rng.integers(0, X))) for t_ in ts]
+        rows = [(t_ * Y + y_) * X + x_ for t_, y_, x_ in ps]
+        ref = brute.tile_lse(T, Y, X, w.core, w.halo, q2, k2, 1.0 / np.sqrt(w.d), (kt, 0, 0), rows)
+        slots = [_slot(w, box, b * w.nh + h, (kt, 0, 0), p) for p in ps]
+        got = lse2[torch.as_tensor(slots, device=lse2.device)].double().cpu().numpy() * np.log(2.0)
+        worst = max(worst, float(np.abs(got - ref).max()))
+    print(f"c3 row normaliser: max |lse - lse_ref| = {worst:.3e} (nats)")
+    assert worst <= 2e-5, worst
+
+
 @pytest.mark.parametrize("name", ["c4_1m_p", "c3_4m_p"])
 def test_full_size_sampled_rows_and_identities(name):
     build.build()
@@ -42,6 +96,8 @@ def test_full_size_sampled_rows_and_identities(name):
     out, saved = gattn.forward(q, k, v, tiling, out_dtype=torch.bfloat16)
     dq, dk, dv = gattn.backward(q, k, v, out, go, saved, tiling)
     assert gattn.gattn_stream_status() == 0
+    if name == "c3_4m_p":
+        _check_row_normalisers(w, q, k, saved, gattn.desc_for(q, tiling, torch.bfloat16))
     del saved
 
     # identities of the operator at every size (dk, dv)

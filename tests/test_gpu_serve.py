@@ -106,3 +106,36 @@ def test_request_loop_reports_latency_percentiles():
     assert st.completed == 6 and st.iterations >= 4
     assert st.p50_latency_s <= st.p99_latency_s
     assert st.token_steps == sum(8 * s.T * Y * X * 4 for s in specs)
+
+
+def test_five_steps_replay_through_the_oracle():
+    """The serving step loop over several denoising steps (the per-step
+    Hann-weighted merge is what carries context from tile to tile, Sec. III-C):
+    servers running 1..5 steps on the same request give every intermediate
+    BF16 state; each step is replayed by the FP64 oracle from the previous GPU
+    state (BF16 bar), and the 5-step state is compared with the oracle's own
+    5-step trajectory on BF16-rounded states, within 5 times the per-step bar
+    (per-step errors add at most linearly: the update is a convex blend)."""
+    spec = ServeRequestSpec(0.0, 1, 2, 91)
+    z0 = request_state(spec, Y, X, D)
+    states = [z0]
+    for k in range(1, 6):
+        with gattn.Server(_cfg(steps=k)) as srv:
+            rid = srv.submit(z0)
+            while not srv.done(rid):
+                srv.step()
+            zk, _ = srv.result(rid, z0.shape)
+        states.append(zk)
+    geo = oracle.Geometry(1, spec.nh, D, spec.T, Y, X, CORE, HALO)
+
+    def step(z):
+        att = oracle.forward(geo, z[None], z[None], z[None])[0]
+        return z + 0.5 * (att - z)
+
+    for k in range(1, 6):
+        prev = states[k - 1].double().numpy()
+        assert_close(f"serve/step{k}", states[k].double().numpy()[None], step(prev)[None], 2e-2, 3e-3)
+    z = z0.double().numpy()
+    for _ in range(5):
+        z = torch.from_numpy(step(z)).to(torch.bfloat16).double().numpy()
+    assert_close("serve/trajectory5", states[5].double().numpy()[None], z[None], 5 * 2e-2, 5 * 3e-3)

@@ -11,6 +11,7 @@ import torch
 
 import oracle
 from oracle import dps
+from paper_2604_16590_gb300 import gattn
 
 
 def _setup(geo, seed, frac=0.3):
@@ -106,3 +107,41 @@ def test_bf16_attention_reading_rounds_the_state():
     # same attention input; the prior score subtracts the FP64 state
     delta = 1.0 - 0.36
     assert np.abs(a - b - (z - zb) * (1 - delta)).max() < 5e-3
+
+
+def test_sigma_schedule_roots_are_equally_spaced():
+    """The schedule of Karras et al. (2022) interpolates sigma^(1/rho) linearly
+    between the end points: the rho-th roots of the levels are an arithmetic
+    sequence (a wrong exponent or spacing breaks it), for the oracle and for
+    the library's host-side schedule alike."""
+    for n, smax, smin, rho in ((20, 2.0, 0.05, 7.0), (7, 80.0, 0.002, 7.0), (12, 1.0, 0.1, 3.0)):
+        for s in (dps.sigma_schedule(n, smax, smin, rho), np.array(gattn.sigma_schedule(n, smax, smin, rho))):
+            r = s[:-1] ** (1.0 / rho)
+            np.testing.assert_allclose(np.diff(r), (smin ** (1 / rho) - smax ** (1 / rho)) / (n - 1), rtol=1e-9)
+            np.testing.assert_allclose([s[0], s[-2], s[-1]], [smax, smin, 0.0], rtol=1e-12)
+
+
+def test_step_to_zero_noise_lands_on_the_denoiser_output():
+    """Without noise and guidance, the Euler step from sigma to 0 moves the
+    state by sigma^2 times the prior score (D(z) - z) / sigma^2: it lands on
+    the denoiser's output D(z) itself (Tweedie's estimate), whatever sigma."""
+    geo = oracle.Geometry(1, 2, 8, 1, 6, 8, core=(1, 3, 4), halo=(0, 1, 1))
+    z, y, eps, mask = _setup(geo, 8)
+    for sigma in (0.3, 1.0, 2.5):
+        got, D = dps.step(geo, z, y, mask, np.zeros_like(eps), sigma, 0.0, 0.0)
+        np.testing.assert_allclose(got, D, rtol=0, atol=1e-12)
+
+
+def test_noise_of_a_step_has_the_variance_sigma_drop():
+    """A state whose tokens are all equal is a fixed point of the denoiser
+    (constant values are returned), so the prior score vanishes and, without
+    guidance, the step adds exactly sqrt(sigma^2 - sigma_next^2) eps: the
+    variance the noise level drops by (a noise term scaled by delta instead of
+    its square root fails)."""
+    geo = oracle.Geometry(1, 1, 4, 1, 4, 6, core=(1, 2, 3), halo=(0, 1, 1))
+    _, y, eps, mask = _setup(geo, 9)
+    z = np.broadcast_to(np.array([0.3, -1.2, 0.7, 2.0]), (1, 1, 24, 4)).copy()
+    sigma, sigma_next = 1.5, 0.4
+    got, D = dps.step(geo, z, y, mask, eps, sigma, sigma_next, 0.0)
+    np.testing.assert_allclose(D, z, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(got - z, np.sqrt(sigma**2 - sigma_next**2) * eps, rtol=0, atol=1e-12)

@@ -291,3 +291,28 @@ def test_sampled_rows_agree_with_full_oracle():
         np.testing.assert_allclose(dq_r[n], dq[b, h, i], atol=1e-13)
         np.testing.assert_allclose(dk_r[n], dk[b, h, i], atol=1e-13)
         np.testing.assert_allclose(dv_r[n], dv[b, h, i], atol=1e-13)
+
+
+def test_tile_lse_is_the_tile_softmax_normaliser():
+    """brute.tile_lse against torch's logsumexp (library): over the whole grid
+    when one tile covers it, and over a tile's token set built by hand when the
+    grid is cut into 2 x 2 cores without halo."""
+    import torch
+
+    from oracle import brute
+
+    rng = np.random.default_rng(5)
+    T, Y, X, d = 2, 8, 12, 16
+    q2 = rng.standard_normal((T * Y * X, d))
+    k2 = rng.standard_normal((T * Y * X, d))
+    s = 0.3
+    rows = [0, 17, 100, T * Y * X - 1]
+    got = brute.tile_lse(T, Y, X, (T, Y, X), (0, 0, 0), q2, k2, s, (0, 0, 0), rows)
+    ref = torch.logsumexp(s * torch.from_numpy(q2[rows]) @ torch.from_numpy(k2).T, dim=1).numpy()
+    assert np.allclose(got, ref, rtol=0, atol=1e-12)
+    # tile (1, 0, 1) of cores (1, 4, 6): frame 1, rows 0..3, columns 6..11
+    idx = np.array([(1 * Y + y) * X + x for y in range(4) for x in range(6, 12)])
+    rows = [int(idx[0]), int(idx[7]), int(idx[-1])]
+    got = brute.tile_lse(T, Y, X, (1, 4, 6), (0, 0, 0), q2, k2, s, (1, 0, 1), rows)
+    ref = torch.logsumexp(s * torch.from_numpy(q2[rows]) @ torch.from_numpy(k2[idx]).T, dim=1).numpy()
+    assert np.allclose(got, ref, rtol=0, atol=1e-12)
