@@ -34,7 +34,11 @@ UNIT = "Gtokens/s"
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a leg's dominant
 # kernel, from the ncu captures summarised in profiles/; None for a kernel
 # that changed since its counters were taken.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    # dkdv64: 1539.3 MB in one ncu capture of the same geometry with 1/16 of the
+    # (batch*head) units (c2_262k_p1), times 16 (the units are independent)
+    ("c2_262k_p", "bwd_dkdv"): 24.63e9,
+}
 # MUFU ex2 results per clock per SM (measured on GB300 with a micro-benchmark:
 # 32 per clock, i.e. 8 per SM sub-partition), the exponential-unit peak of the
 # attainable-time bound.
