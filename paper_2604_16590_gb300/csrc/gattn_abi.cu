@@ -307,8 +307,8 @@ gattn_status gattn_bwd(const gattn_desc* desc, const void* q, const void* k, con
   char* w = static_cast<char*>(ws);
   float* lse2c = reinterpret_cast<float*>(w + bl.lse_off);
   float* dd = reinterpret_cast<float*>(w + bl.dd_off);
-  // the statistics rows are read only by the d = 64 tensor-core dK/dV kernel
-  void* ext = desc->in_dtype == GATTN_BF16 && g.d == 64 ? static_cast<void*>(w + bl.ext_off) : nullptr;
+  // the statistics rows are read only by the tensor-core dK/dV kernels
+  void* ext = desc->in_dtype == GATTN_BF16 ? static_cast<void*>(w + bl.ext_off) : nullptr;
   float* dq_s = reinterpret_cast<float*>(w + bl.dq_off);
   float* dk_s = reinterpret_cast<float*>(w + bl.dk_off);
   float* dv_s = reinterpret_cast<float*>(w + bl.dv_off);

@@ -35,8 +35,8 @@ inline SavedLayout saved_layout(const Geom& g) {
 //   dd    : float[S]      -D, D = dOut . O_t per slot, negated
 //   dq_s, dk_s, dv_s : float[S * d]  per-tile gradients of multiply-covered rows
 //   ext   : 16 B[S]       BF16 row (x0, x1, x2, y0, y1, y2, 0, 0) per slot: x0 + x1 + x2 = -lse' / (scale
-//                          log2 e) and y0 + y1 + y2 = -D, each split into three BF16 terms; the d = 64
-//                          dK/dV kernel adds both to S^T and dP^T with one extra K = 16 MMA step each
+//                          log2 e) and y0 + y1 + y2 = -D, each split into three BF16 terms; the BF16
+//                          dK/dV kernels add both to S^T and dP^T with one extra K = 16 MMA step each
 struct BwdLayout {
   size_t S, lse_off, dd_off, ext_off, dq_off, dk_off, dv_off, bytes;
 };

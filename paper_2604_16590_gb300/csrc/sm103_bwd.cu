@@ -1,31 +1,50 @@
-// sm103_bwd.cu -- BF16 tensor-core backward of STORM-GPA tile attention on
-// GB300 (sm_103a), general head size (d = 128; d = 64 runs the TMEM-operand
-// kernels of sm103_bwd64.cu).  Two deterministic kernels (no atomics):
+// sm103_bwd.cu -- BF16 tensor-core backward of STORM-GPA tile attention for
+// head size d = 128 on GB300 (sm_103a); d = 64 runs sm103_bwd64.cu.  Two
+// deterministic kernels (no atomics), every product over whole 128-token
+// boxes (M = N = 128):
 //
-//   dKdV kernel, one work item per (batch*head, tile, 128-key block kb):
-//     for every 64-query half-block i of the tile:
-//       S^T  = K_kb Q_i^T            tcgen05 -> TMEM (double-buffered)
-//       dP^T = V_kb dOut_i^T         tcgen05 -> TMEM (double-buffered)
-//       P'^T = exp2(s S^T log2e - lse'_i)        (softmax warps, BF16 -> smem)
-//       dS^T = P'^T (dP^T - D_i)                 (softmax warps, BF16 -> smem)
-//       dV  += P'^T dOut_i,  dK += dS^T Q_i      tcgen05, FP32 accumulators in TMEM
-//   dQ kernel, one work item per (batch*head, tile, 128-query block qb):
-//     for every 64-key half-block j:  S = Q K_j^T, dP = dOut V_j^T,
-//       dS = P' (dP - D) (keys outside the tile masked), dQ += dS K_j.
+//   dK/dV kernel, one work item per (batch*head, tile, 128-key box kb):
+//     for every 128-query box i of the tile:
+//       S'^T  = K Q_i^T  + 1 x_i^T,  x = -lse' / (scale log2 e)      8 + 1 K-steps
+//       dP'^T = V dO_i^T + 1 y_i^T,  y = -D                          8 + 1 K-steps
+//       P'^T = exp2(scale log2e S'^T),  dS^T = P'^T * dP'^T          math warps, BF16 pairs -> TMEM
+//       dV += P'^T dO_i,  dK += dS^T Q_i                             A from TMEM, FP32 in TMEM
+//   dQ kernel, one work item per (batch*head, tile, 128-query box qb):
+//     for every 128-key box j of the tile:
+//       S = Q K_j^T (+ 1 b_j^T, b = -1e30 on keys outside the tile),  dP = dO V_j^T
+//       dS = P' (dP - D),  dQ += dS K_j                              A from TMEM, FP32 in TMEM
+//
+// TMEM at d = 128: the two accumulators of the dK/dV kernel take 256 of the
+// 512 columns and its two score matrices the other 256, so the packed P'^T
+// and dS^T are written over the FP32 scores they come from (each math warp
+// packs the 32 columns it read into the first 16 of them).  The next box's
+// S'^T therefore waits for this box's dV product, the reader of P'^T, and its
+// dP'^T for the dK product; with one issuing thread per product pair those
+// waits overlap the other pair's MMAs.  The dQ kernel has one accumulator, so
+// its packed dS has two buffers of its own: S 0, dP 128, dQ 256, dS 384 / 448.
+//
+// Shared memory (one operand box = 32 KB, two 64-element halves of 128-byte
+// rows): the dK/dV kernel holds the item's K and V and a two-stage ring of
+// (Q, dO, statistics rows); the dQ kernel the item's Q and dO and a two-stage
+// ring of (K, V, key-bias row).  A work item streams every box of its tile,
+// so one K, V (resp. Q, dO) buffer per item costs one load wait per item.
 //
 // The merge weight of the Hann-weighted overlap average (arXiv 2604.16590,
-// Sec. III-C) enters through the per-row statistics the prep pass writes
-// (negated, -lse' and -D, so each element costs one packed FMA for the exp2
-// argument and one packed add + multiply for dS): lse' = lse - log2(w_t/sum w)
-// makes P' = (w_t / sum w) P, the probabilities of the per-tile gradient
-// dO_t = (w_t / sum w) dOut, and D = dOut . O_t.  P is recomputed from lse' (never stored).  Rows covered by
-// one tile are written straight to dQ/dK/dV; multiply-covered rows go to FP32
-// per-tile slots that the merge kernel sums in fixed tile order.
+// Sec. III-C) enters through lse' = lse - log2(w_t / sum w), which makes P'
+// the probabilities of the per-tile gradient dO_t = (w_t / sum w) dOut, and
+// D = dOut . O_t.  The statistics of a query slot enter the dK/dV scores as
+// one extra K = 16 MMA step against a constant A operand of ones (the prep
+// pass writes each slot's -lse' / (scale log2 e) and -D as sums of three BF16
+// terms).  Rows covered by one tile are written straight to dQ/dK/dV;
+// multiply-covered rows go to FP32 per-tile slots that the merge kernel sums
+// in fixed tile order.
 //
-// Warp roles: warp 0 TMA producer, warp 1 TMEM allocator + single-thread MMA
-// issuer, warps 2..9 elementwise math + epilogue: one TMEM lane = one block row,
-// two warps per lane quadrant, each taking half of the row's columns (eight
-// math warps keep two warps per SM sub-partition to hide TMEM and MUFU latency).
+// Warp roles: warp 0 TMA producer, warp 1 TMEM allocator + issuer of the
+// score products, warp 2 issuer of the gradient products, warps 3..18
+// elementwise math + epilogue: one TMEM lane = one box row, four warps per
+// lane quadrant, each taking 32 of the row's 128 score columns.  Two issuing
+// threads, because a thread's mbarrier wait is held until the tcgen05.mma it
+// issued before it have drained from the tensor pipe.
 #include "sm103_bwd_common.cuh"
 
 GATTN_DEFINE_STATUS(sm103_bwd)
@@ -37,33 +56,39 @@ using namespace sm103;
 __device__ void set_status_bwd(uint32_t c) { set_status(c); }
 #define WAIT(bar, par) mbar_wait<set_status_bwd>((bar), (par), abort_flag)
 
+constexpr int kD = 128;
+constexpr int kBox = 128 * kD * 2;  // one 128-token box of one operand, BF16, 32 KB
+
+// TMEM column of K-step ks (16 BF16 values = 8 packed columns) of an operand
+// that warp c4 packed into the first 16 of its 32 columns [32 c4, 32 c4 + 32)
+__device__ __forceinline__ uint32_t inplace_col(int ks) { return 32 * (ks >> 1) + 8 * (ks & 1); }
+
 // =============================================================== dK / dV
-template <int D>
-struct KvCfg {
-  static constexpr int kHalves = D / 64;
-  static constexpr int kBlock = 128 * D * 2;
-  static constexpr int kStages = D == 64 ? 2 : 1;  // (Q, dOut, lse', D) ring
+struct Kv128 {
+  static constexpr int kStages = 2;  // (Q, dOut, statistics rows) ring
   static constexpr int kK = 0;
-  static constexpr int kV = kBlock;
-  static constexpr int kQ = 2 * kBlock;             // stage s: Q at kQ + s*2*kBlock, dOut after it
-  static constexpr int kStat = kQ + kStages * 2 * kBlock;  // stage s: 128 lse' + 128 D floats
-  static constexpr int kP = kStat + kStages * 1024;        // 2 buffers x (P'^T 16 KB + dS^T 16 KB)
-  static constexpr int kBar = kP + 2 * 32768;
-  // kv_full, kv_empty, qd_full[S], qd_empty[S], st_full[2], st_empty[2], p_full[2], p_empty[2],
-  // acc_full, acc_empty, drain
-  static constexpr int kNumBars = 2 + 2 * kStages + 8 + 3;
+  static constexpr int kV = kBox;
+  static constexpr int kQ = 2 * kBox;  // stage s: Q at kQ + s*2*kBox, dOut after it
+  // A: ones in K 0..2 at kOnes, ones in K 3..5 at kOnes + 4096; B, stage s at
+  // kExt + s*4096: the box's 128 statistics rows, each block followed by 2 KB of zeros
+  static constexpr int kOnes = kQ + kStages * 2 * kBox;
+  static constexpr int kExt = kOnes + 2 * 4096;
+  static constexpr int kBar = kExt + kStages * 4096;
+  // kv_full, kv_empty, qd_full[S], qd_empty[S], s_full[2], p_full[2], p_empty[2],
+  // acc_full, acc_empty, drain[2]   ([0]: the S'^T / P'^T / dV chain, [1]: dP'^T / dS^T / dK)
+  static constexpr int kNumBars = 2 + 2 * kStages + 6 + 4;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kSmem = kMisc + 16 + 1024;
-  // TMEM columns: S^T[2] 0/64, dP^T[2] 128/192, dV 256, dK 256 + D
-  static constexpr uint32_t kColST = 0, kColDP = 128, kColDV = 256, kColDK = 256 + D;
+  // TMEM: S'^T (then P'^T packed) 0, dP'^T (then dS^T packed) 128, dV 256, dK 384
+  static constexpr uint32_t kColST = 0, kColDP = 128, kColDV = 256, kColDK = 384;
 };
 
-template <int D, typename OutT>
-__global__ void __launch_bounds__(kThreads, 1)
-    sm103_dkdv_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
-                      const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tdo,
-                      const BwdArgs a) {
-  using C = KvCfg<D>;
+template <typename OutT>
+__global__ void __launch_bounds__(kThreadsB, 1)
+    dkdv128_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
+                   const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tdo,
+                   const BwdArgs a) {
+  using C = Kv128;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kBar);
@@ -71,18 +96,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* kv_empty = bars + 1;
   uint64_t* qd_full = bars + 2;
   uint64_t* qd_empty = qd_full + C::kStages;
-  uint64_t* st_full = qd_empty + C::kStages;
-  uint64_t* st_empty = st_full + 2;
-  uint64_t* p_full = st_empty + 2;
-  uint64_t* p_empty = p_full + 2;
+  uint64_t* s_full = qd_empty + C::kStages;  // [2]: S'^T, dP'^T computed
+  uint64_t* p_full = s_full + 2;             // [2]: P'^T, dS^T packed in place
+  uint64_t* p_empty = p_full + 2;            // [2]: dV, dK products of the box done
   uint64_t* acc_full = p_empty + 2;
   uint64_t* acc_empty = acc_full + 1;
-  uint64_t* drain = acc_empty + 1;
+  uint64_t* drain = acc_empty + 1;  // [2]: one per issuing thread
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  zero_pad_rows(smem, (2 + 2 * C::kStages) * C::kHalves, a.g.R);  // K, V and the Q / dOut ring
+  init_ext_operands(smem + C::kOnes, 2, true, smem + C::kExt, C::kStages);
+  zero_pad_rows(smem, (2 + 2 * C::kStages) * 2, a.g.R);  // K, V and the Q / dOut ring (16 KB halves)
+  fence_proxy_async_smem();
   if (threadIdx.x == 0) {
     mbar_init(kv_full, 1);
     mbar_init(kv_empty, 1);
@@ -90,15 +116,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(qd_full + s, 1);
       mbar_init(qd_empty + s, 1);
     }
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(st_full + s, 1);
-      mbar_init(st_empty + s, kMathWarps);
-      mbar_init(p_full + s, kMathWarps);
-      mbar_init(p_empty + s, 1);
+    for (int c = 0; c < 2; ++c) {
+      mbar_init(s_full + c, 1);
+      mbar_init(p_full + c, kMathW);
+      mbar_init(p_empty + c, 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kMathWarps);
+    mbar_init(acc_empty, kMathW);
     mbar_init(drain, 1);
+    mbar_init(drain + 1, 1);
     *abort_flag = 0;
     fence_mbar_init();
     prefetch_tmap(&tq);
@@ -131,32 +157,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         int o[3];
         block_origin(g, tbk, kb, o);
         if (!(ok = WAIT(kv_empty, (W & 1) ^ 1))) break;
-        mbar_arrive_expect_tx(kv_full, 2 * C::kHalves * g.R * 128);
+        mbar_arrive_expect_tx(kv_full, 4 * g.R * 128);
         kv_arm = 1;
         kv_par = W & 1;
-        for (int h = 0; h < C::kHalves; ++h) {
+        for (int h = 0; h < 2; ++h) {
           tma_load_5d(smem + C::kK + h * 16384, &tk, kv_full, 64 * h, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
                       tbk.tb.lo[0] + o[0], bh);
           tma_load_5d(smem + C::kV + h * 16384, &tv, kv_full, 64 * h, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
                       tbk.tb.lo[0] + o[0], bh);
         }
         const int64_t slot0 = tile_slot0(g, bh, tile);
-        for (int i = 0; i < tbk.NB; ++i, ++G) {
+        BlockWalk bw;
+        for (int i = 0; i < tbk.NB; ++i, ++G, bw.next(tbk)) {
           const uint32_t st = G % C::kStages, n = G / C::kStages;
-          block_origin(g, tbk, i, o);
+          const int c1 = tbk.tb.lo[2] + bw.jx * g.bx, c2 = tbk.tb.lo[1] + bw.jy * g.by,
+                    c3 = tbk.tb.lo[0] + bw.jt * g.bt;
           if (!(ok = WAIT(qd_empty + st, (n & 1) ^ 1))) break;
-          mbar_arrive_expect_tx(qd_full + st, 2 * C::kHalves * g.R * 128 + 1024);
+          mbar_arrive_expect_tx(qd_full + st, 4 * g.R * 128 + 2048);
           qd_arm |= 1u << st;
           qd_par = (qd_par & ~(1u << st)) | ((n & 1) << st);
-          uint8_t* sq = smem + C::kQ + st * 2 * C::kBlock;
-          for (int h = 0; h < C::kHalves; ++h) {
-            tma_load_5d(sq + h * 16384, &tq, qd_full + st, 64 * h, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
-                        tbk.tb.lo[0] + o[0], bh);
-            tma_load_5d(sq + C::kBlock + h * 16384, &tdo, qd_full + st, 64 * h, tbk.tb.lo[2] + o[2],
-                        tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
+          uint8_t* sq = smem + C::kQ + st * 2 * kBox;
+          for (int h = 0; h < 2; ++h) {
+            tma_load_5d(sq + h * 16384, &tq, qd_full + st, 64 * h, c1, c2, c3, bh);
+            tma_load_5d(sq + kBox + h * 16384, &tdo, qd_full + st, 64 * h, c1, c2, c3, bh);
           }
-          bulk_load(smem + C::kStat + st * 1024, a.lse2c + slot0 + i * 128, 512, qd_full + st);
-          bulk_load(smem + C::kStat + st * 1024 + 512, a.dd + slot0 + i * 128, 512, qd_full + st);
+          bulk_load(smem + C::kExt + st * 4096, a.ext + slot0 + i * 128, 2048, qd_full + st);
         }
         ++W;
       }
@@ -167,13 +192,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
+    // ------------------------------------------------------------ issuer of S'^T, dP'^T
     if (lane == 0) {
-      constexpr uint32_t idS = idesc_bf16(128, 64, 0);
-      constexpr uint32_t idA = idesc_bf16(128, D, 1);
-      const uint32_t sK = smem_u32(smem + C::kK), sV = smem_u32(smem + C::kV), sQ = smem_u32(smem + C::kQ),
-                     sP = smem_u32(smem + C::kP);
-      uint32_t G = 0, H = 0, W = 0;
+      constexpr uint32_t idS = idesc_bf16(128, 128, 0);
+      const uint32_t sK = smem_u32(smem + C::kK), sV = smem_u32(smem + C::kV), sQ = smem_u32(smem + C::kQ);
+      const uint64_t dOnesS = noswz_desc(smem_u32(smem + C::kOnes), 2048, 128);
+      const uint64_t dOnesD = dmove(dOnesS, 4096);
+      const uint64_t dExt0 = noswz_desc(smem_u32(smem + C::kExt), 2048, 128);
+      uint32_t G = 0, W = 0;
       bool ok = true;
       for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
         int bh, tile, kb;
@@ -182,78 +208,86 @@ __global__ void __launch_bounds__(kThreads, 1)
         tile_blocks(g, tile, tbk);
         if (kb >= tbk.NB) continue;
         if (!(ok = WAIT(kv_full, W & 1))) break;
-        tc_fence_after();
-        const uint32_t G0 = G, H0 = H;
-        // dV/dK accumulation of half-block h (this item's halves start at H0)
-        auto issue_acc = [&](uint32_t h) -> bool {
-          const uint32_t b = h & 1;
-          const uint32_t gbox = G0 + ((h - H0) >> 1), half = (h - H0) & 1, st = gbox % C::kStages;
-          if (!WAIT(p_full + b, (h >> 1) & 1)) return false;
-          if (h == H0 && !WAIT(acc_empty, (W & 1) ^ 1)) return false;
-          tc_fence_after();
-          const uint32_t sq = sQ + st * 2 * C::kBlock + half * 8192;
-          const uint32_t sdo = sq + C::kBlock;
-          const uint32_t pb = sP + b * 32768, dsb = pb + 16384;
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t acc = (h != H0 || ks > 0) ? 1u : 0u;
-            umma_bf16(tmem + C::kColDV, sw128_desc(pb + ks * 32, 16, 1024), sw128_desc(sdo + ks * 2048, 16384, 1024),
-                      idA, acc);
-            umma_bf16(tmem + C::kColDK, sw128_desc(dsb + ks * 32, 16, 1024), sw128_desc(sq + ks * 2048, 16384, 1024),
-                      idA, acc);
-          }
-          umma_commit(p_empty + b);
-          if (half == 1) umma_commit(qd_empty + st);
-          return true;
-        };
-        // The dV/dK product of half h is issued after the S^T/dP^T products of
-        // half h+1 (so the tensor pipe has work while the softmax warps finish h).
-        // With a single (Q, dOut) stage the next box's load waits for the last
-        // half of the previous box to be consumed, so that half is flushed first.
-        bool pending = false;
-        for (int i = 0; i < tbk.NB && ok; ++i, ++G) {
+        for (int i = 0; i < tbk.NB; ++i, ++G) {
           const uint32_t st = G % C::kStages;
-          if (C::kStages == 1 && pending) {
-            if (!(ok = issue_acc(H - 1))) break;
-            pending = false;
-          }
           if (!(ok = WAIT(qd_full + st, (G / C::kStages) & 1))) break;
-          for (int half = 0; half < 2; ++half, ++H) {
-            const uint32_t b = H & 1;
-            if (!(ok = WAIT(st_empty + b, ((H >> 1) & 1) ^ 1))) break;
-            tc_fence_after();
-            const uint32_t sq = sQ + st * 2 * C::kBlock + half * 8192;
-            const uint32_t sdo = sQ + st * 2 * C::kBlock + C::kBlock + half * 8192;
+          // the S'^T columns hold box G-1's packed P'^T until its dV product is done
+          if (G > 0 && !(ok = WAIT(p_empty, (G - 1) & 1))) break;
+          tc_fence_after();
+          const uint32_t sq = sQ + st * 2 * kBox, sdo = sq + kBox;
+          const uint64_t de = dmove(dExt0, st * 4096);
 #pragma unroll
-            for (int ks = 0; ks < D / 16; ++ks) {
-              umma_bf16(tmem + C::kColST + b * 64, sw128_desc(sK + kmaj_off(ks), 16, 1024),
-                        sw128_desc(sq + kmaj_off(ks), 16, 1024), idS, ks > 0);
-              umma_bf16(tmem + C::kColDP + b * 64, sw128_desc(sV + kmaj_off(ks), 16, 1024),
-                        sw128_desc(sdo + kmaj_off(ks), 16, 1024), idS, ks > 0);
-            }
-            umma_commit(st_full + b);
-            if (i == tbk.NB - 1 && half == 1) umma_commit(kv_empty);
-            if (pending && !(ok = issue_acc(H - 1))) break;
-            pending = true;
-          }
+          for (int ks = 0; ks < kD / 16; ++ks)
+            umma_bf16(tmem + C::kColST, sw128_desc(sK + kmaj_off(ks), 16, 1024), sw128_desc(sq + kmaj_off(ks), 16, 1024),
+                      idS, ks > 0);
+          umma_bf16(tmem + C::kColST, dOnesS, de, idS, 1u);
+          umma_commit(s_full);
+          // the dP'^T columns hold box G-1's packed dS^T until its dK product is done
+          if (G > 0 && !(ok = WAIT(p_empty + 1, (G - 1) & 1))) break;
+          tc_fence_after();
+#pragma unroll
+          for (int ks = 0; ks < kD / 16; ++ks)
+            umma_bf16(tmem + C::kColDP, sw128_desc(sV + kmaj_off(ks), 16, 1024),
+                      sw128_desc(sdo + kmaj_off(ks), 16, 1024), idS, ks > 0);
+          umma_bf16(tmem + C::kColDP, dOnesD, de, idS, 1u);
+          umma_commit(s_full + 1);
+          if (i == tbk.NB - 1) umma_commit(kv_empty);  // K, V of this item no longer read
         }
-        if (!ok) break;
-        if (pending && !(ok = issue_acc(H - 1))) break;
-        umma_commit(acc_full);
         ++W;
       }
       umma_commit(drain);
       mbar_wait<set_status_bwd>(drain, 0, abort_flag, false);
     }
+  } else if (warp == kIssuerA) {
+    // ------------------------------------------------------------ issuer of dV += P'^T dO, dK += dS^T Q
+    if (lane == 0) {
+      constexpr uint32_t idA = idesc_bf16(128, kD, 1);  // B MN-major (K = queries, N = d)
+      const uint32_t sQ = smem_u32(smem + C::kQ);
+      uint32_t G = 0, W = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
+        int bh, tile, kb;
+        decode_item(g, w, bh, tile, kb);
+        TileBlocks tbk;
+        tile_blocks(g, tile, tbk);
+        if (kb >= tbk.NB) continue;
+        for (int i = 0; i < tbk.NB; ++i, ++G) {
+          const uint32_t st = G % C::kStages;
+          const uint32_t sq = sQ + st * 2 * kBox, sdo = sq + kBox;
+          // p_full[c](G) implies s_full[c](G): the score product that read this
+          // stage is complete, so the qd_empty commit below covers every reader
+          if (!(ok = WAIT(p_full, G & 1))) break;
+          if (i == 0 && !(ok = WAIT(acc_empty, (W & 1) ^ 1))) break;
+          tc_fence_after();
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks)
+            umma_bf16_ts(tmem + C::kColDV, tmem + C::kColST + inplace_col(ks),
+                         sw128_desc(sdo + ks * 2048, 16384, 1024), idA, (i > 0 || ks > 0) ? 1u : 0u);
+          umma_commit(p_empty);
+          if (!(ok = WAIT(p_full + 1, G & 1))) break;
+          tc_fence_after();
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks)
+            umma_bf16_ts(tmem + C::kColDK, tmem + C::kColDP + inplace_col(ks),
+                         sw128_desc(sq + ks * 2048, 16384, 1024), idA, (i > 0 || ks > 0) ? 1u : 0u);
+          umma_commit(p_empty + 1);
+          umma_commit(qd_empty + st);
+        }
+        if (!ok) break;
+        umma_commit(acc_full);
+        ++W;
+      }
+      umma_commit(drain + 1);
+      mbar_wait<set_status_bwd>(drain + 1, 0, abort_flag, false);
+    }
   } else {
     // ------------------------------------------------------------ elementwise + epilogue (row = key)
     const int quad = warp & 3;
-    const int ch = (warp - 2) >> 2;  // which 32 of the 64 query columns of a half block
+    const int c4 = (warp - kMath0) >> 2;  // query columns [32 c4, 32 c4 + 32)
     const int row = quad * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
-    const uint32_t sP = smem_u32(smem + C::kP);
-    const float sl2 = g.scale_log2;
-    uint32_t G = 0, H = 0, W = 0;
+    const uint64_t s2 = f2pack(g.scale_log2, g.scale_log2);
+    uint32_t G = 0, W = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
       int bh, tile, kb;
@@ -262,53 +296,30 @@ __global__ void __launch_bounds__(kThreads, 1)
       tile_blocks(g, tile, tbk);
       if (kb >= tbk.NB) continue;
       for (int i = 0; i < tbk.NB && ok; ++i, ++G) {
-        const uint32_t st = G % C::kStages;
-        if (!(ok = WAIT(qd_full + st, (G / C::kStages) & 1))) break;
-        const float* sL = reinterpret_cast<const float*>(smem + C::kStat + st * 1024);
-        const float* sD = sL + 128;
-        for (int half = 0; half < 2; ++half, ++H) {
-          const uint32_t b = H & 1;
-          if (!(ok = WAIT(st_full + b, (H >> 1) & 1))) break;
-          tc_fence_after();
-          uint32_t sv[32], dv[32];
-          tmem_ld32(tl + C::kColST + b * 64 + ch * 32, sv);
-          tmem_ld32(tl + C::kColDP + b * 64 + ch * 32, dv);
-          tmem_wait_ld(sv);
-          tmem_wait_ld(dv);
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(st_empty + b);
-          // P' = exp2(s S^T log2e - lse'), dS^T = P' (dP^T - D); the stage holds -lse', -D
-          uint32_t pp[16], pd[16];
-          const float4* nL4 = reinterpret_cast<const float4*>(sL + half * 64 + ch * 32);
-          const float4* nD4 = reinterpret_cast<const float4*>(sD + half * 64 + ch * 32);
-          const uint64_t s2 = f2pack(sl2, sl2);
-#pragma unroll
-          for (int c4 = 0; c4 < 8; ++c4) {
-            const float4 l = nL4[c4], dn = nD4[c4];
-            const int c = 4 * c4;
-            float a0, a1, a2, a3;
-            f2unpack(ffma2(u2pack(sv[c], sv[c + 1]), s2, f2pack(l.x, l.y)), a0, a1);
-            f2unpack(ffma2(u2pack(sv[c + 2], sv[c + 3]), s2, f2pack(l.z, l.w)), a2, a3);
-            const float p0 = ex2(a0), p1 = ex2(a1), p2 = ex2(a2), p3 = ex2(a3);
-            float e0, e1, e2, e3;
-            f2unpack(fmul2(f2pack(p0, p1), fadd2(u2pack(dv[c], dv[c + 1]), f2pack(dn.x, dn.y))), e0, e1);
-            f2unpack(fmul2(f2pack(p2, p3), fadd2(u2pack(dv[c + 2], dv[c + 3]), f2pack(dn.z, dn.w))), e2, e3);
-            pp[2 * c4] = pack_bf16(p0, p1);
-            pp[2 * c4 + 1] = pack_bf16(p2, p3);
-            pd[2 * c4] = pack_bf16(e0, e1);
-            pd[2 * c4 + 1] = pack_bf16(e2, e3);
-          }
-          if (!(ok = WAIT(p_empty + b, ((H >> 1) & 1) ^ 1))) break;
-          store_row32(sP + b * 32768, row, ch, pp);
-          store_row32(sP + b * 32768 + 16384, row, ch, pd);
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(p_full + b);
-        }
+        if (!(ok = WAIT(s_full, G & 1))) break;
+        tc_fence_after();
+        uint32_t sv[32], dv[32], pk[16];
+        tmem_ld32(tl + C::kColST + c4 * 32, sv);
+        tmem_wait_ld(sv);
+        kv_p(sv, s2, pk);  // sv <- P'^T (FP32), pk <- P'^T (BF16 pairs)
+        tmem_st16(tl + C::kColST + c4 * 32, pk);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(p_full);
+        if (!(ok = WAIT(s_full + 1, G & 1))) break;
+        tc_fence_after();
+        tmem_ld32(tl + C::kColDP + c4 * 32, dv);
+        tmem_wait_ld(dv);
+        kv_ds(sv, dv, pk);  // dS^T = P'^T dP'^T (BF16 pairs)
+        tmem_st16(tl + C::kColDP + c4 * 32, pk);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(p_full + 1);
       }
       if (!ok) break;
-      // ---- epilogue: this thread's key row of dK, dV (its half of the columns)
+      // ---- epilogue: this thread's key row of dK, dV (columns [32 c4, 32 c4 + 32))
       if (!(ok = WAIT(acc_full, W & 1))) break;
       tc_fence_after();
       int ko[3], kl[3];
@@ -319,16 +330,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t tok = kvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
       const bool single = kvalid && single_cover(g, p);
       const int64_t slot = tile_slot0(g, bh, tile) + kb * 128 + row;
-      const int c0 = ch * (D / 2);
-      tmem_row_epilogue<D / 2, OutT>(tl + C::kColDK + c0, g.scale, kvalid, single,
-                                     static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * D + c0,
-                                     a.dk_s + slot * D + c0);
-      tmem_row_epilogue<D / 2, OutT>(tl + C::kColDV + c0, 1.f, kvalid, single,
-                                     static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * D + c0,
-                                     a.dv_s + slot * D + c0);
+      const int c0 = c4 * 32;
+      // both accumulators into registers, then they are released at once: the
+      // next item's first gradient products may overwrite them during the stores
+      uint32_t rk[32], rv[32];
+      tmem_ld32(tl + C::kColDK + c0, rk);
+      tmem_ld32(tl + C::kColDV + c0, rv);
+      tmem_wait_ld(rk);
+      tmem_wait_ld(rv);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
+      row_store<32, OutT>(rk, g.scale, kvalid, single, static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * kD + c0,
+                          a.dk_s + slot * kD + c0);
+      row_store<32, OutT>(rv, 1.f, kvalid, single, static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * kD + c0,
+                          a.dv_s + slot * kD + c0);
       ++W;
     }
   }
@@ -341,34 +357,31 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // =============================================================== dQ
-template <int D>
-struct QCfg {
-  static constexpr int kHalves = D / 64;
-  static constexpr int kBlock = 128 * D * 2;
-  static constexpr int kStages = D == 64 ? 3 : 2;  // (K, V) ring
+struct Q128 {
+  static constexpr int kStages = 2;  // (K, V, key-bias row) ring
   static constexpr int kQ = 0;
-  static constexpr int kDO = kBlock;
-  static constexpr int kK = 2 * kBlock;            // stage s: K at kK + s*2*kBlock, V after it
-  static constexpr int kDS = kK + kStages * 2 * kBlock;  // 2 buffers x 16 KB (dS, 128 queries x 64 keys)
-  static constexpr int kBar = kDS + 2 * 16384;
-  // qd_full, qd_empty, kv_full[S], kv_empty[S], s_full[2], s_empty[2], ds_full[2], ds_empty[2],
-  // acc_full, acc_empty, drain
-  static constexpr int kNumBars = 2 + 2 * kStages + 8 + 3;
+  static constexpr int kDO = kBox;
+  static constexpr int kK = 2 * kBox;  // stage s: K at kK + s*2*kBox, V after it
+  // Key-mask extension operands (as in the forward): A = 1 in K-column 0 of
+  // 128 rows, and per stage the key box's bias row (0, or -1e30 for a padding
+  // key or a key outside the tile), each followed by 2 KB of zeros.
+  static constexpr int kOnes = kK + kStages * 2 * kBox;
+  static constexpr int kBias = kOnes + 4096;
+  static constexpr int kBar = kBias + kStages * 4096;
+  // qd_full, qd_empty, kv_full[S], kv_empty[S], s_full[2], s_empty[2], p_full[2], p_empty[2],
+  // acc_full, acc_empty, drain[2]   (s_*[0]: the S chain, s_*[1]: the dP chain; p_*[b]: dS buffer b)
+  static constexpr int kNumBars = 2 + 2 * kStages + 12;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kSmem = kMisc + 16 + 1024;
-  // TMEM columns: S[2] 0/64, dP[2] 128/192, dQ 256
-  static constexpr uint32_t kColS = 0, kColDP = 128, kColDQ = 256;
+  // TMEM: S 0, dP 128, dQ 256, dS buffer b (packed) 384 + 64 b
+  static constexpr uint32_t kColS = 0, kColDP = 128, kColDQ = 256, kColDS = 384;
 };
 
-// dS = P' (dP - D) for 32 key columns of this thread's query row, packed to
-// BF16; nL = -lse', nD = -D of the row; keys outside the tile masked to 0.
-
-template <int D, typename OutT>
-__global__ void __launch_bounds__(kThreads, 1)
-    sm103_dq_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
-                    const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tdo,
-                    const BwdArgs a) {
-  using C = QCfg<D>;
+template <typename OutT>
+__global__ void __launch_bounds__(kThreadsB, 1)
+    dq128_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
+                 const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tdo, const BwdArgs a) {
+  using C = Q128;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kBar);
@@ -378,16 +391,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* kv_empty = kv_full + C::kStages;
   uint64_t* s_full = kv_empty + C::kStages;
   uint64_t* s_empty = s_full + 2;
-  uint64_t* ds_full = s_empty + 2;
-  uint64_t* ds_empty = ds_full + 2;
-  uint64_t* acc_full = ds_empty + 2;
+  uint64_t* p_full = s_empty + 2;  // [2]: one per dS buffer
+  uint64_t* p_empty = p_full + 2;  // [2]
+  uint64_t* acc_full = p_empty + 2;
   uint64_t* acc_empty = acc_full + 1;
-  uint64_t* drain = acc_empty + 1;
+  uint64_t* drain = acc_empty + 1;  // [2]: one per issuing thread
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  zero_pad_rows(smem, (2 + 2 * C::kStages) * C::kHalves, a.g.R);  // Q, dOut and the K / V ring
+  init_ext_operands(smem + C::kOnes, 1, false, smem + C::kBias, C::kStages);
+  zero_pad_rows(smem, (2 + 2 * C::kStages) * 2, a.g.R);  // Q, dOut and the K / V ring (16 KB halves)
+  fence_proxy_async_smem();
   if (threadIdx.x == 0) {
     mbar_init(qd_full, 1);
     mbar_init(qd_empty, 1);
@@ -395,15 +410,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(kv_full + s, 1);
       mbar_init(kv_empty + s, 1);
     }
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(s_full + s, 1);
-      mbar_init(s_empty + s, kMathWarps);
-      mbar_init(ds_full + s, kMathWarps);
-      mbar_init(ds_empty + s, 1);
+    for (int c = 0; c < 2; ++c) {
+      mbar_init(s_full + c, 1);
+      mbar_init(s_empty + c, kMathW);
+      mbar_init(p_full + c, kMathW);
+      mbar_init(p_empty + c, 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kMathWarps);
+    mbar_init(acc_empty, kMathW);
     mbar_init(drain, 1);
+    mbar_init(drain + 1, 1);
     *abort_flag = 0;
     fence_mbar_init();
     prefetch_tmap(&tq);
@@ -422,58 +438,79 @@ __global__ void __launch_bounds__(kThreads, 1)
   const Geom& g = a.g;
 
   if (warp == 0) {
-    if (lane == 0) {
-      uint32_t G = 0, W = 0;
-      uint32_t qd_arm = 0, qd_par = 0, kv_arm = 0, kv_par = 0;
-      bool ok = true;
-      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
-        int bh, tile, qb;
-        decode_item(g, w, bh, tile, qb);
-        TileBlocks tbk;
-        tile_blocks(g, tile, tbk);
-        if (qb >= tbk.NB) continue;
-        int o[3];
-        block_origin(g, tbk, qb, o);
-        if (!(ok = WAIT(qd_empty, (W & 1) ^ 1))) break;
-        mbar_arrive_expect_tx(qd_full, 2 * C::kHalves * g.R * 128);
-        qd_arm = 1;
-        qd_par = W & 1;
-        for (int h = 0; h < C::kHalves; ++h) {
-          tma_load_5d(smem + C::kQ + h * 16384, &tq, qd_full, 64 * h, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
-                      tbk.tb.lo[0] + o[0], bh);
-          tma_load_5d(smem + C::kDO + h * 16384, &tdo, qd_full, 64 * h, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
-                      tbk.tb.lo[0] + o[0], bh);
-        }
-        for (int j = 0; j < tbk.NB; ++j, ++G) {
-          const uint32_t st = G % C::kStages, n = G / C::kStages;
-          block_origin(g, tbk, j, o);
-          if (!(ok = WAIT(kv_empty + st, (n & 1) ^ 1))) break;
-          mbar_arrive_expect_tx(kv_full + st, 2 * C::kHalves * g.R * 128);
-          kv_arm |= 1u << st;
-          kv_par = (kv_par & ~(1u << st)) | ((n & 1) << st);
-          uint8_t* sk = smem + C::kK + st * 2 * C::kBlock;
-          for (int h = 0; h < C::kHalves; ++h) {
-            tma_load_5d(sk + h * 16384, &tk, kv_full + st, 64 * h, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
+    // ------------------------------------------------------------ TMA producer (lane 0) and
+    // key-mask rows (all lanes, for key boxes with padding rows or keys outside the tile)
+    const uint32_t neg = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(-1e30f));
+    uint32_t G = 0, W = 0;
+    uint32_t qd_arm = 0, qd_par = 0, kv_arm = 0, kv_par = 0;
+    bool ok = true;
+    for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
+      int bh, tile, qb;
+      decode_item(g, w, bh, tile, qb);
+      TileBlocks tbk;
+      tile_blocks(g, tile, tbk);
+      if (qb >= tbk.NB) continue;
+      int o[3];
+      block_origin(g, tbk, qb, o);
+      if (lane == 0) {
+        if ((ok = WAIT(qd_empty, (W & 1) ^ 1))) {
+          mbar_arrive_expect_tx(qd_full, 4 * g.R * 128);
+          qd_arm = 1;
+          qd_par = W & 1;
+          for (int h = 0; h < 2; ++h) {
+            tma_load_5d(smem + C::kQ + h * 16384, &tq, qd_full, 64 * h, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
                         tbk.tb.lo[0] + o[0], bh);
-            tma_load_5d(sk + C::kBlock + h * 16384, &tv, kv_full + st, 64 * h, tbk.tb.lo[2] + o[2],
-                        tbk.tb.lo[1] + o[1], tbk.tb.lo[0] + o[0], bh);
+            tma_load_5d(smem + C::kDO + h * 16384, &tdo, qd_full, 64 * h, tbk.tb.lo[2] + o[2], tbk.tb.lo[1] + o[1],
+                        tbk.tb.lo[0] + o[0], bh);
           }
         }
-        ++W;
       }
-      if (!ok) {
-        if (qd_arm) mbar_wait<set_status_bwd>(qd_full, qd_par, abort_flag, false);
-        for (int s = 0; s < C::kStages; ++s)
-          if (kv_arm & (1u << s)) mbar_wait<set_status_bwd>(kv_full + s, (kv_par >> s) & 1, abort_flag, false);
+      if (!(ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0)) break;
+      for (int j = 0; j < tbk.NB; ++j, ++G) {
+        const uint32_t st = G % C::kStages, n = G / C::kStages;
+        int ko[3];
+        block_origin(g, tbk, j, ko);
+        // the stage (K, V and its bias row) is free once box G - kStages is done
+        if (lane == 0) ok = WAIT(kv_empty + st, (n & 1) ^ 1);
+        if (!(ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0)) break;
+        if (!block_full(g, tbk, ko)) {
+          for (int r = lane; r < 128; r += 32) {
+            int kl[3];
+            block_row(g, ko, r, kl);
+            *reinterpret_cast<uint4*>(smem + C::kBias + st * 4096 + r * 16) =
+                make_uint4(inside(tbk, kl) ? 0u : neg, 0u, 0u, 0u);
+          }
+          fence_proxy_async_smem();
+        }
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive_expect_tx(kv_full + st, 4 * g.R * 128);
+          kv_arm |= 1u << st;
+          kv_par = (kv_par & ~(1u << st)) | ((n & 1) << st);
+          uint8_t* sk = smem + C::kK + st * 2 * kBox;
+          for (int h = 0; h < 2; ++h) {
+            tma_load_5d(sk + h * 16384, &tk, kv_full + st, 64 * h, tbk.tb.lo[2] + ko[2], tbk.tb.lo[1] + ko[1],
+                        tbk.tb.lo[0] + ko[0], bh);
+            tma_load_5d(sk + kBox + h * 16384, &tv, kv_full + st, 64 * h, tbk.tb.lo[2] + ko[2],
+                        tbk.tb.lo[1] + ko[1], tbk.tb.lo[0] + ko[0], bh);
+          }
+        }
       }
+      ++W;
+    }
+    if (!ok && lane == 0) {
+      if (qd_arm) mbar_wait<set_status_bwd>(qd_full, qd_par, abort_flag, false);
+      for (int s = 0; s < C::kStages; ++s)
+        if (kv_arm & (1u << s)) mbar_wait<set_status_bwd>(kv_full + s, (kv_par >> s) & 1, abort_flag, false);
     }
   } else if (warp == 1) {
+    // ------------------------------------------------------------ issuer of S, dP
     if (lane == 0) {
-      constexpr uint32_t idS = idesc_bf16(128, 64, 0);
-      constexpr uint32_t idA = idesc_bf16(128, D, 1);
-      const uint32_t sQ = smem_u32(smem + C::kQ), sDO = smem_u32(smem + C::kDO), sK = smem_u32(smem + C::kK),
-                     sDS = smem_u32(smem + C::kDS);
-      uint32_t G = 0, H = 0, W = 0;
+      constexpr uint32_t idS = idesc_bf16(128, 128, 0);
+      const uint32_t sQ = smem_u32(smem + C::kQ), sDO = smem_u32(smem + C::kDO), sK = smem_u32(smem + C::kK);
+      const uint64_t dOnes = noswz_desc(smem_u32(smem + C::kOnes), 2048, 128);
+      const uint64_t dBias0 = noswz_desc(smem_u32(smem + C::kBias), 2048, 128);
+      uint32_t G = 0, W = 0;
       bool ok = true;
       for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
         int bh, tile, qb;
@@ -482,61 +519,82 @@ __global__ void __launch_bounds__(kThreads, 1)
         tile_blocks(g, tile, tbk);
         if (qb >= tbk.NB) continue;
         if (!(ok = WAIT(qd_full, W & 1))) break;
-        tc_fence_after();
-        const uint32_t G0 = G, H0 = H;
-        auto issue_dq = [&](uint32_t h) -> bool {
-          const uint32_t b = h & 1;
-          const uint32_t gbox = G0 + ((h - H0) >> 1), half = (h - H0) & 1, st = gbox % C::kStages;
-          if (!WAIT(ds_full + b, (h >> 1) & 1)) return false;
-          if (h == H0 && !WAIT(acc_empty, (W & 1) ^ 1)) return false;
-          tc_fence_after();
-          const uint32_t sk = sK + st * 2 * C::kBlock + half * 8192;
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            umma_bf16(tmem + C::kColDQ, sw128_desc(sDS + b * 16384 + ks * 32, 16, 1024),
-                      sw128_desc(sk + ks * 2048, 16384, 1024), idA, (h != H0 || ks > 0) ? 1u : 0u);
-          umma_commit(ds_empty + b);
-          if (half == 1) umma_commit(kv_empty + st);
-          return true;
-        };
-        for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
+        const bool all_full = tile_all_full(g, tbk);
+        BlockWalk bw;
+        for (int j = 0; j < tbk.NB; ++j, ++G, bw.next(tbk)) {
           const uint32_t st = G % C::kStages;
+          // a masked box's bias row was filled by the producer warp
+          const bool masked = !all_full && !bw.full(g, tbk);
           if (!(ok = WAIT(kv_full + st, (G / C::kStages) & 1))) break;
-          for (int half = 0; half < 2; ++half, ++H) {
-            const uint32_t b = H & 1;
-            if (!(ok = WAIT(s_empty + b, ((H >> 1) & 1) ^ 1))) break;
-            tc_fence_after();
-            const uint32_t sk = sK + st * 2 * C::kBlock + half * 8192;
-            const uint32_t sv = sk + C::kBlock;
+          if (G > 0 && !(ok = WAIT(s_empty, (G - 1) & 1))) break;  // S of box G-1 read
+          tc_fence_after();
+          const uint32_t sk = sK + st * 2 * kBox, sv = sk + kBox;
 #pragma unroll
-            for (int ks = 0; ks < D / 16; ++ks) {
-              umma_bf16(tmem + C::kColS + b * 64, sw128_desc(sQ + kmaj_off(ks), 16, 1024),
-                        sw128_desc(sk + kmaj_off(ks), 16, 1024), idS, ks > 0);
-              umma_bf16(tmem + C::kColDP + b * 64, sw128_desc(sDO + kmaj_off(ks), 16, 1024),
-                        sw128_desc(sv + kmaj_off(ks), 16, 1024), idS, ks > 0);
-            }
-            umma_commit(s_full + b);
-            if (j == tbk.NB - 1 && half == 1) umma_commit(qd_empty);
-            if (H > H0 && !(ok = issue_dq(H - 1))) break;
-          }
+          for (int ks = 0; ks < kD / 16; ++ks)
+            umma_bf16(tmem + C::kColS, sw128_desc(sQ + kmaj_off(ks), 16, 1024), sw128_desc(sk + kmaj_off(ks), 16, 1024),
+                      idS, ks > 0);
+          // masked keys get -1e30, so P' = 0 there and dS = 0 follows
+          if (masked) umma_bf16(tmem + C::kColS, dOnes, dmove(dBias0, st * 4096), idS, 1u);
+          umma_commit(s_full);
+          if (G > 0 && !(ok = WAIT(s_empty + 1, (G - 1) & 1))) break;  // dP of box G-1 read
+          tc_fence_after();
+#pragma unroll
+          for (int ks = 0; ks < kD / 16; ++ks)
+            umma_bf16(tmem + C::kColDP, sw128_desc(sDO + kmaj_off(ks), 16, 1024),
+                      sw128_desc(sv + kmaj_off(ks), 16, 1024), idS, ks > 0);
+          umma_commit(s_full + 1);
+          if (j == tbk.NB - 1) umma_commit(qd_empty);  // Q, dOut of this item no longer read
         }
-        if (!ok) break;
-        if (!(ok = issue_dq(H - 1))) break;
-        umma_commit(acc_full);
         ++W;
       }
       umma_commit(drain);
       mbar_wait<set_status_bwd>(drain, 0, abort_flag, false);
     }
+  } else if (warp == kIssuerA) {
+    // ------------------------------------------------------------ issuer of dQ += dS K
+    if (lane == 0) {
+      constexpr uint32_t idA = idesc_bf16(128, kD, 1);  // B MN-major (K = keys, N = d)
+      const uint32_t sK = smem_u32(smem + C::kK);
+      uint32_t G = 0, W = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
+        int bh, tile, qb;
+        decode_item(g, w, bh, tile, qb);
+        TileBlocks tbk;
+        tile_blocks(g, tile, tbk);
+        if (qb >= tbk.NB) continue;
+        for (int j = 0; j < tbk.NB; ++j, ++G) {
+          const uint32_t st = G % C::kStages;
+          // p_full(G) implies s_full(G): the score products of this stage are
+          // complete, so the kv_empty commit below covers every reader.  dS is
+          // double-buffered: box G uses buffer G & 1.
+          const uint32_t b = G & 1;
+          if (!(ok = WAIT(p_full + b, (G >> 1) & 1))) break;
+          if (j == 0 && !(ok = WAIT(acc_empty, (W & 1) ^ 1))) break;
+          tc_fence_after();
+          const uint32_t sk = sK + st * 2 * kBox;
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks)
+            umma_bf16_ts(tmem + C::kColDQ, tmem + C::kColDS + 64 * b + ks * 8, sw128_desc(sk + ks * 2048, 16384, 1024),
+                         idA, (j > 0 || ks > 0) ? 1u : 0u);
+          umma_commit(p_empty + b);
+          umma_commit(kv_empty + st);
+        }
+        if (!ok) break;
+        umma_commit(acc_full);
+        ++W;
+      }
+      umma_commit(drain + 1);
+      mbar_wait<set_status_bwd>(drain + 1, 0, abort_flag, false);
+    }
   } else {
     // ------------------------------------------------------------ elementwise + epilogue (row = query)
     const int quad = warp & 3;
-    const int ch = (warp - 2) >> 2;  // which 32 of the 64 key columns of a half block
+    const int c4 = (warp - kMath0) >> 2;  // key columns [32 c4, 32 c4 + 32)
     const int row = quad * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
-    const uint32_t sDS = smem_u32(smem + C::kDS);
     const float sl2 = g.scale_log2;
-    uint32_t G = 0, H = 0, W = 0;
+    uint32_t G = 0, W = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
       int bh, tile, qb;
@@ -548,41 +606,32 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float nL = a.lse2c[qslot];  // -lse' (-inf for padding rows)
       const float nD = a.dd[qslot];     // -D
       for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
-        int ko[3];
-        block_origin(g, tbk, j, ko);
-        const bool full = block_full(g, tbk, ko);
-        uint32_t kmask[2] = {~0u, ~0u};
-        if (!full) {
-#pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2) {
-            int kl[3];
-            block_row(g, ko, h2 * 64 + ch * 32 + lane, kl);
-            kmask[h2] = __ballot_sync(0xffffffffu, inside(tbk, kl));
-          }
-        }
-        for (int half = 0; half < 2; ++half, ++H) {
-          const uint32_t b = H & 1;
-          if (!(ok = WAIT(s_full + b, (H >> 1) & 1))) break;
-          tc_fence_after();
-          uint32_t sv[32], dv[32];
-          tmem_ld32(tl + C::kColS + b * 64 + ch * 32, sv);
-          tmem_ld32(tl + C::kColDP + b * 64 + ch * 32, dv);
-          tmem_wait_ld(sv);
-          tmem_wait_ld(dv);
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(s_empty + b);
-          uint32_t pk[16];
-          if (full)
-            dq_half<false>(sv, dv, 0u, sl2, nL, nD, pk);
-          else
-            dq_half<true>(sv, dv, kmask[half], sl2, nL, nD, pk);
-          if (!(ok = WAIT(ds_empty + b, ((H >> 1) & 1) ^ 1))) break;
-          store_row32(sDS + b * 16384, row, ch, pk);
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(ds_full + b);
-        }
+        if (!(ok = WAIT(s_full, G & 1))) break;
+        tc_fence_after();
+        uint32_t sv[32], dv[32], pk[16];
+        tmem_ld32(tl + C::kColS + c4 * 32, sv);
+        tmem_wait_ld(sv);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(s_empty);  // the next box's S may overwrite this one
+        q_p(sv, sl2, nL);  // sv <- P' (FP32); masked keys carry -1e30 from the extension step
+        if (!(ok = WAIT(s_full + 1, G & 1))) break;
+        tc_fence_after();
+        tmem_ld32(tl + C::kColDP + c4 * 32, dv);
+        tmem_wait_ld(dv);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(s_empty + 1);  // the next box's dP may overwrite this one
+        q_ds(sv, dv, nD, pk);
+        // dS buffer G & 1 is free once the dQ products of box G-2 are done
+        const uint32_t b = G & 1;
+        if (G > 1 && !(ok = WAIT(p_empty + b, ((G >> 1) - 1) & 1))) break;
+        tc_fence_after();
+        tmem_st16(tl + C::kColDS + 64 * b + c4 * 16, pk);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(p_full + b);
       }
       if (!ok) break;
       if (!(ok = WAIT(acc_full, W & 1))) break;
@@ -594,13 +643,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int p[3] = {tbk.tb.lo[0] + ql[0], tbk.tb.lo[1] + ql[1], tbk.tb.lo[2] + ql[2]};
       const int64_t tok = qvalid ? ((int64_t)p[0] * g.G[1] + p[1]) * g.G[2] + p[2] : 0;
       const bool single = qvalid && single_cover(g, p);
-      const int c0 = ch * (D / 2);
-      tmem_row_epilogue<D / 2, OutT>(tl + C::kColDQ + c0, g.scale, qvalid, single,
-                                     static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * D + c0,
-                                     a.dq_s + qslot * D + c0);
+      const int c0 = c4 * 32;
+      uint32_t rq[32];
+      tmem_ld32(tl + C::kColDQ + c0, rq);
+      tmem_wait_ld(rq);
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
+      if (lane == 0) mbar_arrive(acc_empty);  // released before the stores
+      row_store<32, OutT>(rq, g.scale, qvalid, single, static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * kD + c0,
+                          a.dq_s + qslot * kD + c0);
       ++W;
     }
   }
@@ -612,14 +663,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int D, typename OutT>
-cudaError_t run_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v,
-                    const __nv_bfloat16* dout, const float* lse2c, const float* dd, void* dq, void* dk, void* dv,
-                    float* dq_s, float* dk_s, float* dv_s, cudaStream_t st) {
+template <typename OutT>
+cudaError_t run_bwd128(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v,
+                       const __nv_bfloat16* dout, const float* lse2c, const float* dd, const void* ext, void* dq,
+                       void* dk, void* dv, float* dq_s, float* dk_s, float* dv_s, cudaStream_t st) {
+  if (!ext || reinterpret_cast<uintptr_t>(ext) % 16) return cudaErrorInvalidValue;
   BwdArgs a;
   a.g = g;
   a.lse2c = lse2c;
   a.dd = dd;
+  a.ext = static_cast<const uint4*>(ext);
   a.dq = dq;
   a.dk = dk;
   a.dv = dv;
@@ -631,24 +684,24 @@ cudaError_t run_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
   a.items = (int)items;
   const int BH = g.B * g.nh;
   CUtensorMap mq, mk, mv, mdo;
-  if (!make_tmap_5d(&mq, q, D, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
-      !make_tmap_5d(&mk, k, D, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
-      !make_tmap_5d(&mv, v, D, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
-      !make_tmap_5d(&mdo, dout, D, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt))
+  if (!make_tmap_5d(&mq, q, kD, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
+      !make_tmap_5d(&mk, k, kD, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
+      !make_tmap_5d(&mv, v, kD, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt) ||
+      !make_tmap_5d(&mdo, dout, kD, g.G[2], g.G[1], g.G[0], BH, g.bx, g.by, g.bt))
     return cudaErrorInvalidValue;
   const int grid = (int)(a.items < num_sms() ? a.items : num_sms());
-  auto k1 = sm103_dkdv_kernel<D, OutT>;
-  cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, KvCfg<D>::kSmem);
+  auto k1 = dkdv128_kernel<OutT>;
+  cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, Kv128::kSmem);
   if (e != cudaSuccess) return e;
   prof_begin(kKBwdDkdv, st);
-  k1<<<grid, kThreads, KvCfg<D>::kSmem, st>>>(mq, mk, mv, mdo, a);
+  k1<<<grid, kThreadsB, Kv128::kSmem, st>>>(mq, mk, mv, mdo, a);
   prof_end(kKBwdDkdv, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  auto k2 = sm103_dq_kernel<D, OutT>;
-  e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, QCfg<D>::kSmem);
+  auto k2 = dq128_kernel<OutT>;
+  e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, Q128::kSmem);
   if (e != cudaSuccess) return e;
   prof_begin(kKBwdDq, st);
-  k2<<<grid, kThreads, QCfg<D>::kSmem, st>>>(mq, mk, mv, mdo, a);
+  k2<<<grid, kThreadsB, Q128::kSmem, st>>>(mq, mk, mv, mdo, a);
   prof_end(kKBwdDq, st);
   return cudaGetLastError();
 }
@@ -657,17 +710,14 @@ cudaError_t run_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* 
 
 cudaError_t launch_sm103_bwd(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16* k, const __nv_bfloat16* v,
                              const __nv_bfloat16* dout, const float* lse2c, const float* dd, const void* ext,
-                             void* dq, void* dk,
-                             void* dv, int out_dtype, float* dq_s, float* dk_s, float* dv_s, uint32_t,
-                             cudaStream_t st) {
-  const bool bf = out_dtype == GATTN_BF16;
-  using bf16 = __nv_bfloat16;
+                             void* dq, void* dk, void* dv, int out_dtype, float* dq_s, float* dk_s, float* dv_s,
+                             uint32_t, cudaStream_t st) {
   if (g.d == 64)
     return launch_sm103_bwd64(g, q, k, v, dout, lse2c, dd, ext, dq, dk, dv, out_dtype, dq_s, dk_s, dv_s, st);
-  if (g.d == 128)
-    return bf ? run_bwd<128, bf16>(g, q, k, v, dout, lse2c, dd, dq, dk, dv, dq_s, dk_s, dv_s, st)
-              : run_bwd<128, float>(g, q, k, v, dout, lse2c, dd, dq, dk, dv, dq_s, dk_s, dv_s, st);
-  return cudaErrorNotSupported;
+  if (g.d != kD) return cudaErrorNotSupported;
+  if (out_dtype == GATTN_BF16)
+    return run_bwd128<__nv_bfloat16>(g, q, k, v, dout, lse2c, dd, ext, dq, dk, dv, dq_s, dk_s, dv_s, st);
+  return run_bwd128<float>(g, q, k, v, dout, lse2c, dd, ext, dq, dk, dv, dq_s, dk_s, dv_s, st);
 }
 
 }  // namespace gattn

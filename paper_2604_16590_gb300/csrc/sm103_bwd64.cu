@@ -63,28 +63,8 @@ __device__ void set_status_bwd64(uint32_t c) { set_status(c); }
 
 constexpr int kD = 64;
 constexpr int kBox = 128 * kD * 2;  // one 128-token box of one operand, BF16, 16 KB
-constexpr int kMath64 = 16;                 // math warps: 4 per TMEM lane quadrant
-constexpr int kMath0 = 3;                   // first math warp
-constexpr int kIssuerA = 2;                 // warp index of the gradient-product issuer
-constexpr int kThreads64 = 32 * (kMath0 + kMath64);
-
-// Stores 16 FP32 values of this thread's row (already in registers), scaled
-// by `mul`: to `out` (OutT) if the row is covered by one tile, else to the
-// FP32 slot `scr`, nothing if the row lies outside the tile.
-template <typename OutT>
-__device__ __forceinline__ void row_store16(const uint32_t (&r)[16], float mul, bool valid, bool single, OutT* out,
-                                            float* scr) {
-  if (!valid) return;
-#pragma unroll
-  for (int e = 0; e < 16; e += 4) {
-    const float4 v = make_float4(__uint_as_float(r[e]) * mul, __uint_as_float(r[e + 1]) * mul,
-                                 __uint_as_float(r[e + 2]) * mul, __uint_as_float(r[e + 3]) * mul);
-    if (single)
-      store4<OutT>(out + e, v);
-    else
-      store4<float>(scr + e, v);
-  }
-}
+constexpr int kMath64 = kMathW;      // math warps: 4 per TMEM lane quadrant
+constexpr int kThreads64 = kThreadsB;
 
 // =============================================================== dK / dV
 struct Kv64 {
@@ -105,29 +85,6 @@ struct Kv64 {
   // TMEM: S'^T 0, dP'^T 128, P'^T (packed) 256, dS^T (packed) 320, dV 384, dK 448
   static constexpr uint32_t kColST = 0, kColDP = 128, kColP = 256, kColDS = 320, kColDV = 384, kColDK = 448;
 };
-
-// P'^T of 32 columns of this thread's key row (S'^T already carries the
-// statistics): FP32 in place of the scores, and as BF16 pairs.
-__device__ __forceinline__ void kv_p(uint32_t (&s)[32], uint64_t s2, uint32_t (&pp)[16]) {
-#pragma unroll
-  for (int c = 0; c < 32; c += 2) {
-    float a0, a1;
-    f2unpack(fmul2(u2pack(s[c], s[c + 1]), s2), a0, a1);
-    const float p0 = ex2(a0), p1 = ex2(a1);
-    s[c] = __float_as_uint(p0);
-    s[c + 1] = __float_as_uint(p1);
-    pp[c >> 1] = pack_bf16(p0, p1);
-  }
-}
-// dS^T = P'^T dP'^T (dP'^T already carries -D) as BF16 pairs
-__device__ __forceinline__ void kv_ds(const uint32_t (&p)[32], const uint32_t (&dp)[32], uint32_t (&pd)[16]) {
-#pragma unroll
-  for (int c = 0; c < 32; c += 2) {
-    float e0, e1;
-    f2unpack(fmul2(u2pack(p[c], p[c + 1]), u2pack(dp[c], dp[c + 1])), e0, e1);
-    pd[c >> 1] = pack_bf16(e0, e1);
-  }
-}
 
 template <typename OutT>
 __global__ void __launch_bounds__(kThreads64, 1)
@@ -416,9 +373,9 @@ __global__ void __launch_bounds__(kThreads64, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
-      row_store16<OutT>(rk, g.scale, kvalid, single, static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * kD + c0,
+      row_store<16, OutT>(rk, g.scale, kvalid, single, static_cast<OutT*>(a.dk) + ((int64_t)bh * g.N + tok) * kD + c0,
                         a.dk_s + slot * kD + c0);
-      row_store16<OutT>(rv, 1.f, kvalid, single, static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * kD + c0,
+      row_store<16, OutT>(rv, 1.f, kvalid, single, static_cast<OutT*>(a.dv) + ((int64_t)bh * g.N + tok) * kD + c0,
                         a.dv_s + slot * kD + c0);
       ++W;
     }
@@ -432,29 +389,6 @@ __global__ void __launch_bounds__(kThreads64, 1)
 }
 
 // =============================================================== dQ
-// P' = exp2(s S log2e - lse') of 32 columns of this thread's query row, FP32
-// in place of the scores
-__device__ __forceinline__ void q_p(uint32_t (&s)[32], float sl2, float nL) {
-  const uint64_t s2 = f2pack(sl2, sl2), nl2 = f2pack(nL, nL);
-#pragma unroll
-  for (int c = 0; c < 32; c += 2) {
-    float a0, a1;
-    f2unpack(ffma2(u2pack(s[c], s[c + 1]), s2, nl2), a0, a1);
-    s[c] = __float_as_uint(ex2(a0));
-    s[c + 1] = __float_as_uint(ex2(a1));
-  }
-}
-// dS = P' (dP - D) as BF16 pairs
-__device__ __forceinline__ void q_ds(const uint32_t (&p)[32], const uint32_t (&dp)[32], float nD, uint32_t (&pk)[16]) {
-  const uint64_t nd2 = f2pack(nD, nD);
-#pragma unroll
-  for (int c = 0; c < 32; c += 2) {
-    float e0, e1;
-    f2unpack(fmul2(u2pack(p[c], p[c + 1]), fadd2(u2pack(dp[c], dp[c + 1]), nd2)), e0, e1);
-    pk[c >> 1] = pack_bf16(e0, e1);
-  }
-}
-
 struct Q64 {
   static constexpr int kStages = 4;  // (K, V) ring
   static constexpr int kQ = 0;
@@ -767,7 +701,7 @@ __global__ void __launch_bounds__(kThreads64, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);  // released before the stores
-      row_store16<OutT>(rq, g.scale, qvalid, single, static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * kD + c0,
+      row_store<16, OutT>(rq, g.scale, qvalid, single, static_cast<OutT*>(a.dq) + ((int64_t)bh * g.N + tok) * kD + c0,
                         a.dq_s + qslot * kD + c0);
       ++W;
     }
