@@ -208,7 +208,7 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16&
   c = __float2bfloat16_rn(r1 - __bfloat162float(b));
 }
 
-// One 16-byte B-operand row (K = 8 BF16 values) of the d = 64 dK/dV kernel:
+// One 16-byte B-operand row (K = 8 BF16 values) of the BF16 dK/dV kernels:
 // (x0, x1, x2, y0, y1, y2, 0, 0) with x0+x1+x2 = x and y0+y1+y2 = y.  With an
 // A operand of ones in K-columns 0..2 (resp. 3..5) one extra MMA step adds x
 // (resp. y) to every element of the row's S^T (resp. dP^T) column.

@@ -56,6 +56,8 @@ WORKLOADS = {
     "c2_262k_s1": Workload("c2_262k_s1", 1, 4, 64, (32, 64, 128), (1, 16, 16), (0, 4, 4), 0.5, 20262, "bf16"),
     # long temporal context: 2048 frames x 32 x 64, d = 128, Tiles = 16 along time, halo 8 frames
     "c3_4m_p": Workload("c3_4m_p", 1, 8, 128, (2048, 32, 64), (128, 32, 64), (8, 0, 0), 0.5, 20263, "bf16"),
+    # the long-context geometry with 512 frames and one head (each tensor 268 MB > L2): profiling case
+    "c3_512_p1": Workload("c3_512_p1", 1, 1, 128, (512, 32, 64), (128, 32, 64), (8, 0, 0), 0.5, 20263, "bf16"),
     # gradient check size: 32 x 32, 2 heads, d = 32
     "c4_grad": Workload("c4_grad", 1, 2, 32, (1, 32, 32), (1, 16, 16), (0, 4, 4), 1.0, 20264, "fp32"),
     # backward throughput: 16 x 256 x 256, 8 heads, Tiles = 16
