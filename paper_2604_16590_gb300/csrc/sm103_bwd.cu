@@ -20,13 +20,14 @@
 // packs the 32 columns it read into the first 16 of them).  The next box's
 // S'^T therefore waits for this box's dV product, the reader of P'^T, and its
 // dP'^T for the dK product; with one issuing thread per product pair those
-// waits overlap the other pair's MMAs.  The dQ kernel has one accumulator, so
-// its packed dS has two buffers of its own: S 0, dP 128, dQ 256, dS 384 / 448.
+// waits overlap the other pair's MMAs.  The dQ kernel copies the item's Q and
+// dOut into TMEM (S 0, dP 128, dQ 256, Q 384, dOut 448) and packs its dS over
+// the dP it comes from.
 //
 // Shared memory (one operand box = 32 KB, two 64-element halves of 128-byte
 // rows): the dK/dV kernel holds the item's K and V and a two-stage ring of
-// (Q, dO, statistics rows); the dQ kernel the item's Q and dO and a two-stage
-// ring of (K, V, key-bias row).  A work item streams every box of its tile,
+// (Q, dO, statistics rows); the dQ kernel stages the item's Q and dO (for the
+// copy into TMEM) and has a two-stage ring of (K, V, key-bias row).  A work item streams every box of its tile,
 // so one K, V (resp. Q, dO) buffer per item costs one load wait per item.
 //
 // The merge weight of the Hann-weighted overlap average (arXiv 2604.16590,
@@ -357,9 +358,17 @@ __global__ void __launch_bounds__(kThreadsB, 1)
 }
 
 // =============================================================== dQ
+// Q and dOut of the item are copied once into TMEM (the A operands of S and
+// dP), so the score products read only K (resp. V) from shared memory: with
+// both operands there, an N = 128 K-step moves 8 KB against the SM's 128
+// bytes per clock and the products would wait on shared memory.  That leaves
+// no TMEM for separate dS buffers: each math warp packs its dS over the first
+// 16 of the 32 dP columns it read, and the next box's dP waits for this box's
+// dQ product.  S is released as soon as it is read, so the next box's S runs
+// during the exponentials and the dQ product.
 struct Q128 {
   static constexpr int kStages = 2;  // (K, V, key-bias row) ring
-  static constexpr int kQ = 0;
+  static constexpr int kQ = 0;       // Q, dOut of the item, copied into TMEM by the math warps
   static constexpr int kDO = kBox;
   static constexpr int kK = 2 * kBox;  // stage s: K at kK + s*2*kBox, V after it
   // Key-mask extension operands (as in the forward): A = 1 in K-column 0 of
@@ -368,13 +377,13 @@ struct Q128 {
   static constexpr int kOnes = kK + kStages * 2 * kBox;
   static constexpr int kBias = kOnes + 4096;
   static constexpr int kBar = kBias + kStages * 4096;
-  // qd_full, qd_empty, kv_full[S], kv_empty[S], s_full[2], s_empty[2], p_full[2], p_empty[2],
-  // acc_full, acc_empty, drain[2]   (s_*[0]: the S chain, s_*[1]: the dP chain; p_*[b]: dS buffer b)
-  static constexpr int kNumBars = 2 + 2 * kStages + 12;
+  // qd_full, qd_empty, qt_full, kv_full[S], kv_empty[S], s_full[2], s_empty, p_full, p_empty,
+  // acc_full, acc_empty, drain[2]   (s_full[0]: S, s_full[1]: dP)
+  static constexpr int kNumBars = 3 + 2 * kStages + 2 + 4 + 4;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kSmem = kMisc + 16 + 1024;
-  // TMEM: S 0, dP 128, dQ 256, dS buffer b (packed) 384 + 64 b
-  static constexpr uint32_t kColS = 0, kColDP = 128, kColDQ = 256, kColDS = 384;
+  // TMEM: S 0, dP (then dS packed) 128, dQ 256, Q (packed) 384, dOut (packed) 448
+  static constexpr uint32_t kColS = 0, kColDP = 128, kColDQ = 256, kColQ = 384, kColDO = 448;
 };
 
 template <typename OutT>
@@ -387,13 +396,14 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kBar);
   uint64_t* qd_full = bars;
   uint64_t* qd_empty = bars + 1;
-  uint64_t* kv_full = bars + 2;
+  uint64_t* qt_full = bars + 2;
+  uint64_t* kv_full = bars + 3;
   uint64_t* kv_empty = kv_full + C::kStages;
-  uint64_t* s_full = kv_empty + C::kStages;
+  uint64_t* s_full = kv_empty + C::kStages;  // [2]
   uint64_t* s_empty = s_full + 2;
-  uint64_t* p_full = s_empty + 2;  // [2]: one per dS buffer
-  uint64_t* p_empty = p_full + 2;  // [2]
-  uint64_t* acc_full = p_empty + 2;
+  uint64_t* p_full = s_empty + 1;
+  uint64_t* p_empty = p_full + 1;
+  uint64_t* acc_full = p_empty + 1;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* drain = acc_empty + 1;  // [2]: one per issuing thread
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
@@ -405,17 +415,17 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
     mbar_init(qd_full, 1);
-    mbar_init(qd_empty, 1);
+    mbar_init(qd_empty, kMathW);
+    mbar_init(qt_full, kMathW);
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(kv_full + s, 1);
       mbar_init(kv_empty + s, 1);
     }
-    for (int c = 0; c < 2; ++c) {
-      mbar_init(s_full + c, 1);
-      mbar_init(s_empty + c, kMathW);
-      mbar_init(p_full + c, kMathW);
-      mbar_init(p_empty + c, 1);
-    }
+    mbar_init(s_full, 1);
+    mbar_init(s_full + 1, 1);
+    mbar_init(s_empty, kMathW);
+    mbar_init(p_full, kMathW);
+    mbar_init(p_empty, 1);
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, kMathW);
     mbar_init(drain, 1);
@@ -453,6 +463,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       int o[3];
       block_origin(g, tbk, qb, o);
       if (lane == 0) {
+        // the staging buffer is free once the math warps copied the previous item's Q, dOut
         if ((ok = WAIT(qd_empty, (W & 1) ^ 1))) {
           mbar_arrive_expect_tx(qd_full, 4 * g.R * 128);
           qd_arm = 1;
@@ -507,7 +518,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     // ------------------------------------------------------------ issuer of S, dP
     if (lane == 0) {
       constexpr uint32_t idS = idesc_bf16(128, 128, 0);
-      const uint32_t sQ = smem_u32(smem + C::kQ), sDO = smem_u32(smem + C::kDO), sK = smem_u32(smem + C::kK);
+      const uint32_t sK = smem_u32(smem + C::kK);
       const uint64_t dOnes = noswz_desc(smem_u32(smem + C::kOnes), 2048, 128);
       const uint64_t dBias0 = noswz_desc(smem_u32(smem + C::kBias), 2048, 128);
       uint32_t G = 0, W = 0;
@@ -518,7 +529,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
         TileBlocks tbk;
         tile_blocks(g, tile, tbk);
         if (qb >= tbk.NB) continue;
-        if (!(ok = WAIT(qd_full, W & 1))) break;
+        if (!(ok = WAIT(qt_full, W & 1))) break;  // Q, dOut in TMEM
         const bool all_full = tile_all_full(g, tbk);
         BlockWalk bw;
         for (int j = 0; j < tbk.NB; ++j, ++G, bw.next(tbk)) {
@@ -531,19 +542,19 @@ __global__ void __launch_bounds__(kThreadsB, 1)
           const uint32_t sk = sK + st * 2 * kBox, sv = sk + kBox;
 #pragma unroll
           for (int ks = 0; ks < kD / 16; ++ks)
-            umma_bf16(tmem + C::kColS, sw128_desc(sQ + kmaj_off(ks), 16, 1024), sw128_desc(sk + kmaj_off(ks), 16, 1024),
-                      idS, ks > 0);
+            umma_bf16_ts(tmem + C::kColS, tmem + C::kColQ + ks * 8, sw128_desc(sk + kmaj_off(ks), 16, 1024), idS,
+                         ks > 0);
           // masked keys get -1e30, so P' = 0 there and dS = 0 follows
           if (masked) umma_bf16(tmem + C::kColS, dOnes, dmove(dBias0, st * 4096), idS, 1u);
           umma_commit(s_full);
-          if (G > 0 && !(ok = WAIT(s_empty + 1, (G - 1) & 1))) break;  // dP of box G-1 read
+          // the dP columns hold box G-1's packed dS until its dQ product is done
+          if (G > 0 && !(ok = WAIT(p_empty, (G - 1) & 1))) break;
           tc_fence_after();
 #pragma unroll
           for (int ks = 0; ks < kD / 16; ++ks)
-            umma_bf16(tmem + C::kColDP, sw128_desc(sDO + kmaj_off(ks), 16, 1024),
-                      sw128_desc(sv + kmaj_off(ks), 16, 1024), idS, ks > 0);
+            umma_bf16_ts(tmem + C::kColDP, tmem + C::kColDO + ks * 8, sw128_desc(sv + kmaj_off(ks), 16, 1024), idS,
+                         ks > 0);
           umma_commit(s_full + 1);
-          if (j == tbk.NB - 1) umma_commit(qd_empty);  // Q, dOut of this item no longer read
         }
         ++W;
       }
@@ -565,19 +576,17 @@ __global__ void __launch_bounds__(kThreadsB, 1)
         if (qb >= tbk.NB) continue;
         for (int j = 0; j < tbk.NB; ++j, ++G) {
           const uint32_t st = G % C::kStages;
-          // p_full(G) implies s_full(G): the score products of this stage are
-          // complete, so the kv_empty commit below covers every reader.  dS is
-          // double-buffered: box G uses buffer G & 1.
-          const uint32_t b = G & 1;
-          if (!(ok = WAIT(p_full + b, (G >> 1) & 1))) break;
+          // p_full(G) implies s_full[0,1](G): the score products of this stage
+          // are complete, so the kv_empty commit below covers every reader
+          if (!(ok = WAIT(p_full, G & 1))) break;
           if (j == 0 && !(ok = WAIT(acc_empty, (W & 1) ^ 1))) break;
           tc_fence_after();
           const uint32_t sk = sK + st * 2 * kBox;
 #pragma unroll
           for (int ks = 0; ks < 8; ++ks)
-            umma_bf16_ts(tmem + C::kColDQ, tmem + C::kColDS + 64 * b + ks * 8, sw128_desc(sk + ks * 2048, 16384, 1024),
+            umma_bf16_ts(tmem + C::kColDQ, tmem + C::kColDP + inplace_col(ks), sw128_desc(sk + ks * 2048, 16384, 1024),
                          idA, (j > 0 || ks > 0) ? 1u : 0u);
-          umma_commit(p_empty + b);
+          umma_commit(p_empty);
           umma_commit(kv_empty + st);
         }
         if (!ok) break;
@@ -594,8 +603,28 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     const int row = quad * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     const float sl2 = g.scale_log2;
+    // Q and dOut of a query box: shared memory -> TMEM (A operands of S, dP),
+    // elements [32 c4, 32 c4 + 32) of the row (16-byte units 4 (c4 & 1) .. +4
+    // of the 64-element half c4 >> 1)
+    auto copy_qdo = [&](uint32_t par) -> bool {
+      if (!WAIT(qd_full, par)) return false;
+      const uint32_t half = (uint32_t)(c4 >> 1) * 16384;
+      uint32_t r16[16];
+      ld_swizzled_row<4>(smem_u32(smem + C::kQ) + half, row, 4 * (c4 & 1), r16);
+      tmem_st16(tl + C::kColQ + 16 * c4, r16);
+      ld_swizzled_row<4>(smem_u32(smem + C::kDO) + half, row, 4 * (c4 & 1), r16);
+      tmem_st16(tl + C::kColDO + 16 * c4, r16);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(qd_empty);
+        mbar_arrive(qt_full);
+      }
+      return true;
+    };
     uint32_t G = 0, W = 0;
-    bool ok = true;
+    bool ok = true, staged = false;  // staged: this item's Q, dOut were copied during the previous item
     for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
       int bh, tile, qb;
       decode_item(g, w, bh, tile, qb);
@@ -605,6 +634,19 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       const int64_t qslot = tile_slot0(g, bh, tile) + qb * 128 + row;
       const float nL = a.lse2c[qslot];  // -lse' (-inf for padding rows)
       const float nD = a.dd[qslot];     // -D
+      if (!staged && !(ok = copy_qdo(W & 1))) break;
+      staged = false;
+      // the next item's Q, dOut are copied once this item's last score
+      // products are complete, so its first S and dP run during this item's
+      // epilogue
+      bool has_next = false;
+      for (int wn = w + gridDim.x; wn < a.items && !has_next; wn += gridDim.x) {
+        int bh2, tile2, qb2;
+        decode_item(g, wn, bh2, tile2, qb2);
+        TileBlocks t2;
+        tile_blocks(g, tile2, t2);
+        has_next = qb2 < t2.NB;
+      }
       for (int j = 0; j < tbk.NB && ok; ++j, ++G) {
         if (!(ok = WAIT(s_full, G & 1))) break;
         tc_fence_after();
@@ -619,19 +661,20 @@ __global__ void __launch_bounds__(kThreadsB, 1)
         tc_fence_after();
         tmem_ld32(tl + C::kColDP + c4 * 32, dv);
         tmem_wait_ld(dv);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(s_empty + 1);  // the next box's dP may overwrite this one
         q_ds(sv, dv, nD, pk);
-        // dS buffer G & 1 is free once the dQ products of box G-2 are done
-        const uint32_t b = G & 1;
-        if (G > 1 && !(ok = WAIT(p_empty + b, ((G >> 1) - 1) & 1))) break;
-        tc_fence_after();
-        tmem_st16(tl + C::kColDS + 64 * b + c4 * 16, pk);
+        // dS over the dP columns this warp read: dP of box G was computed after
+        // the dQ product of box G-1 had read its dS there
+        tmem_st16(tl + C::kColDP + c4 * 32, pk);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(p_full + b);
+        if (lane == 0) mbar_arrive(p_full);
+        // s_full[1] of the last box covers every score product of the item:
+        // Q, dOut in TMEM are no longer read
+        if (j == tbk.NB - 1 && has_next) {
+          if (!(ok = copy_qdo((W + 1) & 1))) break;
+          staged = true;
+        }
       }
       if (!ok) break;
       if (!(ok = WAIT(acc_full, W & 1))) break;
