@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "merge_common.cuh"
 #include "sm103_common.cuh"
 
 GATTN_DEFINE_STATUS(serve)
@@ -107,6 +108,103 @@ __global__ void __launch_bounds__(kThreads) serve_update_kernel(const ReqDesc* _
   }
 }
 
+// The same update, a warp per 32 consecutive rows (as the merge kernels of
+// merge.cu): each lane resolves its row's request, head and token and lists
+// the row's covering tiles with their slots and window weights; half-warps
+// then update the rows two at a time, lane f of a half holding columns
+// [4 f, 4 f + 4) (and [4 f + 64, 4 f + 68) at d = 128), so the per-tile rows
+// are read as contiguous runs and the geometry is resolved once per row
+// instead of once per 4 columns.  The window table is built from the first
+// request's geometry; a row whose request differs in core, halo, window or
+// tiled dimensions evaluates its window directly.  For up to kMaxCover
+// covering tiles per token (the host checks it).
+__global__ void __launch_bounds__(kThreads, 2) serve_update_warp_kernel(const ReqDesc* __restrict__ reqs,
+                                                                     const int64_t* __restrict__ counts, int d,
+                                                                     float c) {
+  __shared__ float win[kWinMax];
+  const int nreq = (int)counts[0];
+  if (nreq < 1) return;  // uniform over the grid: no request, no table
+  const int64_t rows = counts[2];
+  const Geom& g0 = reqs[0].g;
+  const WinTable tbl = build_win_table(g0, win);
+  const int lane = threadIdx.x & 31;
+  const int F4 = d / 4;  // 16 or 32
+  const int64_t stride = (int64_t)gridDim.x * (kThreads / 32) * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32; base < rows;
+       base += stride) {
+    const int64_t idx = base + lane;
+    int r = -1, n = 0;
+    int64_t local = 0;
+    int64_t slot[kMaxCover];
+    float w[kMaxCover];
+    float wsum = 0.f;
+    if (idx < rows) {
+      r = find_request(reqs, nreq, idx);
+      const Geom& g = reqs[r].g;
+      local = idx - reqs[r].tok0;  // head * N + token
+      if (local < 0 || local >= (int64_t)g.nh * g.N) {
+        set_status(kStatusBounds);
+        r = -1;
+      } else {
+        bool same = g.window == g0.window;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) same = same && g.c[a] == g0.c[a] && g.h[a] == g0.h[a] && g.tiled[a] == g0.tiled[a];
+        WinTable t = tbl;
+        t.direct = t.direct || !same;
+        n = token_covers(g, t, (int)(local / g.N), local % g.N, slot, w);
+#pragma unroll
+        for (int k = 0; k < kMaxCover; ++k)
+          if (k < n) wsum += w[k];
+      }
+    }
+    for (int q = 0; q < 16; ++q) {
+      const int owner = 2 * q + (lane >> 4);
+      const int ro = __shfl_sync(0xffffffffu, r, owner);
+      const int nc = __shfl_sync(0xffffffffu, n, owner);
+      const int64_t lo = __shfl_sync(0xffffffffu, local, owner);
+      const float inv = 1.f / __shfl_sync(0xffffffffu, wsum, owner);
+      const int ncmax = max(nc, __shfl_xor_sync(0xffffffffu, nc, 16));
+      const int f0 = lane & 15;
+      float4 acc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+      const float* ot = ro >= 0 ? reqs[ro].ot : nullptr;
+#pragma unroll
+      for (int k = 0; k < kMaxCover; ++k) {
+        if (k >= ncmax) break;
+        const int64_t sc = __shfl_sync(0xffffffffu, slot[k], owner);
+        const float wc = __shfl_sync(0xffffffffu, w[k], owner);
+        if (k < nc) {
+          const float4* row = reinterpret_cast<const float4*>(ot + sc * d);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int f = f0 + 16 * u;
+            if (f < F4) {
+              const float4 o = __ldg(row + f);
+              acc[u] = make_float4(fmaf(wc, o.x, acc[u].x), fmaf(wc, o.y, acc[u].y), fmaf(wc, o.z, acc[u].z),
+                                   fmaf(wc, o.w, acc[u].w));
+            }
+          }
+        }
+      }
+      if (ro < 0) continue;
+      const ReqDesc& rq = reqs[ro];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int f = f0 + 16 * u;
+        if (f >= F4) continue;
+        float4 att;
+        if (nc == 0)
+          att = load4<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(rq.out) + lo * d + 4 * f);
+        else
+          att = make_float4(acc[u].x * inv, acc[u].y * inv, acc[u].z * inv, acc[u].w * inv);
+        __nv_bfloat16* zp = rq.z + lo * d + 4 * f;
+        const float4 z = load4<__nv_bfloat16>(zp);
+        store4<__nv_bfloat16>(zp, make_float4(fmaf(c, att.x - z.x, z.x), fmaf(c, att.y - z.y, z.y),
+                                              fmaf(c, att.z - z.z, z.z), fmaf(c, att.w - z.w, z.w)));
+      }
+    }
+  }
+}
+
 using Clock = std::chrono::steady_clock;
 double seconds_since(Clock::time_point t0) {
   return std::chrono::duration<double>(Clock::now() - t0).count();
@@ -114,8 +212,12 @@ double seconds_since(Clock::time_point t0) {
 
 }  // namespace
 
-cudaError_t launch_serve_update(const ReqDesc* reqs, const int64_t* counts, int d, float c, cudaStream_t st) {
-  serve_update_kernel<<<num_sms() * 8, kThreads, 0, st>>>(reqs, counts, d, c);
+cudaError_t launch_serve_update(const ReqDesc* reqs, const int64_t* counts, int d, float c, bool warp_rows,
+                                cudaStream_t st) {
+  if (warp_rows)
+    serve_update_warp_kernel<<<num_sms() * 8, kThreads, 0, st>>>(reqs, counts, d, c);
+  else
+    serve_update_kernel<<<num_sms() * 8, kThreads, 0, st>>>(reqs, counts, d, c);
   return cudaGetLastError();
 }
 
@@ -155,6 +257,7 @@ struct gattn_server {
   ReqDesc* h_reqs = nullptr;  // pinned staging
   int64_t* h_counts = nullptr;
   cudaGraphExec_t graph = nullptr;
+  bool warp_rows = false;  // the update kernel's warp-per-32-rows form applies
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   size_t hbm_in_use = 0, hbm_peak = 0;
   int64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, iterations = 0;
@@ -227,6 +330,12 @@ gattn_status gattn_serve_create(const gattn_serve_cfg* cfg, gattn_stream_t strea
   if (!serve_geom(cfg, cfg->core[0], 1, &probe, true)) return GATTN_ERR_INVALID_ARG;
   gattn_server* s = new gattn_server();
   s->cfg = *cfg;
+  {
+    // covering tiles per token: temporal extents of 3 c + 2 h frames show the maximum
+    Geom span;
+    s->warp_rows = serve_geom(cfg, 3 * cfg->core[0] + 2 * cfg->halo[0], 1, &span, true) &&
+                   max_covers(span) <= kMaxCover;
+  }
   s->stream = reinterpret_cast<cudaStream_t>(stream);
   if (!s->stream) {
     // the legacy default stream cannot be captured into a graph: use an own
@@ -347,12 +456,12 @@ gattn_status gattn_serve_step(gattn_server* s, int32_t* n_active, int32_t* n_wai
         // kernels' attributes outside capture), then records the same two
         // launches into the graph that every later iteration replays
         if (launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, probe_rows(s), s->stream) != cudaSuccess ||
-            launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->stream) != cudaSuccess)
+            launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->warp_rows, s->stream) != cudaSuccess)
           return GATTN_ERR_CUDA;
         cudaGraph_t gr;
         if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GATTN_ERR_CUDA;
         cudaError_t e1 = launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, probe_rows(s), s->stream);
-        cudaError_t e2 = launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->stream);
+        cudaError_t e2 = launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->warp_rows, s->stream);
         cudaError_t e3 = cudaStreamEndCapture(s->stream, &gr);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return GATTN_ERR_CUDA;
         if (cudaGraphInstantiate(&s->graph, gr, 0) != cudaSuccess) return GATTN_ERR_CUDA;
@@ -362,7 +471,7 @@ gattn_status gattn_serve_step(gattn_server* s, int32_t* n_active, int32_t* n_wai
       }
     } else {
       if (launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, probe_rows(s), s->stream) != cudaSuccess ||
-          launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->stream) != cudaSuccess)
+          launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->warp_rows, s->stream) != cudaSuccess)
         return GATTN_ERR_CUDA;
     }
     cudaEventRecord(s->ev1, s->stream);
