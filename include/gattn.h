@@ -63,7 +63,7 @@ typedef enum {
   GATTN_ERR_OOM = 6,           /* serving: request does not fit the HBM budget */
   GATTN_ERR_BUSY = 7,          /* serving: no free slot */
   GATTN_ERR_DEVICE_BOUNDS = 8, /* debug bounds check tripped on the device */
-  GATTN_ERR_NOT_FOUND = 9      /* serving: unknown request id */
+  GATTN_ERR_NOT_FOUND = 9      /* serving: unknown request id, or a result already taken */
 } gattn_status;
 
 typedef enum { GATTN_BF16 = 0, GATTN_FP32 = 1 } gattn_dtype;
@@ -185,9 +185,13 @@ gattn_status gattn_bwd(const gattn_desc *desc, const void *q, const void *k, con
  * then runs one step of every active request in one persistent ragged
  * attention launch (per-request descriptors and item offsets) followed by one
  * merge-and-update launch, both captured in a CUDA graph that is replayed
- * every iteration; requests that finish are retired, their result copied to
- * host memory and their device memory released.  Results do not depend on
- * which other requests share an iteration (deterministic kernels).
+ * every iteration; requests that finish are retired: their scratch goes back
+ * to the server's memory pool and their final state stays in device memory
+ * until the client takes it (gattn_serve_poll with a buffer) or drops it
+ * (gattn_serve_release).  Unclaimed results count against hbm_budget; when
+ * the head of the queue does not fit, the oldest unclaimed results are moved
+ * to host memory first.  Results do not depend on which other requests share
+ * an iteration (deterministic kernels).
  * The server owns its device memory (within hbm_budget) and one internal
  * device buffer per slot of descriptors; calls on one server must not overlap.
  */
@@ -217,7 +221,7 @@ typedef struct {
 typedef struct {
   int64_t submitted, admitted, completed, rejected, active, waiting;
   int64_t iterations;       /* engine iterations that ran GPU work */
-  double p50_latency_s, p99_latency_s, mean_latency_s, max_latency_s;  /* submit -> result on host */
+  double p50_latency_s, p99_latency_s, mean_latency_s, max_latency_s;  /* submit -> final state complete */
   double token_steps;       /* sum over completed requests of nh * N * steps */
   double gpu_busy_s;        /* device time of the engine iterations */
   double wall_s;            /* host time from the first submit to the last completion */
@@ -239,10 +243,16 @@ gattn_status gattn_serve_submit(gattn_server *s, const gattn_request *req, uint6
  * retirement); synchronises the server's stream.  *n_active receives the
  * number of active requests after the iteration, *n_waiting the queue length. */
 gattn_status gattn_serve_step(gattn_server *s, int32_t *n_active, int32_t *n_waiting);
-/* *done = 1 once the request finished; then copies its final state into
- * result_host ([nh, N, d] BF16, may be NULL) and reports its latency.
- * GATTN_ERR_NOT_FOUND for an unknown id. */
+/* *done = 1 once the request finished, and then *latency_s its latency.  With
+ * result_host (host or device memory, [nh, N, d] BF16; NULL: only poll) the
+ * final state is copied there and released: a result can be taken once
+ * (GATTN_ERR_NOT_FOUND when it was already taken or released, as for an
+ * unknown id). */
 gattn_status gattn_serve_poll(gattn_server *s, uint64_t id, int32_t *done, double *latency_s, void *result_host);
+/* Drops the final state of a finished request without copying it (its device
+ * memory returns to the pool).  GATTN_ERR_INVALID_ARG if the request has not
+ * finished, GATTN_ERR_NOT_FOUND for an unknown id. */
+gattn_status gattn_serve_release(gattn_server *s, uint64_t id);
 gattn_status gattn_serve_stats(gattn_server *s, gattn_serve_stats_t *out);
 void gattn_serve_destroy(gattn_server *s);
 

@@ -239,7 +239,9 @@ struct ServeRequest {
   int steps_done = 0;
   double t_submit = 0.0;
   double latency = -1.0;
-  std::vector<uint16_t> result;
+  size_t held = 0;                // bytes of this request counted in hbm_in_use
+  bool taken = false;             // the result was fetched or released
+  std::vector<uint16_t> result;   // the result, once spilled to host memory
 };
 
 struct gattn_server {
@@ -251,6 +253,8 @@ struct gattn_server {
   uint64_t next_id = 1;
   std::deque<ServeRequest*> waiting;
   std::vector<ServeRequest*> active;
+  std::deque<ServeRequest*> finished;  // retired, result possibly still in device memory
+  cudaMemPool_t pool = nullptr;        // request memory (kept by the pool between requests)
   std::unordered_map<uint64_t, ServeRequest*> all;
   ReqDesc* d_reqs = nullptr;
   int64_t* d_counts = nullptr;
@@ -305,14 +309,35 @@ static size_t request_bytes(const Geom& g) {
   return align_up(nd * 2) + align_up(nd * 2) + align_up(slots * g.d * 4);
 }
 
+// Device memory of a request goes back to the server's pool (stream-ordered,
+// after the request's last use on the server's stream).
+static void free_dev(gattn_server* s, void*& p) {
+  if (p) cudaFreeAsync(p, s->stream);
+  p = nullptr;
+}
+
 static void release(gattn_server* s, ServeRequest* r) {
-  if (r->z) cudaFree(r->z);
-  if (r->out) cudaFree(r->out);
-  if (r->ot) cudaFree(r->ot);
+  void* z = r->z;
+  free_dev(s, z);
+  free_dev(s, r->out);
+  void* ot = r->ot;
+  free_dev(s, ot);
   r->z = nullptr;
-  r->out = nullptr;
   r->ot = nullptr;
-  s->hbm_in_use -= r->bytes;
+  s->hbm_in_use -= r->held;
+  r->held = 0;
+}
+
+// Moves the result of a retired request from device to host memory (when
+// waiting requests need the budget and its client has not fetched it yet).
+static bool spill(gattn_server* s, ServeRequest* r) {
+  const size_t nd = (size_t)r->g.nh * r->g.N * r->g.d;
+  r->result.resize(nd);
+  if (cudaMemcpyAsync(r->result.data(), r->z, nd * 2, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return false;
+  release(s, r);
+  return true;
 }
 
 extern "C" {
@@ -347,7 +372,17 @@ gattn_status gattn_serve_create(const gattn_serve_cfg* cfg, gattn_stream_t strea
     }
     s->own_stream = true;
   }
-  bool ok = cudaMalloc(&s->d_reqs, sizeof(ReqDesc) * cfg->max_active) == cudaSuccess &&
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  const uint64_t keep_all = ~0ull;  // the pool keeps freed request memory for the next admissions
+  bool ok = cudaMemPoolCreate(&s->pool, &props) == cudaSuccess &&
+            cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, (void*)&keep_all) == cudaSuccess &&
+            cudaMalloc(&s->d_reqs, sizeof(ReqDesc) * cfg->max_active) == cudaSuccess &&
             cudaMalloc(&s->d_counts, 4 * sizeof(int64_t)) == cudaSuccess &&
             cudaMallocHost(&s->h_reqs, sizeof(ReqDesc) * cfg->max_active) == cudaSuccess &&
             cudaMallocHost(&s->h_counts, 4 * sizeof(int64_t)) == cudaSuccess &&
@@ -400,23 +435,36 @@ gattn_status gattn_serve_step(gattn_server* s, int32_t* n_active, int32_t* n_wai
   // ---- admission: arrival order, slot limit, HBM budget (head of line waits)
   while (!s->waiting.empty() && (int)s->active.size() < s->cfg.max_active) {
     ServeRequest* r = s->waiting.front();
+    // results that their clients have not fetched yet move to host memory
+    // (oldest first) while the head of the queue does not fit the budget
+    while (s->hbm_in_use + r->bytes > s->cfg.hbm_budget && !s->finished.empty()) {
+      ServeRequest* f = s->finished.front();
+      s->finished.pop_front();
+      if (f->z && !spill(s, f)) return GATTN_ERR_CUDA;
+    }
     if (s->hbm_in_use + r->bytes > s->cfg.hbm_budget) break;
     const Geom& g = r->g;
     const size_t nd = (size_t)g.nh * g.N * g.d;
     const size_t slots = (size_t)g.nh * g.ntiles * g.per_tile;
-    if (cudaMalloc(&r->z, nd * 2) != cudaSuccess || cudaMalloc(&r->out, nd * 2) != cudaSuccess ||
-        cudaMalloc(&r->ot, slots * g.d * 4) != cudaSuccess) {
-      s->hbm_in_use += r->bytes;
+    r->held = r->bytes;
+    s->hbm_in_use += r->bytes;
+    void *z = nullptr, *ot = nullptr;
+    if (cudaMallocFromPoolAsync(&z, nd * 2, s->pool, s->stream) != cudaSuccess ||
+        cudaMallocFromPoolAsync(&r->out, nd * 2, s->pool, s->stream) != cudaSuccess ||
+        cudaMallocFromPoolAsync(&ot, slots * g.d * 4, s->pool, s->stream) != cudaSuccess) {
+      r->z = static_cast<__nv_bfloat16*>(z);
+      r->ot = static_cast<float*>(ot);
       release(s, r);
       cudaGetLastError();
       break;  // the device is fuller than the budget says: retry next iteration
     }
+    r->z = static_cast<__nv_bfloat16*>(z);
+    r->ot = static_cast<float*>(ot);
     const void* src = r->z0_dev ? r->z0_dev : (const void*)r->z0_host.data();
     if (cudaMemcpyAsync(r->z, src, nd * 2, cudaMemcpyDefault, s->stream) != cudaSuccess) return GATTN_ERR_CUDA;
     if (!make_tmap_5d(&r->tmap, r->z, g.d, g.G[2], g.G[1], g.G[0], g.nh, g.bx, g.by, g.bt)) return GATTN_ERR_CUDA;
     s->waiting.pop_front();
     s->active.push_back(r);
-    s->hbm_in_use += r->bytes;
     s->hbm_peak = std::max(s->hbm_peak, s->hbm_in_use);
     ++s->admitted;
   }
@@ -488,10 +536,16 @@ gattn_status gattn_serve_step(gattn_server* s, int32_t* n_active, int32_t* n_wai
         still.push_back(r);
         continue;
       }
-      const size_t nd = (size_t)r->g.nh * r->g.N * r->g.d;
-      r->result.resize(nd);
-      if (cudaMemcpy(r->result.data(), r->z, nd * 2, cudaMemcpyDeviceToHost) != cudaSuccess) return GATTN_ERR_CUDA;
-      release(s, r);
+      // the final state stays in device memory until its client fetches it
+      // (gattn_serve_poll) or releases it; the scratch goes back to the pool
+      free_dev(s, r->out);
+      void* ot = r->ot;
+      free_dev(s, ot);
+      r->ot = nullptr;
+      const size_t zb = align_up((size_t)r->g.nh * r->g.N * r->g.d * 2);
+      s->hbm_in_use -= r->held - zb;
+      r->held = zb;
+      s->finished.push_back(r);
       r->z0_host.clear();
       r->z0_host.shrink_to_fit();
       const double now = seconds_since(s->t0);
@@ -517,8 +571,35 @@ gattn_status gattn_serve_poll(gattn_server* s, uint64_t id, int32_t* done, doubl
   *done = r->latency >= 0.0 ? 1 : 0;
   if (*done) {
     if (latency_s) *latency_s = r->latency;
-    if (result_host) memcpy(result_host, r->result.data(), r->result.size() * 2);
+    if (result_host) {
+      if (r->taken) return GATTN_ERR_NOT_FOUND;
+      const size_t nd = (size_t)r->g.nh * r->g.N * r->g.d;
+      if (r->z) {
+        if (cudaMemcpyAsync(result_host, r->z, nd * 2, cudaMemcpyDefault, s->stream) != cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess)
+          return GATTN_ERR_CUDA;
+        release(s, r);
+      } else {
+        memcpy(result_host, r->result.data(), nd * 2);
+        r->result.clear();
+        r->result.shrink_to_fit();
+      }
+      r->taken = true;
+    }
   }
+  return GATTN_OK;
+}
+
+gattn_status gattn_serve_release(gattn_server* s, uint64_t id) {
+  if (!s) return GATTN_ERR_INVALID_ARG;
+  auto it = s->all.find(id);
+  if (it == s->all.end()) return GATTN_ERR_NOT_FOUND;
+  ServeRequest* r = it->second;
+  if (r->latency < 0.0) return GATTN_ERR_INVALID_ARG;  // not finished (or rejected)
+  if (r->z) release(s, r);
+  r->result.clear();
+  r->result.shrink_to_fit();
+  r->taken = true;
   return GATTN_OK;
 }
 
@@ -560,9 +641,11 @@ void gattn_serve_destroy(gattn_server* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
   for (auto& kv : s->all) {
-    if (kv.second->z) release(s, kv.second);
+    release(s, kv.second);
     delete kv.second;
   }
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->pool) cudaMemPoolDestroy(s->pool);
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->d_reqs) cudaFree(s->d_reqs);
   if (s->d_counts) cudaFree(s->d_counts);

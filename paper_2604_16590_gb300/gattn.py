@@ -174,6 +174,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), P],
             ctypes.c_int,
         ),
+        "gattn_serve_release": ([P, ctypes.c_uint64], ctypes.c_int),
         "gattn_serve_stats": ([P, ctypes.POINTER(gattn_serve_stats_t)], ctypes.c_int),
         "gattn_serve_destroy": ([P], None),
         "gattn_linear_workspace_bytes": ([ctypes.POINTER(gattn_linear_desc)], S),
@@ -449,6 +450,10 @@ def gattn_serve_poll(server, rid, result_host=None):
     return st, bool(done.value), lat.value
 
 
+def gattn_serve_release(server, rid) -> int:
+    return load_library().gattn_serve_release(server, ctypes.c_uint64(rid))
+
+
 def gattn_serve_stats(server) -> gattn_serve_stats_t:
     out = gattn_serve_stats_t()
     check(load_library().gattn_serve_stats(server, ctypes.byref(out)), "gattn_serve_stats")
@@ -501,13 +506,24 @@ class Server:
         check(st, "gattn_serve_step")
         return a, w
 
-    def result(self, rid, shape):
-        out = torch.empty(shape, dtype=torch.bfloat16)
+    def result(self, rid, shape=None, out=None):
+        """(final state, latency) of a finished request, else (None, None).
+        The state is copied into `out` (a BF16 tensor on the host or the
+        device) or a new host tensor of `shape`; a result can be taken once."""
+        st, done, _ = gattn_serve_poll(self.h, rid, None)
+        check(st, "gattn_serve_poll")
+        if not done:
+            return None, None
+        if out is None:
+            out = torch.empty(shape, dtype=torch.bfloat16)
         st, done, lat = gattn_serve_poll(self.h, rid, out)
         check(st, "gattn_serve_poll")
-        if done:
-            self._keep.pop(rid, None)
-        return (out, lat) if done else (None, None)
+        self._keep.pop(rid, None)
+        return out, lat
+
+    def release(self, rid):
+        """Drops the final state of a finished request without copying it."""
+        check(gattn_serve_release(self.h, rid), "gattn_serve_release")
 
     def done(self, rid) -> bool:
         st, done, _ = gattn_serve_poll(self.h, rid, None)

@@ -4,7 +4,9 @@ Each request runs `steps` denoising steps z <- z + c (GPA(z) - z) with its
 state kept on the device; engine iterations batch all active requests into one
 ragged attention launch and one merge-update launch (CUDA graph).  Checked:
 one step against the FP64 oracle, bitwise identity of a request's result alone
-and in a mix, admission under the HBM budget and the slot limit, statistics.
+and in a mix, admission under the HBM budget and the slot limit (unclaimed
+results moved to host memory to make room), results taken once or released,
+statistics.
 """
 import numpy as np
 import pytest
@@ -139,3 +141,39 @@ def test_five_steps_replay_through_the_oracle():
     for _ in range(5):
         z = torch.from_numpy(step(z)).to(torch.bfloat16).double().numpy()
     assert_close("serve/trajectory5", states[5].double().numpy()[None], z[None], 5 * 2e-2, 5 * 3e-3)
+
+
+def test_results_are_taken_once_and_release_frees_memory():
+    specs = [ServeRequestSpec(0.0, 2, 2, 600 + i) for i in range(3)]
+    states = [request_state(sp, Y, X, D) for sp in specs]
+    with gattn.Server(_cfg(steps=2)) as srv:
+        ids = [srv.submit(z) for z in states]
+        with pytest.raises(gattn.GattnError) as e:
+            srv.release(ids[0])  # not finished yet
+        assert e.value.status == 1
+        while not all(srv.done(r) for r in ids):
+            srv.step()
+        per = gattn.gattn_serve_request_bytes(srv.cfg, 2, 2)
+        held = srv.stats().hbm_in_use
+        assert 0 < held < 3 * per  # the final states only: scratch went back to the pool
+        # taken into a device tensor, then into a host tensor: the same bytes
+        dev = torch.empty(states[0].shape, dtype=torch.bfloat16, device="cuda")
+        a, lat = srv.result(ids[0], out=dev)
+        assert lat > 0
+        b, _ = srv.result(ids[1], states[1].shape)
+        with pytest.raises(gattn.GattnError) as e:
+            srv.result(ids[0], states[0].shape)  # already taken
+        assert e.value.status == 9
+        srv.release(ids[2])
+        assert srv.stats().hbm_in_use == 0
+        with pytest.raises(gattn.GattnError) as e:
+            srv.release(12345)
+        assert e.value.status == 9
+    # the same requests served one at a time give the same final states
+    for z0, got in ((states[0], a.cpu()), (states[1], b)):
+        with gattn.Server(_cfg(steps=2)) as srv:
+            rid = srv.submit(z0)
+            while not srv.done(rid):
+                srv.step()
+            ref, _ = srv.result(rid, z0.shape)
+        assert torch.equal(ref, got)
