@@ -27,6 +27,10 @@ FWD_CASES = [
     ("d128_temporal", 1, 2, 128, (16, 8, 8), (8, 8, 8), (2, 0, 0)),
     ("long_tile_ring_wrap", 1, 1, 64, (8, 32, 32), (8, 16, 16), (0, 4, 4)),
     ("d128_s_spec", 1, 1, 128, (1, 48, 40), (1, 16, 16), (0, 4, 4)),
+    # d = 128 with ragged tiles in all three dimensions (masked key boxes, padding rows)
+    ("d128_ragged_all_dims", 2, 3, 128, (3, 10, 13), (2, 4, 5), (1, 2, 2)),
+    # d = 128, several boxes per tile in every dimension and a long item (two K/V ring wraps)
+    ("d128_multi_box", 1, 2, 128, (6, 24, 24), (3, 12, 12), (1, 2, 2)),
     # one 1x8x48 tile = three 1x8x16 boxes: the second box of the last query pair is empty
     ("odd_box_count", 1, 2, 64, (1, 8, 48), (1, 8, 48), (0, 0, 0)),
 ]

@@ -51,6 +51,25 @@ def test_one_step_matches_oracle():
     assert_close("serve/z1", z1.double().numpy()[None], ref[None], 2e-2, 3e-3)
 
 
+def test_one_step_matches_oracle_d128_mixed_requests():
+    """d = 128 runs the ragged one-box kernel (sm103_fwd.cu): two requests of
+    different lengths and head counts in one iteration, each checked against
+    the oracle."""
+    specs = [ServeRequestSpec(0.0, 3, 2, 81), ServeRequestSpec(0.0, 1, 1, 82)]
+    states = [request_state(sp, Y, X, 128) for sp in specs]
+    with gattn.Server(_cfg(d=128, steps=1)) as srv:
+        ids = [srv.submit(z) for z in states]
+        while not all(srv.done(r) for r in ids):
+            srv.step()
+        outs = [srv.result(r, z.shape)[0] for r, z in zip(ids, states)]
+    for sp, z0, z1 in zip(specs, states, outs):
+        geo = oracle.Geometry(1, sp.nh, 128, sp.T, Y, X, CORE, HALO)
+        z = z0.double().numpy()[None]
+        att = oracle.forward(geo, z, z, z)[0]
+        ref = z[0] + 0.5 * (att - z[0])
+        assert_close(f"serve128/T{sp.T}", z1.double().numpy()[None], ref[None], 2e-2, 3e-3)
+
+
 @pytest.mark.parametrize("use_graph", [True, False], ids=["graph", "direct"])
 def test_result_is_identical_alone_and_in_a_mix(use_graph):
     a = ServeRequestSpec(0.0, 3, 2, 101)
