@@ -676,35 +676,89 @@ def run_gpa(w, steps, warmup, dev, rank, world, peaks, cpu=True, e2e_steps=1, fp
     hbm = {"algorithmic_bytes_per_step": alg_bytes, "gbs": alg_bytes / (ms * 1e-3) / 1e9,
            "frac_of_hbm": alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, "peak_gbs": hbm_peak, "peak_source": peak_src}
 
-    # ---- e2e through the public API with host buffers
+    # ---- e2e through the public API with host buffers: every step copies its
+    # inputs (Q, K, V, dOut) from pinned host memory and its results (Out, dQ,
+    # dK, dV) back, on a copy-in and a copy-out stream.  With two device buffer
+    # sets, the inputs of step i+1 load while step i computes, and Out of a
+    # step leaves while its backward runs: the timed region (its first
+    # copy-in to its last copy-out) holds every copy of every step.
     e2e = None
     if e2e_steps > 0:
         host_in = [torch.empty(w.shape, dtype=torch.bfloat16, pin_memory=True) for _ in range(4)]
         for h, t in zip(host_in, (q, k, v, go)):
             h.copy_(t)
         host_out = [torch.empty(w.shape, dtype=torch.bfloat16, pin_memory=True) for _ in range(4)]
+        nset = 2 if e2e_steps > 1 else 1
+        sets_in = [(q, k, v, go)] + [tuple(torch.empty_like(q) for _ in range(4)) for _ in range(nset - 1)]
+        sets_out = [(out, dq, dk, dv)] + [tuple(torch.empty_like(q) for _ in range(4)) for _ in range(nset - 1)]
+        s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
-        def e2e_step():
-            for d_, h_ in zip((q, k, v, go), host_in):
-                d_.copy_(h_, non_blocking=True)
-            step()
-            for h_, d_ in zip(host_out, (out, dq, dk, dv)):
-                h_.copy_(d_, non_blocking=True)
+        def e2e_run(n, start_ev=None):
+            loaded = [torch.cuda.Event() for _ in range(nset)]
+            inputs_free = [None] * nset   # backward of the set's previous step done
+            outputs_out = [None] * nset   # outputs of the set's previous step copied out
 
-        e2e_step()
+            def load(b, after=None):
+                if after is not None:
+                    s_in.wait_event(after)
+                if inputs_free[b] is not None:
+                    s_in.wait_event(inputs_free[b])
+                with torch.cuda.stream(s_in):
+                    for d_, h_ in zip(sets_in[b], host_in):
+                        d_.copy_(h_, non_blocking=True)
+                loaded[b].record(s_in)
+
+            load(0, start_ev)
+            last = None
+            for i in range(n):
+                b = i % nset
+                if nset > 1 and i + 1 < n:
+                    load((i + 1) % nset)
+                elif nset == 1 and i > 0:
+                    load(0)
+                stream.wait_event(loaded[b])
+                if outputs_out[b] is not None:
+                    stream.wait_event(outputs_out[b])
+                qq, kk, vv, gg = sets_in[b]
+                o, a, bb, c = sets_out[b]
+                gattn.check(gattn.gattn_fwd(desc, qq, kk, vv, o, saved, stream=stream), "gattn_fwd")
+                ev_f = torch.cuda.Event()
+                ev_f.record(stream)
+                gattn.check(gattn.gattn_bwd(desc, qq, kk, vv, o, gg, saved, a, bb, c, ws, stream=stream),
+                            "gattn_bwd")
+                ev_b = torch.cuda.Event()
+                ev_b.record(stream)
+                inputs_free[b] = ev_b
+                s_out.wait_event(ev_f)
+                with torch.cuda.stream(s_out):
+                    host_out[0].copy_(o, non_blocking=True)
+                s_out.wait_event(ev_b)
+                with torch.cuda.stream(s_out):
+                    for h_, d_ in zip(host_out[1:], (a, bb, c)):
+                        h_.copy_(d_, non_blocking=True)
+                last = torch.cuda.Event()
+                last.record(s_out)
+                outputs_out[b] = last
+            stream.wait_event(last)
+
+        e2e_run(1)
         torch.cuda.synchronize()
         barrier()
         e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e2.record(stream)
-        for _ in range(e2e_steps):
-            e2e_step()
+        e2e_run(e2e_steps, e2)
         e3.record(stream)
         torch.cuda.synchronize()
+        st = gattn.gattn_stream_status(stream)
+        if st != 0:
+            raise RuntimeError(f"{w.name}: device status after e2e steps: {gattn.STATUS.get(st, st)}")
         e2e_ms = replicas.max_over_ranks(e2.elapsed_time(e3) / e2e_steps, device=dev)
         bytes_io = 4 * q.numel() * q.element_size()
         e2e = {"value": w.B * w.N * world / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
-               "steps": e2e_steps, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io}
-        del host_in, host_out
+               "steps": e2e_steps, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
+               "overlap": "copies on two streams beside the compute stream, two device buffer sets"
+                          if nset > 1 else "copies on two streams, one buffer set (one step)"}
+        del host_in, host_out, sets_in, sets_out
 
     # ---- the plain FP32 form on the same values
     fp32 = None
@@ -925,7 +979,7 @@ def main():
 
     # ---------------------------------------------------------------- the headline workload
     head = run_gpa(w, args.steps, args.warmup, dev, rank, world, peaks, cpu=not args.no_cpu,
-                   e2e_steps=max(1, min(args.steps, 3)), fp32_steps=args.fp32_steps, clocks=True, barrier=barrier)
+                   e2e_steps=max(1, min(args.steps, 5)), fp32_steps=args.fp32_steps, clocks=True, barrier=barrier)
 
     if rank == 0:
         line = {

@@ -47,6 +47,7 @@ def test_steps_match_oracle(case, attn):
     zr = z.double().numpy()
     tol = (2e-2, 3e-3) if attn == "bf16" else (4e-5, 4e-5)
     g = torch.Generator().manual_seed(7)
+    worst = (0.0, 0.0)
     for i in range(5):
         eps = torch.randn(z.shape, generator=g)
         before = sampler.z.double().cpu().numpy()
@@ -56,11 +57,14 @@ def test_steps_match_oracle(case, attn):
         # one step from the GPU's own state (no drift between the trajectories)
         ref, _ = od.step(geo, before, y.double().numpy(), mask.double().numpy(), eps.double().numpy(),
                          sig[i], sig[i + 1], 0.8, attn_dtype="bf16" if attn == "bf16" else "fp64")
-        assert_close(f"{name}/{attn}/step{i}", got - before, ref - before, *tol)
+        mx, rms = assert_close(f"{name}/{attn}/step{i}", got - before, ref - before, *tol)
+        worst = (max(worst[0], mx), max(worst[1], rms))
         zr, _ = od.step(geo, zr, y.double().numpy(), mask.double().numpy(), eps.double().numpy(),
                         sig[i], sig[i + 1], 0.8, attn_dtype="bf16" if attn == "bf16" else "fp64")
     # the five-step trajectory stays close to the oracle's own trajectory
     traj = np.linalg.norm(sampler.z.double().cpu().numpy() - zr) / np.linalg.norm(zr - z.double().numpy())
+    # the measured margins (shown with pytest -s)
+    print(f"{name}/{attn}: worst step max-rel {worst[0]:.2e} rms-rel {worst[1]:.2e}, trajectory {traj:.2e}")
     assert traj <= (2e-2 if attn == "bf16" else 4e-5), traj
 
 
