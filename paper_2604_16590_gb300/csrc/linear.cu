@@ -510,10 +510,10 @@ __global__ void __launch_bounds__(kThreadsQ, 3) la_query_kernel(const __grid_con
 // core's BF16 operands stays below 2^-16; phi(k) and dS in the key pass are
 // split the same way.
 
-constexpr int kThreadsB = 192;               // producer, issuer, 4 math warps
+constexpr int kThreadsB = 320;               // producer, issuer, 8 math warps (two per TMEM lane quadrant)
 constexpr int kBQStage = 4 * kTileBytes;     // q -> phi hi, g -> g/den hi, phi lo, g/den lo
 constexpr int kBQStages = 2;
-constexpr int kBQBase = 16384 + 1024;        // S^T hi, lo (8 KB each), then z and padding
+constexpr int kBQBase = 16384 + 3072;        // S^T hi, lo (8 KB each), z, the row-sum exchange, padding
 constexpr int kBQSmem = kBQBase + kBQStages * kBQStage + 1024 + 256;
 constexpr int kBKStage = 3 * kTileBytes;     // k -> phi hi, v, phi lo
 constexpr int kBKStages = 2;
@@ -522,8 +522,9 @@ constexpr int kBKSmem = kBKBase + kBKStages * kBKStage + 1024 + 256;
 
 // 64 x 64 BF16 matrices (rows of 128 bytes) from global memory into 128-byte-
 // swizzled shared memory, n of them; every math thread (tid 0..127) takes part
-__device__ __forceinline__ void load_mats(int tid, int n, const __nv_bfloat16* const* src, uint8_t* const* dst) {
-  for (int i = tid; i < n * 64 * 8; i += 128) {
+__device__ __forceinline__ void load_mats(int tid, int nthr, int n, const __nv_bfloat16* const* src,
+                                          uint8_t* const* dst) {
+  for (int i = tid; i < n * 64 * 8; i += nthr) {
     const int m = i >> 9, row = (i >> 3) & 63, c = i & 7;
     *reinterpret_cast<uint4*>(dst[m] + swz(row, c)) = *reinterpret_cast<const uint4*>(src[m] + row * kD + c * 8);
   }
@@ -546,7 +547,11 @@ struct BQArgs {
 //           tokens (both operands MN-major; chains hi.hi, hi.lo, lo.hi)
 //   math:   per row, phi(q) and den in FP32, phi's parts over the q tile and a
 //           side buffer; with U: go, dq (stored), dz; g / den's parts over the
-//           g tile and a side buffer
+//           g tile and a side buffer.  Two warps per TMEM lane quadrant, each
+//           taking 32 of a row's 64 columns (the work per row is long and
+//           latency-bound: one warp per sub-partition left it idle most of the
+//           time); the row's two sums (den, phi(q) . U) are exchanged through
+//           shared memory and added in a fixed order.
 // At the end the CTA writes its dS and dz partials.
 __global__ void __launch_bounds__(kThreadsB, 1) la_bwd_query_kernel(const __grid_constant__ CUtensorMap tq,
                                                                     const __grid_constant__ CUtensorMap tg,
@@ -556,6 +561,8 @@ __global__ void __launch_bounds__(kThreadsB, 1) la_bwd_query_kernel(const __grid
   uint8_t* sHi = smem;
   uint8_t* sLo = smem + 8192;
   float* zs = reinterpret_cast<float*>(smem + 16384);
+  float* xden = reinterpret_cast<float*>(smem + 16384 + 256);  // [2 halves][128 rows]
+  float* xgo = xden + 256;                                     // [2 halves][128 rows]
   auto stq = [&](int st) { return smem + kBQBase + st * kBQStage; };  // q, then phi hi
   auto stg = [&](int st) { return stq(st) + kTileBytes; };              // g, then g/den hi
   auto stpl = [&](int st) { return stq(st) + 2 * kTileBytes; };         // phi lo
@@ -577,10 +584,10 @@ __global__ void __launch_bounds__(kThreadsB, 1) la_bwd_query_kernel(const __grid
       mbar_init(full + i, 1);
       mbar_init(empty + i, 1);
       mbar_init(ufull + i, 1);
-      mbar_init(ufree + i, 4);
-      mbar_init(dsready + i, 4);
+      mbar_init(ufree + i, 8);
+      mbar_init(dsready + i, 8);
     }
-    mbar_init(sready, 4);
+    mbar_init(sready, 8);
     mbar_init(done, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -651,89 +658,94 @@ __global__ void __launch_bounds__(kThreadsB, 1) la_bwd_query_kernel(const __grid
   } else {
     // ------------------------------------------------------------------ math warps
     const int quad = warp & 3;
+    const int h = (warp - 2) >> 2;   // columns [32 h, 32 h + 32) of the row: chunks 4 h .. 4 h + 3
     const int r = quad * 32 + lane;  // tile row = TMEM lane
     const int tid = threadIdx.x - 64;
+    const int pair_bar = 2 + quad;   // named barrier of the two warps of this lane quadrant
     {
       const __nv_bfloat16* src[2] = {a.sth + (size_t)bh * kD * kD, a.stl + (size_t)bh * kD * kD};
       uint8_t* dst[2] = {sHi, sLo};
-      load_mats(tid, 2, src, dst);
+      load_mats(tid, 256, 2, src, dst);
       if (tid < kD) zs[tid] = a.zt[(size_t)bh * kD + tid];
       fence_proxy_async_smem();
-      asm volatile("bar.sync 1, 128;" ::: "memory");  // z visible to all four math warps
+      asm volatile("bar.sync 1, 256;" ::: "memory");  // z visible to all eight math warps
       __syncwarp();
       if (lane == 0) mbar_arrive(sready);
     }
-    float dz[kD];
+    float dz[kD / 2];
 #pragma unroll
-    for (int i = 0; i < kD; ++i) dz[i] = 0.f;
+    for (int i = 0; i < kD / 2; ++i) dz[i] = 0.f;
     bool ok = true;
     for (int t = t0, G = 0; t < t1; ++t, ++G) {
       const int st = G % kBQStages, n = G / kBQStages, b = G & 1;
       const bool valid = (int64_t)t * kTile + r < a.N;
       if (!(ok = LWAIT(full + st, n & 1))) break;
-      // phi(q) in FP32, den, and phi's parts (hi over q, lo in its own tile)
-      float den = 0.f;
+      // phi(q) in FP32, this half's part of den, and phi's parts (hi over q, lo in its own tile)
+      float dpart = 0.f;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 4 * h; c < 4 * h + 4; ++c) {
         uint4* pq = reinterpret_cast<uint4*>(stq(st) + swz(r, c));
         float f[8];
         phi8(*pq, valid, f);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) den = fmaf(f[e], zs[c * 8 + e], den);
+        for (int e = 0; e < 8; ++e) dpart = fmaf(f[e], zs[c * 8 + e], dpart);
         uint4 hi, lo;
         split8(f, hi, lo);
         *pq = hi;
         *reinterpret_cast<uint4*>(stpl(st) + swz(r, c)) = lo;
       }
+      xden[h * 128 + r] = dpart;
+      asm volatile("bar.sync %0, 64;" ::"r"(pair_bar) : "memory");
+      const float den = xden[r] + xden[128 + r];
       const float inv = valid ? 1.f / den : 0.f;
-      // U row (the U product is done: the g tile may be overwritten below)
+      // this half of the U row (the U product is done: the g tile may be overwritten below)
       if (!(ok = LWAIT(ufull + b, n & 1))) break;
       tc_fence_after();
-      uint32_t u0[32], u1[32];
-      const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + 64 * b;
-      tmem_ld32(tl, u0);
-      tmem_ld32(tl + 32, u1);
-      tmem_wait_ld(u0);
-      tmem_wait_ld(u1);
+      uint32_t u[32];
+      const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + 64 * b + 32 * h;
+      tmem_ld32(tl, u);
+      tmem_wait_ld(u);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(ufree + b);
-      float go = 0.f;
+      float gpart = 0.f;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < 4; ++c) {
         float f[8];
-        join8(*reinterpret_cast<const uint4*>(stq(st) + swz(r, c)), *reinterpret_cast<const uint4*>(stpl(st) + swz(r, c)),
-              f);
-        const uint32_t* u = c < 4 ? u0 + 8 * c : u1 + 8 * (c - 4);
+        join8(*reinterpret_cast<const uint4*>(stq(st) + swz(r, 4 * h + c)),
+              *reinterpret_cast<const uint4*>(stpl(st) + swz(r, 4 * h + c)), f);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) go = fmaf(f[e], __uint_as_float(u[e]), go);
+        for (int e = 0; e < 8; ++e) gpart = fmaf(f[e], __uint_as_float(u[8 * c + e]), gpart);
       }
-      go *= inv;
+      xgo[h * 128 + r] = gpart;
+      asm volatile("bar.sync %0, 64;" ::"r"(pair_bar) : "memory");
+      const float go = (xgo[r] + xgo[128 + r]) * inv;
       // dq = (U - z go) / den * phi'(q); dz -= phi(q) go / den
       __nv_bfloat16* dst = a.dq + ((size_t)bh * a.N + (size_t)t * kTile + r) * kD;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < 4; ++c) {
+        const int cc = 4 * h + c;
         float f[8];
-        join8(*reinterpret_cast<const uint4*>(stq(st) + swz(r, c)), *reinterpret_cast<const uint4*>(stpl(st) + swz(r, c)),
+        join8(*reinterpret_cast<const uint4*>(stq(st) + swz(r, cc)), *reinterpret_cast<const uint4*>(stpl(st) + swz(r, cc)),
               f);
-        const uint32_t* u = c < 4 ? u0 + 8 * c : u1 + 8 * (c - 4);
         uint32_t pk[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-          const float d0 = (__uint_as_float(u[e]) - zs[c * 8 + e] * go) * inv * (f[e] > 1.f ? 1.f : f[e]);
-          const float d1 = (__uint_as_float(u[e + 1]) - zs[c * 8 + e + 1] * go) * inv * (f[e + 1] > 1.f ? 1.f : f[e + 1]);
+          const float d0 = (__uint_as_float(u[8 * c + e]) - zs[cc * 8 + e] * go) * inv * (f[e] > 1.f ? 1.f : f[e]);
+          const float d1 =
+              (__uint_as_float(u[8 * c + e + 1]) - zs[cc * 8 + e + 1] * go) * inv * (f[e + 1] > 1.f ? 1.f : f[e + 1]);
           pk[e >> 1] = pack_bf16(d0, d1);
           dz[c * 8 + e] = fmaf(-f[e], go * inv, dz[c * 8 + e]);
           dz[c * 8 + e + 1] = fmaf(-f[e + 1], go * inv, dz[c * 8 + e + 1]);
         }
-        if (valid) *reinterpret_cast<uint4*>(dst + c * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        if (valid) *reinterpret_cast<uint4*>(dst + cc * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
       }
       // g / den: hi over the g tile, lo in its own tile
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 4 * h; c < 4 * h + 4; ++c) {
         uint4* pg = reinterpret_cast<uint4*>(stg(st) + swz(r, c));
-        const uint4 u = *pg;
-        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+        const uint4 uu = *pg;
+        const uint32_t w[4] = {uu.x, uu.y, uu.z, uu.w};
         float f[8];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -750,33 +762,29 @@ __global__ void __launch_bounds__(kThreadsB, 1) la_bwd_query_kernel(const __grid
       if (lane == 0) mbar_arrive(dsready + st);
     }
     // epilogue: dS partial (M = 64: rows 16q .. 16q+15 in lanes 0..15 of lane
-    // quadrant q) and dz reduced over the 128 rows in fixed order
+    // quadrant q; this warp's 32 of the 64 columns) and dz reduced over the
+    // 128 rows in fixed order
     const bool got = ok && LWAIT(done, 0);
     tc_fence_after();
-    uint32_t s0[32], s1[32];
-    const uint32_t tq4 = tmem + ((uint32_t)(quad * 32) << 16) + 128;
+    uint32_t s0[32];
+    const uint32_t tq4 = tmem + ((uint32_t)(quad * 32) << 16) + 128 + 32 * h;
     tmem_ld32(tq4, s0);
-    tmem_ld32(tq4 + 32, s1);
     tmem_wait_ld(s0);
-    tmem_wait_ld(s1);
     const size_t part = (size_t)chunk * a.BH + bh;
     if (got && lane < 16) {
-      float* dst = a.part_dS + (part * kD + quad * 16 + lane) * kD;
+      float* dst = a.part_dS + (part * kD + quad * 16 + lane) * kD + 32 * h;
 #pragma unroll
-      for (int j = 0; j < 32; j += 4) {
+      for (int j = 0; j < 32; j += 4)
         *reinterpret_cast<float4*>(dst + j) = make_float4(__uint_as_float(s0[j]), __uint_as_float(s0[j + 1]),
                                                           __uint_as_float(s0[j + 2]), __uint_as_float(s0[j + 3]));
-        *reinterpret_cast<float4*>(dst + 32 + j) = make_float4(
-            __uint_as_float(s1[j]), __uint_as_float(s1[j + 1]), __uint_as_float(s1[j + 2]), __uint_as_float(s1[j + 3]));
-      }
     }
     // the stages are idle once `done` completed: reuse them for the dz rows
     float* zbuf = reinterpret_cast<float*>(smem + kBQBase);
     if (got) {
 #pragma unroll
-      for (int i = 0; i < kD; ++i) zbuf[r * kD + i] = dz[i];
+      for (int i = 0; i < kD / 2; ++i) zbuf[r * kD + 32 * h + i] = dz[i];
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, 256;" ::: "memory");
     if (got && tid < kD) {
       float sum = 0.f;
       for (int i = 0; i < kTile; ++i) sum += zbuf[i * kD + tid];
@@ -845,8 +853,10 @@ struct BKArgs {
 //           (A = phi parts, B = dS^T rows; chains hi.hi, hi.lo, lo.hi), into
 //           one of two TMEM buffer pairs
 //   math:   dk = (P1 + dz) * phi'(k), dv = P2, stored row by row
-// A stage is released by the issuer's commit and the four math warps together
-// (phi' is recomputed from phi's parts in the epilogue).
+// A stage is released by the issuer's commit and the eight math warps together
+// (phi' is recomputed from phi's parts in the epilogue).  Two math warps per
+// TMEM lane quadrant, each taking 32 of a row's 64 columns (nothing here sums
+// over a row).
 __global__ void __launch_bounds__(kThreadsB, 1) la_bwd_key_kernel(const __grid_constant__ CUtensorMap tk,
                                                                   const __grid_constant__ CUtensorMap tv,
                                                                   const BKArgs a) {
@@ -874,12 +884,12 @@ __global__ void __launch_bounds__(kThreadsB, 1) la_bwd_key_kernel(const __grid_c
   if (threadIdx.x == 0) {
     for (int i = 0; i < kBKStages; ++i) {
       mbar_init(full + i, 1);
-      mbar_init(empty + i, 5);  // the issuer's commit and the four math warps
-      mbar_init(kready + i, 4);
+      mbar_init(empty + i, 9);  // the issuer's commit and the eight math warps
+      mbar_init(kready + i, 8);
       mbar_init(pfull + i, 1);
-      mbar_init(pfree + i, 4);
+      mbar_init(pfree + i, 8);
     }
-    mbar_init(sready, 4);
+    mbar_init(sready, 8);
     *abort_flag = 0;
     fence_mbar_init();
     prefetch_tmap(&tk);
@@ -944,16 +954,17 @@ __global__ void __launch_bounds__(kThreadsB, 1) la_bwd_key_kernel(const __grid_c
   } else {
     // ------------------------------------------------------------------ math warps
     const int quad = warp & 3;
+    const int h = (warp - 2) >> 2;  // columns [32 h, 32 h + 32) of the row: chunks 4 h .. 4 h + 3
     const int r = quad * 32 + lane;
     const int tid = threadIdx.x - 64;
     {
       const size_t m = (size_t)bh * kD * kD;
       const __nv_bfloat16* src[4] = {a.dsh + m, a.dsl + m, a.dsth + m, a.dstl + m};
       uint8_t* dst[4] = {mDh, mDl, mTh, mTl};
-      load_mats(tid, 4, src, dst);
+      load_mats(tid, 256, 4, src, dst);
       if (tid < kD) dzs[tid] = a.dz[(size_t)bh * kD + tid];
       fence_proxy_async_smem();
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, 256;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(sready);
     }
@@ -963,7 +974,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) la_bwd_key_kernel(const __grid_c
       const bool valid = (int64_t)t * kTile + r < a.N;
       if (!(ok = LWAIT(full + st, n & 1))) break;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 4 * h; c < 4 * h + 4; ++c) {
         uint4* pk = reinterpret_cast<uint4*>(stk(st) + swz(r, c));
         float f[8];
         phi8(*pk, true, f);
@@ -977,38 +988,33 @@ __global__ void __launch_bounds__(kThreadsB, 1) la_bwd_key_kernel(const __grid_c
       if (lane == 0) mbar_arrive(kready + st);
       if (!(ok = LWAIT(pfull + b, n & 1))) break;
       tc_fence_after();
-      uint32_t p1a[32], p1b[32], p2a[32], p2b[32];
-      const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + 128 * b;
-      tmem_ld32(tl, p1a);
-      tmem_ld32(tl + 32, p1b);
-      tmem_ld32(tl + 64, p2a);
-      tmem_ld32(tl + 96, p2b);
-      tmem_wait_ld(p1a);
-      tmem_wait_ld(p1b);
-      tmem_wait_ld(p2a);
-      tmem_wait_ld(p2b);
+      uint32_t p1[32], p2[32];
+      const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + 128 * b + 32 * h;
+      tmem_ld32(tl, p1);
+      tmem_ld32(tl + 64, p2);
+      tmem_wait_ld(p1);
+      tmem_wait_ld(p2);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(pfree + b);
       const size_t row = ((size_t)bh * a.N + (size_t)t * kTile + r) * kD;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < 4; ++c) {
+        const int cc = 4 * h + c;
         float f[8];
-        join8(*reinterpret_cast<const uint4*>(stk(st) + swz(r, c)), *reinterpret_cast<const uint4*>(stpl(st) + swz(r, c)),
+        join8(*reinterpret_cast<const uint4*>(stk(st) + swz(r, cc)), *reinterpret_cast<const uint4*>(stpl(st) + swz(r, cc)),
               f);
-        const uint32_t* p1 = c < 4 ? p1a + 8 * c : p1b + 8 * (c - 4);
-        const uint32_t* p2 = c < 4 ? p2a + 8 * c : p2b + 8 * (c - 4);
         uint32_t ok4[4], ov4[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-          const float k0 = (__uint_as_float(p1[e]) + dzs[c * 8 + e]) * (f[e] > 1.f ? 1.f : f[e]);
-          const float k1 = (__uint_as_float(p1[e + 1]) + dzs[c * 8 + e + 1]) * (f[e + 1] > 1.f ? 1.f : f[e + 1]);
+          const float k0 = (__uint_as_float(p1[8 * c + e]) + dzs[cc * 8 + e]) * (f[e] > 1.f ? 1.f : f[e]);
+          const float k1 = (__uint_as_float(p1[8 * c + e + 1]) + dzs[cc * 8 + e + 1]) * (f[e + 1] > 1.f ? 1.f : f[e + 1]);
           ok4[e >> 1] = pack_bf16(k0, k1);
-          ov4[e >> 1] = pack_bf16(__uint_as_float(p2[e]), __uint_as_float(p2[e + 1]));
+          ov4[e >> 1] = pack_bf16(__uint_as_float(p2[8 * c + e]), __uint_as_float(p2[8 * c + e + 1]));
         }
         if (valid) {
-          *reinterpret_cast<uint4*>(a.dk + row + c * 8) = make_uint4(ok4[0], ok4[1], ok4[2], ok4[3]);
-          *reinterpret_cast<uint4*>(a.dv + row + c * 8) = make_uint4(ov4[0], ov4[1], ov4[2], ov4[3]);
+          *reinterpret_cast<uint4*>(a.dk + row + cc * 8) = make_uint4(ok4[0], ok4[1], ok4[2], ok4[3]);
+          *reinterpret_cast<uint4*>(a.dv + row + cc * 8) = make_uint4(ov4[0], ov4[1], ov4[2], ov4[3]);
         }
       }
       __syncwarp();
