@@ -11,7 +11,8 @@
 // Three kernels, all HBM-bound:
 //   la_summary_kernel  split-N summary: each CTA streams a chunk of 128-token
 //                      K and V tiles (TMA, 128-byte swizzle) through a ring of
-//                      shared-memory stages; four warps apply phi to the K tile
+//                      shared-memory stages; eight warps (two per row, 32
+//                      columns each) apply phi to the K tile
 //                      (rows past N zeroed) and write it as BF16 high parts in
 //                      place and low parts (phi - hi) in the stage's third
 //                      tile, and accumulate z in FP32 from the unrounded phi;
@@ -45,7 +46,7 @@ constexpr int kTile = 128;                 // tokens per tile
 constexpr int kTileBytes = kTile * kD * 2;  // 16 KB, one TMA box
 constexpr int kStagesS = 2;                 // summary ring: K (phi hi) + V + phi lo per stage
 constexpr int kSumStage = 3 * kTileBytes;
-constexpr int kThreadsL = 192;              // producer, issuer, 4 math warps
+constexpr int kThreadsL = 320;              // producer, issuer, 8 math warps (two per TMEM lane quadrant)
 constexpr int kQStages = 2;
 
 __device__ void set_status_l(uint32_t c) { set_status(c); }
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kThreadsL) la_summary_kernel(const __grid_cons
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStagesS; ++i) {
       mbar_init(full + i, 1);
-      mbar_init(kready + i, 4);
+      mbar_init(kready + i, 8);
       mbar_init(empty + i, 1);
     }
     mbar_init(done, 1);
@@ -198,11 +199,14 @@ __global__ void __launch_bounds__(kThreadsL) la_summary_kernel(const __grid_cons
     }
   } else {
     // ------------------------------------------------------------------ phi warps + epilogue
+    // two warps per TMEM lane quadrant: this thread's row (token), columns
+    // [32 h, 32 h + 32) (chunks 4 h .. 4 h + 3)
     const int quad = warp & 3;
-    const int r = quad * 32 + lane;  // tile row (token) of this thread
-    float zacc[kD];
+    const int h = (warp - 2) >> 2;
+    const int r = quad * 32 + lane;
+    float zacc[kD / 2];
 #pragma unroll
-    for (int i = 0; i < kD; ++i) zacc[i] = 0.f;
+    for (int i = 0; i < kD / 2; ++i) zacc[i] = 0.f;
     bool ok = true;
     for (int t = t0, G = 0; t < t1; ++t, ++G) {
       const int st = G % kStagesS, n = G / kStagesS;
@@ -210,14 +214,14 @@ __global__ void __launch_bounds__(kThreadsL) la_summary_kernel(const __grid_cons
       uint8_t* kt = smem + st * kSumStage;
       const bool valid = t * kTile + r < a.N;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        uint4* p = reinterpret_cast<uint4*>(kt + swz(r, c));
+      for (int c = 0; c < 4; ++c) {
+        uint4* p = reinterpret_cast<uint4*>(kt + swz(r, 4 * h + c));
         float f[8];
         phi8(*p, valid, f);
         uint4 hi, lo;
         split8(f, hi, lo);
         *p = hi;
-        *reinterpret_cast<uint4*>(kt + 2 * kTileBytes + swz(r, c)) = lo;
+        *reinterpret_cast<uint4*>(kt + 2 * kTileBytes + swz(r, 4 * h + c)) = lo;
 #pragma unroll
         for (int e = 0; e < 8; ++e) zacc[c * 8 + e] += f[e];
       }
@@ -226,33 +230,29 @@ __global__ void __launch_bounds__(kThreadsL) la_summary_kernel(const __grid_cons
       if (lane == 0) mbar_arrive(kready + st);
     }
     // epilogue: S partial from TMEM (M = 64: rows 16q .. 16q+15 in lanes 0..15
-    // of lane quadrant q), z partial reduced over the 128 rows in fixed order
+    // of lane quadrant q; this warp's 32 of the 64 columns), z partial reduced
+    // over the 128 rows in fixed order
     const bool got = ok && LWAIT(done, 0);
     tc_fence_after();
-    uint32_t s0[32], s1[32];
-    const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16);
+    uint32_t s0[32];
+    const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16) + 32 * h;
     tmem_ld32(tq, s0);
-    tmem_ld32(tq + 32, s1);
     tmem_wait_ld(s0);
-    tmem_wait_ld(s1);
     const size_t part = (size_t)chunk * a.BH + bh;
     if (got && lane < 16) {
-      float* dst = a.ws_S + (part * kD + quad * 16 + lane) * kD;
+      float* dst = a.ws_S + (part * kD + quad * 16 + lane) * kD + 32 * h;
 #pragma unroll
-      for (int j = 0; j < 32; j += 4) {
+      for (int j = 0; j < 32; j += 4)
         *reinterpret_cast<float4*>(dst + j) = make_float4(__uint_as_float(s0[j]), __uint_as_float(s0[j + 1]),
                                                           __uint_as_float(s0[j + 2]), __uint_as_float(s0[j + 3]));
-        *reinterpret_cast<float4*>(dst + 32 + j) = make_float4(
-            __uint_as_float(s1[j]), __uint_as_float(s1[j + 1]), __uint_as_float(s1[j + 2]), __uint_as_float(s1[j + 3]));
-      }
     }
     // all stages are idle once `done` completed: reuse them for the z rows
     float* zbuf = reinterpret_cast<float*>(smem);
     if (got) {
 #pragma unroll
-      for (int i = 0; i < kD; ++i) zbuf[r * kD + i] = zacc[i];
+      for (int i = 0; i < kD / 2; ++i) zbuf[r * kD + 32 * h + i] = zacc[i];
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");  // the four math warps only
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight math warps only
     const int tid = threadIdx.x - 64;
     if (got && tid < kD) {
       float s = 0.f;
