@@ -64,10 +64,10 @@ void prof_end(int kernel, cudaStream_t st) {
 static bool dtype_ok(int32_t t) { return t == GATTN_BF16 || t == GATTN_FP32; }
 
 static int clipped_extent(const Geom& g, int a, int k) {
-  int lo = k * g.c[a] - g.h[a], hi = (k + 1) * g.c[a] + g.h[a];
+  int64_t lo = (int64_t)k * g.c[a] - g.h[a], hi = (int64_t)(k + 1) * g.c[a] + g.h[a];
   lo = lo < 0 ? 0 : lo;
   hi = hi > g.G[a] ? g.G[a] : hi;
-  return hi - lo;
+  return (int)(hi - lo);
 }
 
 bool apply_box(Geom* g, const int b[3]);
@@ -80,7 +80,7 @@ bool apply_box(Geom* g, const int b[3]);
 // contiguous x run.  Non-power-of-two shapes matter for small tiles: a 24 x 24
 // extended tile takes five 5 x 24 boxes instead of six 4 x 32 boxes of which
 // a quarter is outside the tile.
-static void choose_box(Geom* g) {
+static bool choose_box(Geom* g) {
   // per dimension: the distinct clipped extents and how many tiles have each
   double cost[3][129];
   for (int a = 0; a < 3; ++a) {
@@ -104,7 +104,7 @@ static void choose_box(Geom* g) {
     for (int b = 1; b <= 128; ++b) {
       double sum = 0.0;
       for (int i = 0; i < nd; ++i) {
-        const double nb = (double)((ext[i] + b - 1) / b);
+        const double nb = (double)(((int64_t)ext[i] + b - 1) / b);
         sum += cnt[i] * nb * nb;
       }
       cost[a][b] = sum;
@@ -125,7 +125,7 @@ static void choose_box(Geom* g) {
           best[2] = bx;
         }
       }
-  apply_box(g, best);
+  return apply_box(g, best);
 }
 
 bool apply_box(Geom* g, const int b[3]) {
@@ -169,15 +169,18 @@ bool make_geom(const gattn_desc* desc, Geom* g) {
   int64_t ntiles = 1, Lmax = 1;
   for (int a = 0; a < 3; ++a) {
     if (d.core[a] < 1 || d.halo[a] < 0 || d.halo[a] > (1 << 24)) return false;
+    ntiles *= ((int64_t)g->G[a] + d.core[a] - 1) / d.core[a];
+  }
+  if (ntiles > 65535) return false;  // before the per-tile loops below
+  ntiles = 1;
+  for (int a = 0; a < 3; ++a) {
     g->c[a] = d.core[a];
     g->h[a] = d.halo[a];
-    g->n[a] = (g->G[a] + g->c[a] - 1) / g->c[a];
+    g->n[a] = (int32_t)(((int64_t)g->G[a] + g->c[a] - 1) / g->c[a]);
     int emax = 0;
     for (int k = 0; k < g->n[a]; ++k) {
-      int lo = k * g->c[a] - g->h[a], hi = (k + 1) * g->c[a] + g->h[a];
-      lo = lo < 0 ? 0 : lo;
-      hi = hi > g->G[a] ? g->G[a] : hi;
-      emax = hi - lo > emax ? hi - lo : emax;
+      const int e = clipped_extent(*g, a, k);
+      emax = e > emax ? e : emax;
     }
     g->emax[a] = emax;
     g->tiled[a] = (g->n[a] > 1 || g->h[a] > 0) ? 1 : 0;
@@ -191,8 +194,9 @@ bool make_geom(const gattn_desc* desc, Geom* g) {
   g->window = d.window;
   g->scale = d.scale > 0.f ? d.scale : 1.0f / sqrtf((float)d.d);
   g->scale_log2 = g->scale * 1.4426950408889634f;
-  choose_box(g);
-  if (g->R < 1 || (int64_t)g->nbmax_tot * 128 >= (1LL << 31)) return false;
+  // a box shape whose per-tile slot count does not fit 32 bits is refused
+  if (!choose_box(g)) return false;
+  if (g->R < 1 || g->nbmax_tot < 1 || (int64_t)g->nbmax_tot * 128 >= (1LL << 31)) return false;
   return true;
 }
 

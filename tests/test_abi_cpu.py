@@ -71,6 +71,31 @@ def test_invalid_descriptors_rejected(lib, kw):
     assert gattn.gattn_num_tiles(d) == -1
 
 
+@pytest.mark.parametrize(
+    "kw,ok",
+    [
+        # one tile as long as 32-bit slot indices allow: 2^24 - 1 boxes of 128 rows
+        (dict(B=1, nh=1, grid=(1, 1, 2**31 - 129), core=(1, 1, 2**31 - 129), halo=(0, 0, 0)), True),
+        (dict(B=1, nh=1, grid=(1, 2, 2**30 - 1), core=(1, 2, 2**30 - 1), halo=(0, 0, 0)), False),  # 2^24 boxes
+        (dict(B=1, nh=1, grid=(1, 1, 2**31 - 1), core=(1, 1, 2**31 - 1), halo=(0, 0, 0)), False),
+        (dict(B=1, nh=1, grid=(1, 1, 2**31 - 1), core=(1, 1, 1), halo=(0, 0, 0)), False),  # 2^31 - 1 tiles
+        (dict(B=1, nh=1, grid=(1, 2, 2**30), core=(1, 1, 2**30), halo=(0, 0, 0)), False),  # N = 2^31
+        (dict(B=1, nh=1, grid=(1, 256, 256), core=(1, 1, 1), halo=(0, 0, 0)), False),  # 65536 tiles
+        (dict(B=1, nh=1, grid=(1, 255, 257), core=(1, 1, 1), halo=(0, 0, 0)), True),  # 65535 tiles
+        (dict(B=256, nh=256, grid=(1, 8, 8), core=(1, 8, 8), halo=(0, 0, 0)), False),  # B * nh = 65536
+        (dict(B=255, nh=257, grid=(1, 8, 8), core=(1, 8, 8), halo=(0, 0, 0)), True),  # B * nh = 65535
+        (dict(B=1, nh=1, grid=(1, 1, 1), core=(1, 1, 1), halo=(0, 0, 0)), True),  # one token
+    ],
+)
+def test_size_limits(lib, kw, ok):
+    """Descriptors at the edges of the index ranges the kernels use (32-bit
+    token and row indices, 16-bit tile and batch*head grid dimensions) are
+    accepted up to the limit and refused beyond it, on the host."""
+    d = _desc(**kw)
+    assert (gattn.gattn_validate(d) == 0) == ok
+    assert (gattn.gattn_saved_bytes(d) > 0) == ok
+
+
 def test_fwd_rejects_bad_pointers_without_touching_the_gpu(lib):
     d = _desc()
     # NULL and misaligned pointers are refused before any CUDA call

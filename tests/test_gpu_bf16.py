@@ -31,6 +31,11 @@ FWD_CASES = [
     ("d128_ragged_all_dims", 2, 3, 128, (3, 10, 13), (2, 4, 5), (1, 2, 2)),
     # d = 128, several boxes per tile in every dimension and a long item (two K/V ring wraps)
     ("d128_multi_box", 1, 2, 128, (6, 24, 24), (3, 12, 12), (1, 2, 2)),
+    # a halo almost as wide as the core: up to nine covering tiles per token (the merges' general path)
+    ("wide_halo", 1, 1, 64, (1, 20, 20), (1, 4, 4), (0, 3, 3)),
+    # degenerate: one token (a one-row box; every other key and query of the MMA blocks is padding)
+    ("single_token", 1, 2, 64, (1, 1, 1), (1, 1, 1), (0, 0, 0)),
+    ("single_token_d128", 1, 1, 128, (1, 1, 1), (1, 1, 1), (0, 0, 0)),
     # one 1x8x48 tile = three 1x8x16 boxes: the second box of the last query pair is empty
     ("odd_box_count", 1, 2, 64, (1, 8, 48), (1, 8, 48), (0, 0, 0)),
 ]
@@ -73,7 +78,7 @@ def test_bf16_forward_is_deterministic():
     assert torch.equal(a, b)
 
 
-BWD_CASES = [c for c in FWD_CASES if c[0] != "long_tile_ring_wrap"] + [
+BWD_CASES = [c for c in FWD_CASES if c[0] != "long_tile_ring_wrap" and not c[0].startswith("single_token")] + [
     ("bwd_long_tile", 1, 1, 64, (4, 32, 32), (4, 16, 16), (0, 4, 4)),
 ]
 
@@ -107,3 +112,25 @@ def test_bf16_backward_is_deterministic():
     b = gattn.backward(tq, tk, tv, out, tg, saved, tiling)
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("d", [64, 128])
+@pytest.mark.parametrize("out_dtype", [torch.float32, torch.bfloat16], ids=["out_fp32", "out_bf16"])
+def test_single_token_backward(d, out_dtype):
+    """One token, one tile: the output is V, so dV = dOut exactly and dQ = dK = 0
+    (the softmax over one key is the constant 1).  dQ and dK come out as
+    P (dP - D) with dP = dOut . V from the tensor core and D = dOut . Out from the
+    stored output: small, not exactly zero."""
+    q, k, v, go = _inputs(1, 2, d, (1, 1, 1), 77)
+    dev = torch.device("cuda:0")
+    tq, tk, tv, tg = (t.to(dev) for t in (q, k, v, go))
+    tiling = gattn.Tiling((1, 1, 1), (1, 1, 1), (0, 0, 0))
+    out, saved = gattn.forward(tq, tk, tv, tiling, out_dtype=out_dtype)
+    dq, dk, dv = gattn.backward(tq, tk, tv, out, tg, saved, tiling)
+    st = gattn.gattn_stream_status()
+    assert st == 0, gattn.STATUS.get(st, st)
+    assert_close("single/out", out.double().cpu().numpy(), v.double().numpy(), MAX_REL, RMS_REL)
+    assert_close("single/dv", dv.double().cpu().numpy(), go.double().numpy(), MAX_REL, RMS_REL)
+    bound = (1e-3 if out_dtype == torch.float32 else 2e-2) * float(go.abs().max()) * float(v.abs().max())
+    for name, t in (("dq", dq), ("dk", dk)):
+        assert float(t.abs().max()) <= bound, (name, float(t.abs().max()), bound)
