@@ -193,9 +193,9 @@ cudaError_t launch_sm103_fwd_ragged(const ReqDesc* reqs, const int64_t* counts, 
 // d = 64: the two-box kernel; its work items per (head, tile) are pairs of boxes
 cudaError_t launch_sm103_fwd64_ragged(const ReqDesc* reqs, const int64_t* counts, int box_rows, cudaStream_t st);
 int fwd64_ragged_items(const Geom& g);  // nh * ntiles * ceil(nbmax_tot / 2)
-// warp_rows: the warp-per-32-rows form (every token has at most kMaxCover
-// covering tiles), else one thread per 4 columns of a row
-cudaError_t launch_serve_update(const ReqDesc* reqs, const int64_t* counts, int d, float c, bool warp_rows,
+// warp_covers: the most tiles that cover a token, for the warp-per-32-rows
+// form (at most kMaxCover); 0 selects one thread per 4 columns of a row
+cudaError_t launch_serve_update(const ReqDesc* reqs, const int64_t* counts, int d, float c, int warp_covers,
                                 cudaStream_t st);
 
 // ---- small device helpers

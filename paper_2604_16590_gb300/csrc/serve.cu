@@ -112,15 +112,16 @@ __global__ void __launch_bounds__(kThreads) serve_update_kernel(const ReqDesc* _
 // merge.cu): each lane resolves its row's request, head and token and lists
 // the row's covering tiles with their slots and window weights; half-warps
 // then update the rows two at a time, lane f of a half holding columns
-// [4 f, 4 f + 4) (and [4 f + 64, 4 f + 68) at d = 128), so the per-tile rows
-// are read as contiguous runs and the geometry is resolved once per row
-// instead of once per 4 columns.  The window table is built from the first
-// request's geometry; a row whose request differs in core, halo, window or
-// tiled dimensions evaluates its window directly.  For up to kMaxCover
-// covering tiles per token (the host checks it).
-__global__ void __launch_bounds__(kThreads, 2) serve_update_warp_kernel(const ReqDesc* __restrict__ reqs,
-                                                                     const int64_t* __restrict__ counts, int d,
-                                                                     float c) {
+// [4 f, 4 f + 4) (and [4 f + 64, 4 f + 68) at d = 128, U = 2), so the per-tile
+// rows are read as contiguous runs and the geometry is resolved once per row
+// instead of once per 4 columns.  A pair's loads of all its covering rows
+// (at most MAXC) are issued before their weighted sum (ascending tile order):
+// the kernel is bound by how many loads are in flight.  The window table is
+// built from the first request's geometry; a row whose request differs in
+// core, halo, window or tiled dimensions evaluates its window directly.
+template <int MAXC, int U>
+__global__ void __launch_bounds__(kThreads, MAXC == 4 && U == 1 ? 3 : 2)
+    serve_update_warp_kernel(const ReqDesc* __restrict__ reqs, const int64_t* __restrict__ counts, int d, float c) {
   __shared__ float win[kWinMax];
   const int nreq = (int)counts[0];
   if (nreq < 1) return;  // uniform over the grid: no request, no table
@@ -128,7 +129,6 @@ __global__ void __launch_bounds__(kThreads, 2) serve_update_warp_kernel(const Re
   const Geom& g0 = reqs[0].g;
   const WinTable tbl = build_win_table(g0, win);
   const int lane = threadIdx.x & 31;
-  const int F4 = d / 4;  // 16 or 32
   const int64_t stride = (int64_t)gridDim.x * (kThreads / 32) * 32;
   for (int64_t base = ((int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32; base < rows;
        base += stride) {
@@ -152,8 +152,13 @@ __global__ void __launch_bounds__(kThreads, 2) serve_update_warp_kernel(const Re
         WinTable t = tbl;
         t.direct = t.direct || !same;
         n = token_covers(g, t, (int)(local / g.N), local % g.N, slot, w);
+        if (n > MAXC) {  // the host chose MAXC from the largest cover count
+          set_status(kStatusBounds);
+          r = -1;
+          n = 0;
+        }
 #pragma unroll
-        for (int k = 0; k < kMaxCover; ++k)
+        for (int k = 0; k < MAXC; ++k)
           if (k < n) wsum += w[k];
       }
     }
@@ -163,39 +168,37 @@ __global__ void __launch_bounds__(kThreads, 2) serve_update_warp_kernel(const Re
       const int nc = __shfl_sync(0xffffffffu, n, owner);
       const int64_t lo = __shfl_sync(0xffffffffu, local, owner);
       const float inv = 1.f / __shfl_sync(0xffffffffu, wsum, owner);
-      const int ncmax = max(nc, __shfl_xor_sync(0xffffffffu, nc, 16));
       const int f0 = lane & 15;
-      float4 acc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
       const float* ot = ro >= 0 ? reqs[ro].ot : nullptr;
+      float4 o[MAXC][U];
+      float wc[MAXC];
 #pragma unroll
-      for (int k = 0; k < kMaxCover; ++k) {
-        if (k >= ncmax) break;
+      for (int k = 0; k < MAXC; ++k) {
         const int64_t sc = __shfl_sync(0xffffffffu, slot[k], owner);
-        const float wc = __shfl_sync(0xffffffffu, w[k], owner);
-        if (k < nc) {
-          const float4* row = reinterpret_cast<const float4*>(ot + sc * d);
+        wc[k] = __shfl_sync(0xffffffffu, w[k], owner);
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int f = f0 + 16 * u;
-            if (f < F4) {
-              const float4 o = __ldg(row + f);
-              acc[u] = make_float4(fmaf(wc, o.x, acc[u].x), fmaf(wc, o.y, acc[u].y), fmaf(wc, o.z, acc[u].z),
-                                   fmaf(wc, o.w, acc[u].w));
-            }
-          }
+        for (int u = 0; u < U; ++u) {
+          o[k][u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (k < nc) o[k][u] = __ldg(reinterpret_cast<const float4*>(ot + sc * d) + f0 + 16 * u);
         }
       }
       if (ro < 0) continue;
       const ReqDesc& rq = reqs[ro];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < U; ++u) {
         const int f = f0 + 16 * u;
-        if (f >= F4) continue;
         float4 att;
-        if (nc == 0)
+        if (nc == 0) {
           att = load4<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(rq.out) + lo * d + 4 * f);
-        else
-          att = make_float4(acc[u].x * inv, acc[u].y * inv, acc[u].z * inv, acc[u].w * inv);
+        } else {
+          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int k = 0; k < MAXC; ++k)
+            if (k < nc)
+              acc = make_float4(fmaf(wc[k], o[k][u].x, acc.x), fmaf(wc[k], o[k][u].y, acc.y), fmaf(wc[k], o[k][u].z, acc.z),
+                                fmaf(wc[k], o[k][u].w, acc.w));
+          att = make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv);
+        }
         __nv_bfloat16* zp = rq.z + lo * d + 4 * f;
         const float4 z = load4<__nv_bfloat16>(zp);
         store4<__nv_bfloat16>(zp, make_float4(fmaf(c, att.x - z.x, z.x), fmaf(c, att.y - z.y, z.y),
@@ -212,12 +215,19 @@ double seconds_since(Clock::time_point t0) {
 
 }  // namespace
 
-cudaError_t launch_serve_update(const ReqDesc* reqs, const int64_t* counts, int d, float c, bool warp_rows,
+cudaError_t launch_serve_update(const ReqDesc* reqs, const int64_t* counts, int d, float c, int warp_covers,
                                 cudaStream_t st) {
-  if (warp_rows)
-    serve_update_warp_kernel<<<num_sms() * 8, kThreads, 0, st>>>(reqs, counts, d, c);
+  const unsigned grid = num_sms() * 8;
+  if (warp_covers > 0 && warp_covers <= 4 && d == 64)
+    serve_update_warp_kernel<4, 1><<<grid, kThreads, 0, st>>>(reqs, counts, d, c);
+  else if (warp_covers > 0 && warp_covers <= 4)
+    serve_update_warp_kernel<4, 2><<<grid, kThreads, 0, st>>>(reqs, counts, d, c);
+  else if (warp_covers > 0 && d == 64)
+    serve_update_warp_kernel<kMaxCover, 1><<<grid, kThreads, 0, st>>>(reqs, counts, d, c);
+  else if (warp_covers > 0)
+    serve_update_warp_kernel<kMaxCover, 2><<<grid, kThreads, 0, st>>>(reqs, counts, d, c);
   else
-    serve_update_kernel<<<num_sms() * 8, kThreads, 0, st>>>(reqs, counts, d, c);
+    serve_update_kernel<<<grid, kThreads, 0, st>>>(reqs, counts, d, c);
   return cudaGetLastError();
 }
 
@@ -261,7 +271,7 @@ struct gattn_server {
   ReqDesc* h_reqs = nullptr;  // pinned staging
   int64_t* h_counts = nullptr;
   cudaGraphExec_t graph = nullptr;
-  bool warp_rows = false;  // the update kernel's warp-per-32-rows form applies
+  int warp_covers = 0;  // most tiles covering a token (<= kMaxCover: the warp-per-32-rows update), else 0
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   size_t hbm_in_use = 0, hbm_peak = 0;
   int64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, iterations = 0;
@@ -358,8 +368,8 @@ gattn_status gattn_serve_create(const gattn_serve_cfg* cfg, gattn_stream_t strea
   {
     // covering tiles per token: temporal extents of 3 c + 2 h frames show the maximum
     Geom span;
-    s->warp_rows = serve_geom(cfg, 3 * cfg->core[0] + 2 * cfg->halo[0], 1, &span, true) &&
-                   max_covers(span) <= kMaxCover;
+    if (serve_geom(cfg, 3 * cfg->core[0] + 2 * cfg->halo[0], 1, &span, true) && max_covers(span) <= kMaxCover)
+      s->warp_covers = max_covers(span);
   }
   s->stream = reinterpret_cast<cudaStream_t>(stream);
   if (!s->stream) {
@@ -504,12 +514,12 @@ gattn_status gattn_serve_step(gattn_server* s, int32_t* n_active, int32_t* n_wai
         // kernels' attributes outside capture), then records the same two
         // launches into the graph that every later iteration replays
         if (launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, probe_rows(s), s->stream) != cudaSuccess ||
-            launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->warp_rows, s->stream) != cudaSuccess)
+            launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->warp_covers, s->stream) != cudaSuccess)
           return GATTN_ERR_CUDA;
         cudaGraph_t gr;
         if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GATTN_ERR_CUDA;
         cudaError_t e1 = launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, probe_rows(s), s->stream);
-        cudaError_t e2 = launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->warp_rows, s->stream);
+        cudaError_t e2 = launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->warp_covers, s->stream);
         cudaError_t e3 = cudaStreamEndCapture(s->stream, &gr);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return GATTN_ERR_CUDA;
         if (cudaGraphInstantiate(&s->graph, gr, 0) != cudaSuccess) return GATTN_ERR_CUDA;
@@ -519,7 +529,7 @@ gattn_status gattn_serve_step(gattn_server* s, int32_t* n_active, int32_t* n_wai
       }
     } else {
       if (launch_sm103_fwd_ragged(s->d_reqs, s->d_counts, s->cfg.d, probe_rows(s), s->stream) != cudaSuccess ||
-          launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->warp_rows, s->stream) != cudaSuccess)
+          launch_serve_update(s->d_reqs, s->d_counts, s->cfg.d, s->cfg.c, s->warp_covers, s->stream) != cudaSuccess)
         return GATTN_ERR_CUDA;
     }
     cudaEventRecord(s->ev1, s->stream);
