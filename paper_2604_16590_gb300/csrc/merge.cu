@@ -87,12 +87,13 @@ __global__ void __launch_bounds__(kThreads) merge_fwd_kernel(Geom g, const float
 // The same merge, one warp per 32 consecutive tokens: each lane lists its
 // token's covering slots and weights (token_covers), then the half-warps take
 // the tokens in pairs, lane f of a half reading 16 bytes f of every covering
-// slot's row (contiguous 256-byte runs at d = 64) with the slot and the weight
-// broadcast from the owner lane.  Used when no token has more than kMaxCover
-// covering tiles.
-template <typename OutT>
-__global__ void __launch_bounds__(kThreads, 4) merge_fwd_warp_kernel(Geom g, const float* __restrict__ ot,
-                                                                  OutT* __restrict__ out) {
+// slot's row (contiguous 256-byte runs at d = 64; U = 2 more 16-byte units at
+// d = 128) with the slot and the weight broadcast from the owner lane.  A
+// pair's loads of all its covering rows (at most MAXC, the host's bound for
+// the geometry) are issued before their weighted sum in ascending tile order.
+template <typename OutT, int MAXC, int U>
+__global__ void __launch_bounds__(kThreads, MAXC <= 2 ? 4 : MAXC == 4 ? 3 : 2)
+    merge_fwd_warp_kernel(Geom g, const float* __restrict__ ot, OutT* __restrict__ out) {
   __shared__ float win[kWinMax];
   const WinTable tbl = build_win_table(g, win);
   const int lane = threadIdx.x & 31;
@@ -102,14 +103,14 @@ __global__ void __launch_bounds__(kThreads, 4) merge_fwd_warp_kernel(Geom g, con
   for (int64_t base = ((int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32; base < total;
        base += stride) {
     const int64_t idx = base + lane;
-    int64_t slot[kMaxCover];
-    float w[kMaxCover];
+    int64_t slot[MAXC];
+    float w[MAXC];
     int n = 0;
     float wsum = 0.f;
     if (idx < total) {
       n = token_covers(g, tbl, (int)(idx / g.N), idx % g.N, slot, w);
 #pragma unroll
-      for (int c = 0; c < kMaxCover; ++c)
+      for (int c = 0; c < MAXC; ++c)
         if (c < n) wsum += w[c];
     }
     for (int q = 0; q < 16; ++q) {
@@ -119,31 +120,32 @@ __global__ void __launch_bounds__(kThreads, 4) merge_fwd_warp_kernel(Geom g, con
       if (ncmax == 0) continue;  // both tokens written by their tile kernel
       const float inv = 1.f / __shfl_sync(0xffffffffu, wsum, owner);
       const int f0 = lane & 15;
-      float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+      float4 o[MAXC][U];
+      float wc[MAXC];
 #pragma unroll
-      for (int c = 0; c < kMaxCover; ++c) {
-        if (c >= ncmax) break;
+      for (int c = 0; c < MAXC; ++c) {
         const int64_t sc = __shfl_sync(0xffffffffu, slot[c], owner);
-        const float wc = __shfl_sync(0xffffffffu, w[c], owner);
-        if (c < nc) {
-          const float4* row = reinterpret_cast<const float4*>(ot + sc * g.d);
-          if (f0 < F4) {
-            const float4 o = __ldg(row + f0);
-            acc0 = make_float4(fmaf(wc, o.x, acc0.x), fmaf(wc, o.y, acc0.y), fmaf(wc, o.z, acc0.z),
-                               fmaf(wc, o.w, acc0.w));
-          }
-          if (f0 + 16 < F4) {
-            const float4 o = __ldg(row + f0 + 16);
-            acc1 = make_float4(fmaf(wc, o.x, acc1.x), fmaf(wc, o.y, acc1.y), fmaf(wc, o.z, acc1.z),
-                               fmaf(wc, o.w, acc1.w));
-          }
+        wc[c] = __shfl_sync(0xffffffffu, w[c], owner);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          o[c][u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (c < nc && f0 + 16 * u < F4) o[c][u] = __ldg(reinterpret_cast<const float4*>(ot + sc * g.d) + f0 + 16 * u);
         }
       }
       if (nc > 0) {
         OutT* dst = out + (base + owner) * g.d;
-        if (f0 < F4) store4<OutT>(dst + 4 * f0, make_float4(acc0.x * inv, acc0.y * inv, acc0.z * inv, acc0.w * inv));
-        if (f0 + 16 < F4)
-          store4<OutT>(dst + 4 * (f0 + 16), make_float4(acc1.x * inv, acc1.y * inv, acc1.z * inv, acc1.w * inv));
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int f = f0 + 16 * u;
+          if (f >= F4) continue;
+          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int c = 0; c < MAXC; ++c)
+            if (c < nc)
+              acc = make_float4(fmaf(wc[c], o[c][u].x, acc.x), fmaf(wc[c], o[c][u].y, acc.y), fmaf(wc[c], o[c][u].z, acc.z),
+                                fmaf(wc[c], o[c][u].w, acc.w));
+          store4<OutT>(dst + 4 * f, make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv));
+        }
       }
     }
   }
@@ -381,12 +383,33 @@ inline unsigned grid_warp(int64_t tokens) {
 }
 
 cudaError_t launch_merge_fwd(const Geom& g, const float* ot, void* out, int out_dtype, cudaStream_t st) {
-  if (max_covers(g) <= kMaxCover) {
+  const int mc = max_covers(g);
+  if (mc <= kMaxCover) {
     const unsigned grid = grid_warp((int64_t)g.B * g.nh * g.N);
-    if (out_dtype == GATTN_BF16)
-      merge_fwd_warp_kernel<__nv_bfloat16><<<grid, kThreads, 0, st>>>(g, ot, static_cast<__nv_bfloat16*>(out));
-    else
-      merge_fwd_warp_kernel<float><<<grid, kThreads, 0, st>>>(g, ot, static_cast<float*>(out));
+    using bf = __nv_bfloat16;
+    const bool b16 = out_dtype == GATTN_BF16, wide = g.d > 64;
+    if (mc <= 2) {
+      if (b16)
+        wide ? merge_fwd_warp_kernel<bf, 2, 2><<<grid, kThreads, 0, st>>>(g, ot, static_cast<bf*>(out))
+             : merge_fwd_warp_kernel<bf, 2, 1><<<grid, kThreads, 0, st>>>(g, ot, static_cast<bf*>(out));
+      else
+        wide ? merge_fwd_warp_kernel<float, 2, 2><<<grid, kThreads, 0, st>>>(g, ot, static_cast<float*>(out))
+             : merge_fwd_warp_kernel<float, 2, 1><<<grid, kThreads, 0, st>>>(g, ot, static_cast<float*>(out));
+    } else if (mc <= 4) {
+      if (b16)
+        wide ? merge_fwd_warp_kernel<bf, 4, 2><<<grid, kThreads, 0, st>>>(g, ot, static_cast<bf*>(out))
+             : merge_fwd_warp_kernel<bf, 4, 1><<<grid, kThreads, 0, st>>>(g, ot, static_cast<bf*>(out));
+      else
+        wide ? merge_fwd_warp_kernel<float, 4, 2><<<grid, kThreads, 0, st>>>(g, ot, static_cast<float*>(out))
+             : merge_fwd_warp_kernel<float, 4, 1><<<grid, kThreads, 0, st>>>(g, ot, static_cast<float*>(out));
+    } else {
+      if (b16)
+        wide ? merge_fwd_warp_kernel<bf, kMaxCover, 2><<<grid, kThreads, 0, st>>>(g, ot, static_cast<bf*>(out))
+             : merge_fwd_warp_kernel<bf, kMaxCover, 1><<<grid, kThreads, 0, st>>>(g, ot, static_cast<bf*>(out));
+      else
+        wide ? merge_fwd_warp_kernel<float, kMaxCover, 2><<<grid, kThreads, 0, st>>>(g, ot, static_cast<float*>(out))
+             : merge_fwd_warp_kernel<float, kMaxCover, 1><<<grid, kThreads, 0, st>>>(g, ot, static_cast<float*>(out));
+    }
     return cudaGetLastError();
   }
   const int64_t total = (int64_t)g.B * g.nh * g.N * (g.d / 4);

@@ -79,9 +79,11 @@ __device__ __forceinline__ float table_weight(const Geom& g, const WinTable& t, 
 }
 
 // Covering tiles of token i of batch*head bh in ascending tile order: their
-// slots and weights.  Returns the count (0 for a token covered by one tile).
-__device__ __forceinline__ int token_covers(const Geom& g, const WinTable& t, int bh, int64_t i,
-                                            int64_t (&slot)[kMaxCover], float (&w)[kMaxCover]) {
+// slots and weights (the first NC of them).  Returns the count (0 for a token
+// covered by one tile).
+template <int NC>
+__device__ __forceinline__ int token_covers(const Geom& g, const WinTable& t, int bh, int64_t i, int64_t (&slot)[NC],
+                                            float (&w)[NC]) {
   int p[3], k0[3], k1[3];
   token_pos(g, i, p);
   bool multi = false;
@@ -108,7 +110,7 @@ __device__ __forceinline__ int token_covers(const Geom& g, const WinTable& t, in
         }
         const int tile = (k[0] * g.n[1] + k[1]) * g.n[2] + k[2];
 #pragma unroll
-        for (int c = 0; c < kMaxCover; ++c)
+        for (int c = 0; c < NC; ++c)
           if (c == n) {
             slot[c] = slot_of(g, bh, tile, e, l);
             w[c] = table_weight(g, t, p, k);
