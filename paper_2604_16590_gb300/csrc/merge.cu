@@ -84,24 +84,32 @@ __global__ void __launch_bounds__(kThreads) merge_fwd_kernel(Geom g, const float
   }
 }
 
-// The same merge, one warp per 32 consecutive tokens: each lane lists its
-// token's covering slots and weights (token_covers), then the half-warps take
-// the tokens in pairs, lane f of a half reading 16 bytes f of every covering
-// slot's row (contiguous 256-byte runs at d = 64; U = 2 more 16-byte units at
-// d = 128) with the slot and the weight broadcast from the owner lane.  A
-// pair's loads of all its covering rows (at most MAXC, the host's bound for
-// the geometry) are issued before their weighted sum in ascending tile order.
+// The same merge, one warp per 32 consecutive tokens.  Each lane lists its
+// token's covering slots and weights (token_covers) and writes them into one
+// of two shared-memory row lists (parity_offset): half-warp h reads the rows
+// of the tokens of lanes h, h + 2, ... in turn, lane f of the half holding
+// 16 bytes f of every row (contiguous 256-byte runs at d = 64; U = 2 more
+// 16-byte units at d = 128).  The halves take their lists R rows at a time,
+// all R loads issued before the weighted sums: how many rows are in flight no
+// longer depends on how many tiles cover each token, and the kernel is bound
+// by how many are.  Each token's rows come in ascending tile order and are
+// summed in that order.
 template <typename OutT, int MAXC, int U>
-__global__ void __launch_bounds__(kThreads, MAXC <= 2 ? 4 : MAXC == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, 2)
     merge_fwd_warp_kernel(Geom g, const float* __restrict__ ot, OutT* __restrict__ out) {
+  constexpr int R = (MAXC <= 4 ? 16 : 8) / U;  // 64 or 32 registers of rows in flight per lane, no spills
+  constexpr int W = kThreads / 32;
   __shared__ float win[kWinMax];
+  __shared__ RowRef rows[W][2][16 * MAXC];
+  __shared__ float tinv[W][32];
   const WinTable tbl = build_win_table(g, win);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int f0 = lane & 15;
   const int64_t total = (int64_t)g.B * g.nh * g.N;
   const int F4 = g.d / 4;  // 8, 16 or 32
-  const int64_t stride = (int64_t)gridDim.x * (kThreads / 32) * 32;
-  for (int64_t base = ((int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32; base < total;
-       base += stride) {
+  const int64_t stride = (int64_t)gridDim.x * W * 32;
+  const RowRef* list = rows[wid][lane >> 4];
+  for (int64_t base = ((int64_t)blockIdx.x * W + wid) * 32; base < total; base += stride) {
     const int64_t idx = base + lane;
     int64_t slot[MAXC];
     float w[MAXC];
@@ -109,45 +117,67 @@ __global__ void __launch_bounds__(kThreads, MAXC <= 2 ? 4 : MAXC == 4 ? 3 : 2)
     float wsum = 0.f;
     if (idx < total) {
       n = token_covers(g, tbl, (int)(idx / g.N), idx % g.N, slot, w);
+      if (n > MAXC) {  // the host chose MAXC from the largest cover count
+        set_status(kStatusBounds);
+        n = 0;
+      }
 #pragma unroll
       for (int c = 0; c < MAXC; ++c)
         if (c < n) wsum += w[c];
     }
-    for (int q = 0; q < 16; ++q) {
-      const int owner = 2 * q + (lane >> 4);
-      const int nc = __shfl_sync(0xffffffffu, n, owner);
-      const int ncmax = max(nc, __shfl_xor_sync(0xffffffffu, nc, 16));
-      if (ncmax == 0) continue;  // both tokens written by their tile kernel
-      const float inv = 1.f / __shfl_sync(0xffffffffu, wsum, owner);
-      const int f0 = lane & 15;
-      float4 o[MAXC][U];
-      float wc[MAXC];
+    int len;
+    RowRef* mine = rows[wid][lane & 1] + parity_offset(n, lane, len);
 #pragma unroll
-      for (int c = 0; c < MAXC; ++c) {
-        const int64_t sc = __shfl_sync(0xffffffffu, slot[c], owner);
-        wc[c] = __shfl_sync(0xffffffffu, w[c], owner);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          o[c][u] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (c < nc && f0 + 16 * u < F4) o[c][u] = __ldg(reinterpret_cast<const float4*>(ot + sc * g.d) + f0 + 16 * u);
-        }
+    for (int c = 0; c < MAXC; ++c)
+      if (c < n) {
+        RowRef e;
+        e.p = ot + slot[c] * g.d;
+        e.w = w[c];
+        e.flags = lane | (c == n - 1 ? kRowLast : 0);
+        mine[c] = e;
       }
-      if (nc > 0) {
-        OutT* dst = out + (base + owner) * g.d;
+    tinv[wid][lane] = 1.f / wsum;  // read only for tokens with rows
+    __syncwarp();
+    const int lmax = max(len, __shfl_xor_sync(0xffffffffu, len, 16));
+    float4 acc[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int f = f0 + 16 * u;
-          if (f >= F4) continue;
-          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int u = 0; u < U; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int e0 = 0; e0 < lmax; e0 += R) {
+      const int nv = len - e0;  // rows of this half's list from e0 on
+      float4 o[R][U];
 #pragma unroll
-          for (int c = 0; c < MAXC; ++c)
-            if (c < nc)
-              acc = make_float4(fmaf(wc[c], o[c][u].x, acc.x), fmaf(wc[c], o[c][u].y, acc.y), fmaf(wc[c], o[c][u].z, acc.z),
-                                fmaf(wc[c], o[c][u].w, acc.w));
-          store4<OutT>(dst + 4 * f, make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv));
+      for (int j = 0; j < R; ++j)
+        if (j < nv) {
+          const float4* p = reinterpret_cast<const float4*>(row_addr(list + e0 + j));
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (f0 + 16 * u < F4) o[j][u] = __ldg(p + f0 + 16 * u);
+        }
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        if (j >= nv) break;
+        float wr;
+        int fl;
+        row_weight_flags(list + e0 + j, wr, fl);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          acc[u] = make_float4(fmaf(wr, o[j][u].x, acc[u].x), fmaf(wr, o[j][u].y, acc[u].y),
+                               fmaf(wr, o[j][u].z, acc[u].z), fmaf(wr, o[j][u].w, acc[u].w));
+        if (fl & kRowLast) {
+          const int owner = fl & 31;
+          const float inv = tinv[wid][owner];
+          OutT* dst = out + (base + owner) * g.d;
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int f = f0 + 16 * u;
+            if (f < F4) store4<OutT>(dst + 4 * f, make_float4(acc[u].x * inv, acc[u].y * inv, acc[u].z * inv, acc[u].w * inv));
+            acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
         }
       }
     }
+    __syncwarp();  // the lists are rewritten for the next 32 tokens
   }
 }
 

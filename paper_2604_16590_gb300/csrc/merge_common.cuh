@@ -16,7 +16,18 @@
 namespace gattn {
 
 constexpr int kMaxCover = 8;    // covering tiles a lane lists for its token
-constexpr int kWinMax = 6144;   // table entries (sum of c_a + 2 h_a) kept in shared memory
+constexpr int kWinMax = 2048;   // table entries (sum of c_a + 2 h_a) kept in shared memory
+
+// One row in a half-warp's list of rows to read (the flattened merge loops):
+// the row's address, its weight and flags (bits 0-4: the lane that owns the
+// row's token; kRowLast: the token's last covering row; kRowBf16: a BF16 row,
+// else FP32; kRowState: the token's state row, read, updated and written back).
+struct alignas(16) RowRef {
+  const void* p;
+  float w;
+  int flags;
+};
+constexpr int kRowLast = 32, kRowBf16 = 64, kRowState = 128;
 
 // Most tiles covering one token (product over dimensions of the per-dimension
 // maximum); the cover pattern repeats with period c, edges only lower it.
@@ -76,6 +87,39 @@ __device__ __forceinline__ float table_weight(const Geom& g, const WinTable& t, 
 #pragma unroll
   for (int a = 0; a < 3; ++a) w *= t.w[t.off[a] + p[a] - (k[a] * g.c[a] - g.h[a])];
   return w;
+}
+
+// Reads of a list entry's address, and of its weight and flags.  They are
+// volatile so that the compiler does not merge a second read of an entry with
+// the first (that would keep every entry's fields live across the row loads).
+__device__ __forceinline__ uint64_t row_addr(const RowRef* e) {
+  uint64_t v;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"((uint32_t)__cvta_generic_to_shared(e)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void row_weight_flags(const RowRef* e, float& w, int& flags) {
+  uint32_t a, b;
+  asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];"
+               : "=r"(a), "=r"(b)
+               : "r"((uint32_t)__cvta_generic_to_shared(e) + 8)
+               : "memory");
+  w = __uint_as_float(a);
+  flags = (int)b;
+}
+
+// The rows of the 32 tokens of a warp are read from two lists, one per
+// half-warp: half h reads the rows of the tokens of lanes h, h + 2, ..., h + 30
+// in that order.  Returns where this lane's n rows start in its parity's list
+// and sets len to the length of the list that this lane's half reads.
+__device__ __forceinline__ int parity_offset(int n, int lane, int& len) {
+  int x = n;  // inclusive sum over the lanes of this lane's parity
+#pragma unroll
+  for (int s = 2; s < 32; s <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, s);
+    if (lane >= s) x += y;
+  }
+  len = __shfl_sync(0xffffffffu, x, 30 + (lane >> 4));
+  return x - n;
 }
 
 // Covering tiles of token i of batch*head bh in ascending tile order: their

@@ -108,37 +108,45 @@ __global__ void __launch_bounds__(kThreads) serve_update_kernel(const ReqDesc* _
   }
 }
 
-// The same update, a warp per 32 consecutive rows (as the merge kernels of
-// merge.cu): each lane resolves its row's request, head and token and lists
-// the row's covering tiles with their slots and window weights; half-warps
-// then update the rows two at a time, lane f of a half holding columns
-// [4 f, 4 f + 4) (and [4 f + 64, 4 f + 68) at d = 128, U = 2), so the per-tile
-// rows are read as contiguous runs and the geometry is resolved once per row
-// instead of once per 4 columns.  A pair's loads of all its covering rows
-// (at most MAXC) are issued before their weighted sum (ascending tile order):
-// the kernel is bound by how many loads are in flight.  The window table is
-// built from the first request's geometry; a row whose request differs in
-// core, halo, window or tiled dimensions evaluates its window directly.
+// The same update, a warp per 32 consecutive rows, organised like the forward
+// merge of merge.cu: each lane resolves its row's request, head and token and
+// lists what the row needs, in order -- its covering tiles' FP32 rows with
+// their window weights (or, for a token covered by one tile, the tile
+// kernel's BF16 output row with weight 1), then its BF16 state row, whose
+// entry carries 1 / sum of weights -- into one of two shared-memory lists
+// (parity_offset).  Half-warp h works through the rows of the tokens of lanes
+// h, h + 2, ..., R rows at a time with all R loads issued first, lane f of the
+// half holding columns [4 f, 4 f + 4) (and [4 f + 64, 4 f + 68) at d = 128,
+// U = 2); at a state row it forms a = (weighted sum) / (sum of weights) and
+// writes z + c (a - z) back.  The window table is built from the first
+// request's geometry; a row whose request differs in core, halo, window or
+// tiled dimensions evaluates its window directly.
 template <int MAXC, int U>
-__global__ void __launch_bounds__(kThreads, MAXC == 4 && U == 1 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, 2)
     serve_update_warp_kernel(const ReqDesc* __restrict__ reqs, const int64_t* __restrict__ counts, int d, float c) {
+  constexpr int R = 8 / U;
+  constexpr int W = kThreads / 32;
+  constexpr int NE = MAXC + 1;  // rows listed per token
   __shared__ float win[kWinMax];
+  __shared__ RowRef rows[W][2][16 * NE];
   const int nreq = (int)counts[0];
   if (nreq < 1) return;  // uniform over the grid: no request, no table
-  const int64_t rows = counts[2];
+  const int64_t nrows = counts[2];
   const Geom& g0 = reqs[0].g;
   const WinTable tbl = build_win_table(g0, win);
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * (kThreads / 32) * 32;
-  for (int64_t base = ((int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32; base < rows;
-       base += stride) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int f0 = lane & 15;
+  const int F4 = d / 4;
+  const int64_t stride = (int64_t)gridDim.x * W * 32;
+  const RowRef* list = rows[wid][lane >> 4];
+  for (int64_t base = ((int64_t)blockIdx.x * W + wid) * 32; base < nrows; base += stride) {
     const int64_t idx = base + lane;
     int r = -1, n = 0;
     int64_t local = 0;
-    int64_t slot[kMaxCover];
-    float w[kMaxCover];
+    int64_t slot[MAXC];
+    float w[MAXC];
     float wsum = 0.f;
-    if (idx < rows) {
+    if (idx < nrows) {
       r = find_request(reqs, nreq, idx);
       const Geom& g = reqs[r].g;
       local = idx - reqs[r].tok0;  // head * N + token
@@ -162,49 +170,91 @@ __global__ void __launch_bounds__(kThreads, MAXC == 4 && U == 1 ? 3 : 2)
           if (k < n) wsum += w[k];
       }
     }
-    for (int q = 0; q < 16; ++q) {
-      const int owner = 2 * q + (lane >> 4);
-      const int ro = __shfl_sync(0xffffffffu, r, owner);
-      const int nc = __shfl_sync(0xffffffffu, n, owner);
-      const int64_t lo = __shfl_sync(0xffffffffu, local, owner);
-      const float inv = 1.f / __shfl_sync(0xffffffffu, wsum, owner);
-      const int f0 = lane & 15;
-      const float* ot = ro >= 0 ? reqs[ro].ot : nullptr;
-      float4 o[MAXC][U];
-      float wc[MAXC];
+    const int cnt = r < 0 ? 0 : n == 0 ? 2 : n + 1;
+    int len;
+    RowRef* mine = rows[wid][lane & 1] + parity_offset(cnt, lane, len);
+    if (r >= 0) {
+      const ReqDesc& rq = reqs[r];
+      RowRef e;
+      if (n == 0) {
+        e.p = reinterpret_cast<const char*>(static_cast<const __nv_bfloat16*>(rq.out) + local * d) + 1;
+        e.w = 1.f;
+        e.flags = lane | kRowBf16;
+        mine[0] = e;
+      }
 #pragma unroll
-      for (int k = 0; k < MAXC; ++k) {
-        const int64_t sc = __shfl_sync(0xffffffffu, slot[k], owner);
-        wc[k] = __shfl_sync(0xffffffffu, w[k], owner);
+      for (int k = 0; k < MAXC; ++k)
+        if (k < n) {
+          e.p = rq.ot + slot[k] * d;
+          e.w = w[k];
+          e.flags = lane;
+          mine[k] = e;
+        }
+      e.p = reinterpret_cast<const char*>(rq.z + local * d) + 1;
+      e.w = n == 0 ? 1.f : 1.f / wsum;
+      e.flags = lane | kRowBf16 | kRowState;
+      mine[cnt - 1] = e;
+    }
+    __syncwarp();
+    const int lmax = max(len, __shfl_xor_sync(0xffffffffu, len, 16));
+    float4 acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int e0 = 0; e0 < lmax; e0 += R) {
+      const int nv = len - e0;  // rows of this half's list from e0 on
+      uint4 v[R][U];
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (j < nv) {
+          const uint64_t a = row_addr(list + e0 + j);
+          const bool bf = a & 1;  // BF16 rows are listed with the low address bit set
+          const void* p = reinterpret_cast<const void*>(a & ~(uint64_t)1);
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if (f0 + 16 * u >= F4) continue;
+            if (bf) {
+              const uint2 b = __ldg(static_cast<const uint2*>(p) + f0 + 16 * u);
+              v[j][u] = make_uint4(b.x, b.y, 0u, 0u);
+            } else {
+              v[j][u] = __ldg(static_cast<const uint4*>(p) + f0 + 16 * u);
+            }
+          }
+        }
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        if (j >= nv) break;
+        float wr;
+        int fl;
+        row_weight_flags(list + e0 + j, wr, fl);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          o[k][u] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (k < nc) o[k][u] = __ldg(reinterpret_cast<const float4*>(ot + sc * d) + f0 + 16 * u);
+          float4 x;
+          if (fl & kRowBf16) {
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v[j][u].x));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v[j][u].y));
+            x = make_float4(a.x, a.y, b.x, b.y);
+          } else {
+            x = make_float4(__uint_as_float(v[j][u].x), __uint_as_float(v[j][u].y), __uint_as_float(v[j][u].z),
+                            __uint_as_float(v[j][u].w));
+          }
+          if (fl & kRowState) {  // wr = 1 / sum of weights
+            const float4 a = make_float4(acc[u].x * wr, acc[u].y * wr, acc[u].z * wr, acc[u].w * wr);
+            const int f = f0 + 16 * u;
+            __nv_bfloat16* zrow = reinterpret_cast<__nv_bfloat16*>(row_addr(list + e0 + j) & ~(uint64_t)1);
+            if (f < F4)
+              store4<__nv_bfloat16>(zrow + 4 * f,
+                                    make_float4(fmaf(c, a.x - x.x, x.x), fmaf(c, a.y - x.y, x.y),
+                                                fmaf(c, a.z - x.z, x.z), fmaf(c, a.w - x.w, x.w)));
+            acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          } else {
+            acc[u] = make_float4(fmaf(wr, x.x, acc[u].x), fmaf(wr, x.y, acc[u].y), fmaf(wr, x.z, acc[u].z),
+                                 fmaf(wr, x.w, acc[u].w));
+          }
         }
-      }
-      if (ro < 0) continue;
-      const ReqDesc& rq = reqs[ro];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int f = f0 + 16 * u;
-        float4 att;
-        if (nc == 0) {
-          att = load4<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(rq.out) + lo * d + 4 * f);
-        } else {
-          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-          for (int k = 0; k < MAXC; ++k)
-            if (k < nc)
-              acc = make_float4(fmaf(wc[k], o[k][u].x, acc.x), fmaf(wc[k], o[k][u].y, acc.y), fmaf(wc[k], o[k][u].z, acc.z),
-                                fmaf(wc[k], o[k][u].w, acc.w));
-          att = make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv);
-        }
-        __nv_bfloat16* zp = rq.z + lo * d + 4 * f;
-        const float4 z = load4<__nv_bfloat16>(zp);
-        store4<__nv_bfloat16>(zp, make_float4(fmaf(c, att.x - z.x, z.x), fmaf(c, att.y - z.y, z.y),
-                                              fmaf(c, att.z - z.z, z.z), fmaf(c, att.w - z.w, z.w)));
       }
     }
+    __syncwarp();  // the lists are rewritten for the next 32 rows
   }
 }
 

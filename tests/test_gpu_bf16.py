@@ -38,6 +38,9 @@ FWD_CASES = [
     ("single_token_d128", 1, 1, 128, (1, 1, 1), (1, 1, 1), (0, 0, 0)),
     # one 1x8x48 tile = three 1x8x16 boxes: the second box of the last query pair is empty
     ("odd_box_count", 1, 2, 64, (1, 8, 48), (1, 8, 48), (0, 0, 0)),
+    # sum over dimensions of core + 2 halo = 2230, more than the merges' shared-memory
+    # window table holds: the merge kernels evaluate the window directly
+    ("window_direct", 1, 1, 64, (1, 1, 4200), (1, 1, 2100), (0, 0, 64)),
 ]
 
 
