@@ -43,13 +43,21 @@
 // elementwise math + epilogue: one TMEM lane = one box row, four warps per
 // lane quadrant, each taking 32 of the row's 128 columns (a warp reads its
 // scores with one load per operand and releases them at once; four warps per
-// SM sub-partition hide the TMEM and MUFU latencies).  Two issuing threads,
-// because a thread's shared-memory accesses (an mbarrier wait included) are
-// held until the tcgen05.mma it issued before them have drained from the
-// tensor pipe: with one issuer every wait between the two product groups
+// SM sub-partition hide the TMEM and MUFU latencies).  Several issuing
+// threads, because a thread's shared-memory accesses (an mbarrier wait
+// included) are held until the tcgen05.mma it issued before them have drained
+// from the tensor pipe: with one issuer every wait between two product groups
 // empties the pipe; with two, one thread's waits overlap the other's MMAs.
-// The tensor pipe interleaves the two streams; the barriers below order every
-// TMEM region and shared-memory stage they share.
+// The dQ kernel gives the dP chain a third issuer (warp 19), so that the next
+// box's S chain goes out as soon as the current S was read, whatever the dP
+// chain still has in the pipe (dQ kernel 313 -> 300 ms on the paper-regime
+// workload).  In the dK/dV kernel the same split measured slower (401 -> 430
+// ms): there the next S chain then overtakes the current dP chain, which the
+// math warps wait for, so one thread keeps issuing S, dP, S, dP in that order.
+// (The d = 128 dQ kernel, whose dP chain waits for the previous dQ product,
+// was slower with the split as well: 6.21 -> 6.45 s on the long-context case.)
+// The tensor pipe interleaves the threads' streams; the barriers below order
+// every TMEM region and shared-memory stage they share.
 #include "sm103_bwd_common.cuh"
 
 GATTN_DEFINE_STATUS(sm103_bwd64)
@@ -64,7 +72,9 @@ __device__ void set_status_bwd64(uint32_t c) { set_status(c); }
 constexpr int kD = 64;
 constexpr int kBox = 128 * kD * 2;  // one 128-token box of one operand, BF16, 16 KB
 constexpr int kMath64 = kMathW;      // math warps: 4 per TMEM lane quadrant
-constexpr int kThreads64 = kThreadsB;
+constexpr int kThreads64 = kThreadsB;  // dK/dV kernel
+constexpr int kIssuerD = kMath0 + kMath64;  // dQ kernel: issuer of the dP chain (after the math warps)
+constexpr int kThreadsQ64 = kThreadsB + 32;
 
 // =============================================================== dK / dV
 struct Kv64 {
@@ -401,8 +411,8 @@ struct Q64 {
   static constexpr int kBias = kOnes + 4096;
   static constexpr int kBar = kBias + kStages * 4096;
   // qd_full, qd_empty, qt_full, kv_full[S], kv_empty[S], s_full[2], s_empty[2], p_full[2], p_empty[2],
-  // acc_full, acc_empty, drain[2]   (s_*[0]: the S chain, s_*[1]: the dP chain)
-  static constexpr int kNumBars = 3 + 2 * kStages + 12;
+  // acc_full, acc_empty, drain[3]   (s_*[0]: the S chain, s_*[1]: the dP chain)
+  static constexpr int kNumBars = 3 + 2 * kStages + 13;
   static constexpr int kMisc = kBar + kNumBars * 8;
   static constexpr int kSmem = kMisc + 16 + 1024;
   // TMEM: S 0, dP 128, dS buffer 0 (packed) 256, dQ 320, Q (packed) 384, dOut (packed) 416, dS buffer 1 448
@@ -411,7 +421,7 @@ struct Q64 {
 };
 
 template <typename OutT>
-__global__ void __launch_bounds__(kThreads64, 1)
+__global__ void __launch_bounds__(kThreadsQ64, 1)
     dq64_kernel(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tk,
                 const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tdo, const BwdArgs a) {
   using C = Q64;
@@ -429,13 +439,13 @@ __global__ void __launch_bounds__(kThreads64, 1)
   uint64_t* p_empty = p_full + 2;   // [2]
   uint64_t* acc_full = p_empty + 2;
   uint64_t* acc_empty = acc_full + 1;
-  uint64_t* drain = acc_empty + 1;  // [2]: one per issuing thread
+  uint64_t* drain = acc_empty + 1;  // [3]: one per issuing thread
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kMisc + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   zero_pad_rows(smem, 2 + 2 * C::kStages, a.g.R);  // Q, dOut and the K / V ring
-  for (int r = threadIdx.x; r < (1 + C::kStages) * 256; r += kThreads64) {
+  for (int r = threadIdx.x; r < (1 + C::kStages) * 256; r += kThreadsQ64) {
     const int blk = r >> 8, rr = r & 255;
     const uint4 v = (blk == 0 && rr < 128) ? make_uint4(0x00003F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
     if (blk == 0 || rr >= 128) *reinterpret_cast<uint4*>(smem + C::kOnes + blk * 4096 + rr * 16) = v;
@@ -461,6 +471,7 @@ __global__ void __launch_bounds__(kThreads64, 1)
     mbar_init(acc_empty, kMath64);
     mbar_init(drain, 1);
     mbar_init(drain + 1, 1);
+    mbar_init(drain + 2, 1);
     *abort_flag = 0;
     fence_mbar_init();
     prefetch_tmap(&tq);
@@ -540,7 +551,7 @@ __global__ void __launch_bounds__(kThreads64, 1)
         if (kv_arm & (1u << s)) mbar_wait<set_status_bwd64>(kv_full + s, (kv_par >> s) & 1, abort_flag, false);
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ issuer of S, dP
+    // ------------------------------------------------------------ issuer of S
     if (lane == 0) {
       constexpr uint32_t idS = idesc_bf16(128, 128, 0);
       const uint64_t dK0 = sw128_desc(smem_u32(smem + C::kK), 16, 1024);
@@ -564,15 +575,40 @@ __global__ void __launch_bounds__(kThreads64, 1)
           if (!(ok = WAIT(kv_full + st, (G / C::kStages) & 1))) break;
           if (G > 0 && !(ok = WAIT(s_empty, (G - 1) & 1))) break;  // S of box G-1 read
           tc_fence_after();
-          const uint64_t dk = dmove(dK0, st * 2 * kBox), dv = dmove(dk, kBox);
+          const uint64_t dk = dmove(dK0, st * 2 * kBox);
 #pragma unroll
           for (int ks = 0; ks < kD / 16; ++ks)
             umma_bf16_ts(tmem + C::kColS, tmem + C::kColQ + ks * 8, dmove(dk, ks * 32), idS, ks > 0);
           // masked keys get -1e30, so P' = 0 there and dS = 0 follows
           if (masked) umma_bf16(tmem + C::kColS, dOnes, dmove(dBias0, st * 4096), idS, 1u);
           umma_commit(s_full);
+        }
+        ++W;
+      }
+      umma_commit(drain);
+      mbar_wait<set_status_bwd64>(drain, 0, abort_flag, false);
+    }
+  } else if (warp == kIssuerD) {
+    // ------------------------------------------------------------ issuer of dP (its own thread, as in
+    // the dK/dV kernel)
+    if (lane == 0) {
+      constexpr uint32_t idS = idesc_bf16(128, 128, 0);
+      const uint64_t dK0 = sw128_desc(smem_u32(smem + C::kK), 16, 1024);
+      uint32_t G = 0, W = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < a.items && ok; w += gridDim.x) {
+        int bh, tile, qb;
+        decode_item(g, w, bh, tile, qb);
+        TileBlocks tbk;
+        tile_blocks(g, tile, tbk);
+        if (qb >= tbk.NB) continue;
+        if (!(ok = WAIT(qt_full, W & 1))) break;  // Q, dOut in TMEM
+        for (int j = 0; j < tbk.NB; ++j, ++G) {
+          const uint32_t st = G % C::kStages;
+          if (!(ok = WAIT(kv_full + st, (G / C::kStages) & 1))) break;
           if (G > 0 && !(ok = WAIT(s_empty + 1, (G - 1) & 1))) break;  // dP of box G-1 read
           tc_fence_after();
+          const uint64_t dv = dmove(dK0, st * 2 * kBox + kBox);
 #pragma unroll
           for (int ks = 0; ks < kD / 16; ++ks)
             umma_bf16_ts(tmem + C::kColDP, tmem + C::kColDO + ks * 8, dmove(dv, ks * 32), idS, ks > 0);
@@ -580,8 +616,8 @@ __global__ void __launch_bounds__(kThreads64, 1)
         }
         ++W;
       }
-      umma_commit(drain);
-      mbar_wait<set_status_bwd64>(drain, 0, abort_flag, false);
+      umma_commit(drain + 2);
+      mbar_wait<set_status_bwd64>(drain + 2, 0, abort_flag, false);
     }
   } else if (warp == kIssuerA) {
     // ------------------------------------------------------------ issuer of dQ += dS K
@@ -752,7 +788,7 @@ cudaError_t run_bwd64(const Geom& g, const __nv_bfloat16* q, const __nv_bfloat16
   e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, Q64::kSmem);
   if (e != cudaSuccess) return e;
   prof_begin(kKBwdDq, st);
-  k2<<<grid, kThreads64, Q64::kSmem, st>>>(mq, mk, mv, mdo, a);
+  k2<<<grid, kThreadsQ64, Q64::kSmem, st>>>(mq, mk, mv, mdo, a);
   prof_end(kKBwdDq, st);
   return cudaGetLastError();
 }
