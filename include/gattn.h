@@ -187,8 +187,8 @@ gattn_status gattn_bwd(const gattn_desc *desc, const void *q, const void *k, con
  * merge-and-update launch, both captured in a CUDA graph that is replayed
  * every iteration; requests that finish are retired: their scratch goes back
  * to the server's memory pool and their final state stays in device memory
- * until the client takes it (gattn_serve_poll with a buffer) or drops it
- * (gattn_serve_release).  Unclaimed results count against hbm_budget; when
+ * until the client takes it (gattn_serve_poll with a buffer, or
+ * gattn_serve_take_async) or drops it (gattn_serve_release).  Unclaimed results count against hbm_budget; when
  * the head of the queue does not fit, the oldest unclaimed results are moved
  * to host memory first.  Results do not depend on which other requests share
  * an iteration (deterministic kernels).
@@ -251,8 +251,25 @@ gattn_status gattn_serve_step(gattn_server *s, int32_t *n_active, int32_t *n_wai
 gattn_status gattn_serve_poll(gattn_server *s, uint64_t id, int32_t *done, double *latency_s, void *result_host);
 /* Drops the final state of a finished request without copying it (its device
  * memory returns to the pool).  GATTN_ERR_INVALID_ARG if the request has not
- * finished, GATTN_ERR_NOT_FOUND for an unknown id. */
+ * finished, GATTN_ERR_NOT_FOUND for an unknown id or a result already taken
+ * or released. */
 gattn_status gattn_serve_release(gattn_server *s, uint64_t id);
+/* Takes the final state of a finished request without waiting for the copy:
+ * starts copying its nh*N*d BF16 values to `dst` (host memory, pinned for
+ * an asynchronous copy, or device memory) on a copy stream of the server and
+ * returns, so that the engine's next iterations run while the result moves.
+ * `dst` must stay valid and must not be read until gattn_serve_copied reports
+ * the copy complete; the result's device memory returns to the pool at the
+ * first gattn_serve_step or gattn_serve_copied after that.  A result can be
+ * taken once, by this call or by gattn_serve_poll.  Errors:
+ * GATTN_ERR_INVALID_ARG (NULL arguments, request not finished),
+ * GATTN_ERR_NOT_FOUND (unknown id, result already taken or released),
+ * GATTN_ERR_CUDA. */
+gattn_status gattn_serve_take_async(gattn_server *s, uint64_t id, void *dst);
+/* *copied = 1 once the result of `id` has been taken and its copy is complete
+ * (immediately for gattn_serve_poll, which copies before returning), else 0.
+ * GATTN_ERR_NOT_FOUND for an unknown id. */
+gattn_status gattn_serve_copied(gattn_server *s, uint64_t id, int32_t *copied);
 gattn_status gattn_serve_stats(gattn_server *s, gattn_serve_stats_t *out);
 void gattn_serve_destroy(gattn_server *s);
 

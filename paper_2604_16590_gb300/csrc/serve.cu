@@ -301,6 +301,7 @@ struct ServeRequest {
   double latency = -1.0;
   size_t held = 0;                // bytes of this request counted in hbm_in_use
   bool taken = false;             // the result was fetched or released
+  cudaEvent_t copied = nullptr;   // end of the result's asynchronous copy, while it is in flight
   std::vector<uint16_t> result;   // the result, once spilled to host memory
 };
 
@@ -315,6 +316,8 @@ struct gattn_server {
   std::vector<ServeRequest*> active;
   std::deque<ServeRequest*> finished;  // retired, result possibly still in device memory
   cudaMemPool_t pool = nullptr;        // request memory (kept by the pool between requests)
+  cudaStream_t copy_stream = nullptr;  // asynchronous result copies (gattn_serve_take_async)
+  std::vector<ServeRequest*> copying;  // results whose asynchronous copy may still be in flight
   std::unordered_map<uint64_t, ServeRequest*> all;
   ReqDesc* d_reqs = nullptr;
   int64_t* d_counts = nullptr;
@@ -388,6 +391,24 @@ static void release(gattn_server* s, ServeRequest* r) {
   r->held = 0;
 }
 
+// Results whose asynchronous copy has completed give their device memory
+// back to the pool; with `wait`, every copy in flight is waited for first.
+static void reap(gattn_server* s, bool wait = false) {
+  std::vector<ServeRequest*> still;
+  for (ServeRequest* r : s->copying) {
+    const cudaError_t e = wait ? cudaEventSynchronize(r->copied) : cudaEventQuery(r->copied);
+    if (e == cudaErrorNotReady) {
+      still.push_back(r);
+      continue;
+    }
+    if (e != cudaSuccess) cudaGetLastError();  // a failed copy still ends: nothing is in flight
+    cudaEventDestroy(r->copied);
+    r->copied = nullptr;
+    release(s, r);
+  }
+  s->copying.swap(still);
+}
+
 // Moves the result of a retired request from device to host memory (when
 // waiting requests need the budget and its client has not fetched it yet).
 static bool spill(gattn_server* s, ServeRequest* r) {
@@ -446,7 +467,8 @@ gattn_status gattn_serve_create(const gattn_serve_cfg* cfg, gattn_stream_t strea
             cudaMalloc(&s->d_counts, 4 * sizeof(int64_t)) == cudaSuccess &&
             cudaMallocHost(&s->h_reqs, sizeof(ReqDesc) * cfg->max_active) == cudaSuccess &&
             cudaMallocHost(&s->h_counts, 4 * sizeof(int64_t)) == cudaSuccess &&
-            cudaEventCreate(&s->ev0) == cudaSuccess && cudaEventCreate(&s->ev1) == cudaSuccess;
+            cudaEventCreate(&s->ev0) == cudaSuccess && cudaEventCreate(&s->ev1) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
   if (!ok) {
     gattn_serve_destroy(s);
     return GATTN_ERR_CUDA;
@@ -492,6 +514,7 @@ gattn_status gattn_serve_submit(gattn_server* s, const gattn_request* req, uint6
 
 gattn_status gattn_serve_step(gattn_server* s, int32_t* n_active, int32_t* n_waiting) {
   if (!s) return GATTN_ERR_INVALID_ARG;
+  reap(s);  // results copied out since the last iteration free their memory
   // ---- admission: arrival order, slot limit, HBM budget (head of line waits)
   while (!s->waiting.empty() && (int)s->active.size() < s->cfg.max_active) {
     ServeRequest* r = s->waiting.front();
@@ -500,7 +523,7 @@ gattn_status gattn_serve_step(gattn_server* s, int32_t* n_active, int32_t* n_wai
     while (s->hbm_in_use + r->bytes > s->cfg.hbm_budget && !s->finished.empty()) {
       ServeRequest* f = s->finished.front();
       s->finished.pop_front();
-      if (f->z && !spill(s, f)) return GATTN_ERR_CUDA;
+      if (f->z && !f->taken && !spill(s, f)) return GATTN_ERR_CUDA;
     }
     if (s->hbm_in_use + r->bytes > s->cfg.hbm_budget) break;
     const Geom& g = r->g;
@@ -656,10 +679,52 @@ gattn_status gattn_serve_release(gattn_server* s, uint64_t id) {
   if (it == s->all.end()) return GATTN_ERR_NOT_FOUND;
   ServeRequest* r = it->second;
   if (r->latency < 0.0) return GATTN_ERR_INVALID_ARG;  // not finished (or rejected)
+  if (r->taken) return GATTN_ERR_NOT_FOUND;             // taken or released already
   if (r->z) release(s, r);
   r->result.clear();
   r->result.shrink_to_fit();
   r->taken = true;
+  return GATTN_OK;
+}
+
+gattn_status gattn_serve_take_async(gattn_server* s, uint64_t id, void* dst) {
+  if (!s || !dst) return GATTN_ERR_INVALID_ARG;
+  auto it = s->all.find(id);
+  if (it == s->all.end()) return GATTN_ERR_NOT_FOUND;
+  ServeRequest* r = it->second;
+  if (r->latency < 0.0) return GATTN_ERR_INVALID_ARG;  // not finished (or rejected)
+  if (r->taken) return GATTN_ERR_NOT_FOUND;
+  const size_t nd = (size_t)r->g.nh * r->g.N * r->g.d;
+  if (!r->z) {  // spilled to host memory: copied at once
+    memcpy(dst, r->result.data(), nd * 2);
+    r->result.clear();
+    r->result.shrink_to_fit();
+    r->taken = true;
+    return GATTN_OK;
+  }
+  // the copy stream starts after everything the server's stream holds so far
+  // (the iteration that wrote the final state included)
+  if (cudaEventCreateWithFlags(&r->copied, cudaEventDisableTiming) != cudaSuccess) return GATTN_ERR_CUDA;
+  if (cudaEventRecord(r->copied, s->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(s->copy_stream, r->copied, 0) != cudaSuccess ||
+      cudaMemcpyAsync(dst, r->z, nd * 2, cudaMemcpyDefault, s->copy_stream) != cudaSuccess ||
+      cudaEventRecord(r->copied, s->copy_stream) != cudaSuccess) {
+    cudaStreamSynchronize(s->copy_stream);
+    cudaEventDestroy(r->copied);
+    r->copied = nullptr;
+    return GATTN_ERR_CUDA;
+  }
+  r->taken = true;
+  s->copying.push_back(r);
+  return GATTN_OK;
+}
+
+gattn_status gattn_serve_copied(gattn_server* s, uint64_t id, int32_t* copied) {
+  if (!s || !copied) return GATTN_ERR_INVALID_ARG;
+  auto it = s->all.find(id);
+  if (it == s->all.end()) return GATTN_ERR_NOT_FOUND;
+  reap(s);
+  *copied = it->second->taken && !it->second->copied ? 1 : 0;
   return GATTN_OK;
 }
 
@@ -700,6 +765,7 @@ gattn_status gattn_serve_stats(gattn_server* s, gattn_serve_stats_t* out) {
 void gattn_serve_destroy(gattn_server* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
+  reap(s, true);
   for (auto& kv : s->all) {
     release(s, kv.second);
     delete kv.second;
@@ -713,6 +779,7 @@ void gattn_serve_destroy(gattn_server* s) {
   if (s->h_counts) cudaFreeHost(s->h_counts);
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->own_stream) cudaStreamDestroy(s->stream);
   delete s;
 }

@@ -175,6 +175,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             ctypes.c_int,
         ),
         "gattn_serve_release": ([P, ctypes.c_uint64], ctypes.c_int),
+        "gattn_serve_take_async": ([P, ctypes.c_uint64, P], ctypes.c_int),
+        "gattn_serve_copied": ([P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "gattn_serve_stats": ([P, ctypes.POINTER(gattn_serve_stats_t)], ctypes.c_int),
         "gattn_serve_destroy": ([P], None),
         "gattn_linear_workspace_bytes": ([ctypes.POINTER(gattn_linear_desc)], S),
@@ -454,6 +456,17 @@ def gattn_serve_release(server, rid) -> int:
     return load_library().gattn_serve_release(server, ctypes.c_uint64(rid))
 
 
+def gattn_serve_take_async(server, rid, dst) -> int:
+    return load_library().gattn_serve_take_async(server, ctypes.c_uint64(rid), _ptr(dst))
+
+
+def gattn_serve_copied(server, rid):
+    """Returns (status, copied)."""
+    c = ctypes.c_int32()
+    st = load_library().gattn_serve_copied(server, ctypes.c_uint64(rid), ctypes.byref(c))
+    return st, bool(c.value)
+
+
 def gattn_serve_stats(server) -> gattn_serve_stats_t:
     out = gattn_serve_stats_t()
     check(load_library().gattn_serve_stats(server, ctypes.byref(out)), "gattn_serve_stats")
@@ -486,6 +499,7 @@ class Server:
         st, self.h = gattn_serve_create(cfg, stream)
         check(st, "gattn_serve_create")
         self._keep = {}
+        self._numel = {}  # result size of each submitted request
 
     def submit(self, z0: torch.Tensor) -> int:
         nh, N, d = z0.shape
@@ -499,6 +513,7 @@ class Server:
         check(st, "gattn_serve_submit")
         if z0.is_cuda:
             self._keep[rid] = z0  # read at admission
+        self._numel[rid] = z0.numel()
         return rid
 
     def step(self):
@@ -516,6 +531,8 @@ class Server:
             return None, None
         if out is None:
             out = torch.empty(shape, dtype=torch.bfloat16)
+        if out.dtype != torch.bfloat16 or not out.is_contiguous() or out.numel() != self._numel.get(rid, out.numel()):
+            raise ValueError("result: out must be a contiguous BF16 tensor of the request's size")
         st, done, lat = gattn_serve_poll(self.h, rid, out)
         check(st, "gattn_serve_poll")
         self._keep.pop(rid, None)
@@ -524,6 +541,20 @@ class Server:
     def release(self, rid):
         """Drops the final state of a finished request without copying it."""
         check(gattn_serve_release(self.h, rid), "gattn_serve_release")
+
+    def take_async(self, rid, out):
+        """Starts copying the final state of a finished request into `out` (a
+        BF16 tensor, pinned host or device memory) and returns; `out` holds the
+        result once copied(rid) is True."""
+        if out.dtype != torch.bfloat16 or not out.is_contiguous() or out.numel() != self._numel.get(rid, -1):
+            raise ValueError("take_async: out must be a contiguous BF16 tensor of the request's size")
+        check(gattn_serve_take_async(self.h, rid, out), "gattn_serve_take_async")
+        self._keep.pop(rid, None)
+
+    def copied(self, rid) -> bool:
+        st, c = gattn_serve_copied(self.h, rid)
+        check(st, "gattn_serve_copied")
+        return c
 
     def done(self, rid) -> bool:
         st, done, _ = gattn_serve_poll(self.h, rid, None)

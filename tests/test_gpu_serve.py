@@ -8,6 +8,8 @@ and in a mix, admission under the HBM budget and the slot limit (unclaimed
 results moved to host memory to make room), results taken once or released,
 statistics.
 """
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -196,3 +198,50 @@ def test_results_are_taken_once_and_release_frees_memory():
                 srv.step()
             ref, _ = srv.result(rid, z0.shape)
         assert torch.equal(ref, got)
+
+
+def test_asynchronous_take_overlaps_the_next_iterations():
+    """gattn_serve_take_async: the copy runs on the server's copy stream while
+    the engine keeps stepping; once copied() the tensor holds the same bytes
+    as a synchronous take, and the result's memory has gone back to the pool."""
+    specs = [ServeRequestSpec(0.0, 2, 2, 700 + i) for i in range(2)] + [ServeRequestSpec(0.0, 4, 2, 702)]
+    states = [request_state(sp, Y, X, D) for sp in specs]
+    with gattn.Server(_cfg(steps=2)) as srv:
+        ids = [srv.submit(z) for z in states[:2]]
+        while not all(srv.done(r) for r in ids):
+            srv.step()
+        late = srv.submit(states[2])  # still running while the first results move
+        host = torch.empty(states[0].shape, dtype=torch.bfloat16, pin_memory=True)
+        dev = torch.empty(states[1].shape, dtype=torch.bfloat16, device="cuda")
+        with pytest.raises(ValueError):
+            srv.take_async(ids[0], torch.empty(3, dtype=torch.bfloat16, pin_memory=True))  # wrong size
+        srv.take_async(ids[0], host)
+        srv.take_async(ids[1], dev)
+        with pytest.raises(gattn.GattnError) as e:
+            srv.take_async(ids[0], host)  # already taken
+        assert e.value.status == 9
+        with pytest.raises(gattn.GattnError) as e:
+            srv.release(ids[1])  # taken: its copy may be in flight
+        assert e.value.status == 9
+        with pytest.raises(gattn.GattnError) as e:
+            srv.take_async(late, torch.empty(states[2].shape, dtype=torch.bfloat16, pin_memory=True))  # not finished
+        assert e.value.status == 1
+        while not srv.done(late):
+            srv.step()
+        t0 = time.monotonic()
+        for r in ids:
+            while not srv.copied(r):
+                assert time.monotonic() - t0 < 30, "asynchronous copy did not complete"
+                time.sleep(0.001)
+        late_state, _ = srv.result(late, states[2].shape)
+        assert srv.copied(late)
+        assert srv.stats().hbm_in_use == 0
+        got = [host.clone(), dev.cpu()]
+    for z0, g in zip(states[:2], got):
+        with gattn.Server(_cfg(steps=2)) as srv:
+            rid = srv.submit(z0)
+            while not srv.done(rid):
+                srv.step()
+            ref, _ = srv.result(rid, z0.shape)
+        assert torch.equal(ref, g)
+    assert late_state is not None and torch.isfinite(late_state.float()).all()
