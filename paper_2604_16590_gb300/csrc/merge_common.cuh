@@ -122,6 +122,21 @@ __device__ __forceinline__ int parity_offset(int n, int lane, int& len) {
   return x - n;
 }
 
+// The same with four lists, one per quarter-warp: quarter q reads the rows
+// of the tokens of lanes q, q + 4, ..., q + 28.  Returns where this lane's n
+// rows start in its list and sets len to the length of the list that this
+// lane's quarter reads.
+__device__ __forceinline__ int group_offset(int n, int lane, int& len) {
+  int x = n;  // inclusive sum over the lanes of this lane's residue mod 4
+#pragma unroll
+  for (int s = 4; s < 32; s <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, s);
+    if (lane >= s) x += y;
+  }
+  len = __shfl_sync(0xffffffffu, x, 28 + (lane >> 3));
+  return x - n;
+}
+
 // Covering tiles of token i of batch*head bh in ascending tile order: their
 // slots and weights (the first NC of them).  Returns the count (0 for a token
 // covered by one tile).

@@ -109,36 +109,39 @@ __global__ void __launch_bounds__(kThreads) serve_update_kernel(const ReqDesc* _
 }
 
 // The same update, a warp per 32 consecutive rows, organised like the forward
-// merge of merge.cu: each lane resolves its row's request, head and token and
-// lists what the row needs, in order -- its covering tiles' FP32 rows with
-// their window weights (or, for a token covered by one tile, the tile
-// kernel's BF16 output row with weight 1), then its BF16 state row, whose
-// entry carries 1 / sum of weights -- into one of two shared-memory lists
-// (parity_offset).  Half-warp h works through the rows of the tokens of lanes
-// h, h + 2, ..., R rows at a time with all R loads issued first, lane f of the
-// half holding columns [4 f, 4 f + 4) (and [4 f + 64, 4 f + 68) at d = 128,
-// U = 2); at a state row it forms a = (weighted sum) / (sum of weights) and
-// writes z + c (a - z) back.  The window table is built from the first
-// request's geometry; a row whose request differs in core, halo, window or
-// tiled dimensions evaluates its window directly.
+// merge of merge.cu but with a quarter-warp per row: each lane resolves its
+// row's request, head and token and lists what the row needs, in order -- its
+// covering tiles' FP32 rows with their window weights (or, for a token covered
+// by one tile, the tile kernel's BF16 output row with weight 1), then its BF16
+// state row, whose entry carries 1 / sum of weights -- into one of four
+// shared-memory lists (group_offset): quarter-warp q works through the rows of
+// the tokens of lanes q, q + 4, ..., R rows at a time with all R loads issued
+// first, lane f of the quarter holding columns [8 f, 8 f + 8) (32 bytes of an
+// FP32 row, 16 of a BF16 row; and [8 f + 64, 8 f + 72) at d = 128, U = 2).
+// Eight lanes per row instead of sixteen halve the list reads, address and
+// flag work per byte moved, which bound the half-warp form.  At a state row it
+// forms a = (weighted sum) / (sum of weights) and writes z + c (a - z) back.
+// The window table is built from the first request's geometry; a row whose
+// request differs in core, halo, window or tiled dimensions evaluates its
+// window directly.
 template <int MAXC, int U>
 __global__ void __launch_bounds__(kThreads, 2)
     serve_update_warp_kernel(const ReqDesc* __restrict__ reqs, const int64_t* __restrict__ counts, int d, float c) {
-  constexpr int R = 8 / U;
+  constexpr int R = 4 / U;
   constexpr int W = kThreads / 32;
   constexpr int NE = MAXC + 1;  // rows listed per token
   __shared__ float win[kWinMax];
-  __shared__ RowRef rows[W][2][16 * NE];
+  __shared__ RowRef rows[W][4][8 * NE];
   const int nreq = (int)counts[0];
   if (nreq < 1) return;  // uniform over the grid: no request, no table
   const int64_t nrows = counts[2];
   const Geom& g0 = reqs[0].g;
   const WinTable tbl = build_win_table(g0, win);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int f0 = lane & 15;
-  const int F4 = d / 4;
+  const int f8 = lane & 7;
+  const int F8 = d / 8;  // 8-column units of a row: 4, 8 or 16
   const int64_t stride = (int64_t)gridDim.x * W * 32;
-  const RowRef* list = rows[wid][lane >> 4];
+  const RowRef* list = rows[wid][lane >> 3];
   for (int64_t base = ((int64_t)blockIdx.x * W + wid) * 32; base < nrows; base += stride) {
     const int64_t idx = base + lane;
     int r = -1, n = 0;
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     const int cnt = r < 0 ? 0 : n == 0 ? 2 : n + 1;
     int len;
-    RowRef* mine = rows[wid][lane & 1] + parity_offset(cnt, lane, len);
+    RowRef* mine = rows[wid][lane & 3] + group_offset(cnt, lane, len);
     if (r >= 0) {
       const ReqDesc& rq = reqs[r];
       RowRef e;
@@ -196,14 +199,17 @@ __global__ void __launch_bounds__(kThreads, 2)
       mine[cnt - 1] = e;
     }
     __syncwarp();
-    const int lmax = max(len, __shfl_xor_sync(0xffffffffu, len, 16));
-    float4 acc[U];
+    int lmax = max(len, __shfl_xor_sync(0xffffffffu, len, 8));
+    lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, 16));
+    float acc[U][8];
 #pragma unroll
-    for (int u = 0; u < U; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[u][e] = 0.f;
 #pragma unroll 1
     for (int e0 = 0; e0 < lmax; e0 += R) {
-      const int nv = len - e0;  // rows of this half's list from e0 on
-      uint4 v[R][U];
+      const int nv = len - e0;  // rows of this quarter's list from e0 on
+      uint4 v[R][U][2];
 #pragma unroll
       for (int j = 0; j < R; ++j)
         if (j < nv) {
@@ -212,12 +218,13 @@ __global__ void __launch_bounds__(kThreads, 2)
           const void* p = reinterpret_cast<const void*>(a & ~(uint64_t)1);
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            if (f0 + 16 * u >= F4) continue;
+            const int col8 = f8 + 8 * u;
+            if (col8 >= F8) continue;
             if (bf) {
-              const uint2 b = __ldg(static_cast<const uint2*>(p) + f0 + 16 * u);
-              v[j][u] = make_uint4(b.x, b.y, 0u, 0u);
+              v[j][u][0] = __ldg(static_cast<const uint4*>(p) + col8);
             } else {
-              v[j][u] = __ldg(static_cast<const uint4*>(p) + f0 + 16 * u);
+              v[j][u][0] = __ldg(static_cast<const uint4*>(p) + 2 * col8);
+              v[j][u][1] = __ldg(static_cast<const uint4*>(p) + 2 * col8 + 1);
             }
           }
         }
@@ -227,29 +234,45 @@ __global__ void __launch_bounds__(kThreads, 2)
         float wr;
         int fl;
         row_weight_flags(list + e0 + j, wr, fl);
+        __nv_bfloat16* zrow =
+            (fl & kRowState) ? reinterpret_cast<__nv_bfloat16*>(row_addr(list + e0 + j) & ~(uint64_t)1) : nullptr;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          float4 x;
+          float x[8];
           if (fl & kRowBf16) {
-            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v[j][u].x));
-            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v[j][u].y));
-            x = make_float4(a.x, a.y, b.x, b.y);
+            const uint32_t q[4] = {v[j][u][0].x, v[j][u][0].y, v[j][u][0].z, v[j][u][0].w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q[h]));
+              x[2 * h] = f.x;
+              x[2 * h + 1] = f.y;
+            }
           } else {
-            x = make_float4(__uint_as_float(v[j][u].x), __uint_as_float(v[j][u].y), __uint_as_float(v[j][u].z),
-                            __uint_as_float(v[j][u].w));
+            x[0] = __uint_as_float(v[j][u][0].x);
+            x[1] = __uint_as_float(v[j][u][0].y);
+            x[2] = __uint_as_float(v[j][u][0].z);
+            x[3] = __uint_as_float(v[j][u][0].w);
+            x[4] = __uint_as_float(v[j][u][1].x);
+            x[5] = __uint_as_float(v[j][u][1].y);
+            x[6] = __uint_as_float(v[j][u][1].z);
+            x[7] = __uint_as_float(v[j][u][1].w);
           }
           if (fl & kRowState) {  // wr = 1 / sum of weights
-            const float4 a = make_float4(acc[u].x * wr, acc[u].y * wr, acc[u].z * wr, acc[u].w * wr);
-            const int f = f0 + 16 * u;
-            __nv_bfloat16* zrow = reinterpret_cast<__nv_bfloat16*>(row_addr(list + e0 + j) & ~(uint64_t)1);
-            if (f < F4)
-              store4<__nv_bfloat16>(zrow + 4 * f,
-                                    make_float4(fmaf(c, a.x - x.x, x.x), fmaf(c, a.y - x.y, x.y),
-                                                fmaf(c, a.z - x.z, x.z), fmaf(c, a.w - x.w, x.w)));
-            acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int col8 = f8 + 8 * u;
+            uint32_t o[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const float a0 = acc[u][2 * h] * wr, a1 = acc[u][2 * h + 1] * wr;
+              const __nv_bfloat162 b =
+                  __floats2bfloat162_rn(fmaf(c, a0 - x[2 * h], x[2 * h]), fmaf(c, a1 - x[2 * h + 1], x[2 * h + 1]));
+              o[h] = *reinterpret_cast<const uint32_t*>(&b);
+            }
+            if (col8 < F8) *(reinterpret_cast<uint4*>(zrow) + col8) = make_uint4(o[0], o[1], o[2], o[3]);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[u][e] = 0.f;
           } else {
-            acc[u] = make_float4(fmaf(wr, x.x, acc[u].x), fmaf(wr, x.y, acc[u].y), fmaf(wr, x.z, acc[u].z),
-                                 fmaf(wr, x.w, acc[u].w));
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[u][e] = fmaf(wr, x[e], acc[u][e]);
           }
         }
       }
