@@ -116,6 +116,14 @@ def test_serve_request_bytes_on_host(lib):
     assert gattn.gattn_serve_request_bytes(cfg, 2 * T, nh) > b
 
 
+def test_serve_entry_points_refuse_null_on_the_host(lib):
+    """The serving calls check their handle and pointers before any CUDA call."""
+    assert gattn.gattn_serve_take_async(None, 1, None) == 1
+    assert gattn.gattn_serve_copied(None, 1)[0] == 1
+    assert gattn.gattn_serve_release(None, 1) == 1
+    assert gattn.gattn_serve_poll(None, 1)[0] == 1
+
+
 def test_compress_validation_on_the_host(lib):
     """Temporal-compression descriptors and pointers are checked before any launch."""
     d = gattn.gattn_compress_desc()
