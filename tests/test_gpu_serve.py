@@ -72,6 +72,25 @@ def test_one_step_matches_oracle_d128_mixed_requests():
         assert_close(f"serve128/T{sp.T}", z1.double().numpy()[None], ref[None], 2e-2, 3e-3)
 
 
+@pytest.mark.parametrize("d", [64, 128])
+def test_one_step_with_a_temporal_halo_matches_oracle(d):
+    """Tiles of two frames with a one-frame halo: up to eight tiles cover a
+    token, so the merge-and-update takes its eight-cover form."""
+    core, halo = (2, 16, 16), (1, 4, 4)
+    spec = ServeRequestSpec(0.0, 5, 2, 91)
+    z0 = request_state(spec, Y, X, d)
+    with gattn.Server(_cfg(d=d, steps=1, core=core, halo=halo)) as srv:
+        rid = srv.submit(z0)
+        while not srv.done(rid):
+            srv.step()
+        z1, _ = srv.result(rid, z0.shape)
+    geo = oracle.Geometry(1, spec.nh, d, spec.T, Y, X, core, halo)
+    z = z0.double().numpy()[None]
+    att = oracle.forward(geo, z, z, z)[0]
+    ref = z[0] + 0.5 * (att - z[0])
+    assert_close(f"serve_thalo/d{d}", z1.double().numpy()[None], ref[None], 2e-2, 3e-3)
+
+
 @pytest.mark.parametrize("use_graph", [True, False], ids=["graph", "direct"])
 def test_result_is_identical_alone_and_in_a_mix(use_graph):
     a = ServeRequestSpec(0.0, 3, 2, 101)
