@@ -182,52 +182,98 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // Input gradients of multiply-covered tokens, organised like
-// merge_fwd_warp_kernel: ascending-tile sums of the FP32 per-tile gradients.
-template <typename OutT>
-__global__ void __launch_bounds__(kThreads, 4) merge_bwd_warp_kernel(Geom g, const float* __restrict__ dq_s,
+// merge_fwd_warp_kernel: each lane lists its token's covering slots in one of
+// two shared-memory lists, and each half-warp reads the dQ, dK and dV rows of
+// its list R slots at a time, all loads first, summing each token's per-tile
+// gradients in ascending tile order.
+template <typename OutT, int MAXC, int U>
+__global__ void __launch_bounds__(kThreads, 2) merge_bwd_warp_kernel(Geom g, const float* __restrict__ dq_s,
                                                                   const float* __restrict__ dk_s,
                                                                   const float* __restrict__ dv_s, OutT* __restrict__ dq,
                                                                   OutT* __restrict__ dk, OutT* __restrict__ dv) {
+  constexpr int R = 4 / U;
+  constexpr int W = kThreads / 32;
   __shared__ float win[kWinMax];
+  __shared__ RowRef rows[W][2][16 * MAXC];
   const WinTable tbl = build_win_table(g, win);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int f0 = lane & 15;
   const int64_t total = (int64_t)g.B * g.nh * g.N;
   const int F4 = g.d / 4;
-  const int64_t stride = (int64_t)gridDim.x * (kThreads / 32) * 32;
-  for (int64_t base = ((int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32; base < total;
-       base += stride) {
+  const int64_t stride = (int64_t)gridDim.x * W * 32;
+  const RowRef* list = rows[wid][lane >> 4];
+  for (int64_t base = ((int64_t)blockIdx.x * W + wid) * 32; base < total; base += stride) {
     const int64_t idx = base + lane;
-    int64_t slot[kMaxCover];
-    float w[kMaxCover];
-    const int n = idx < total ? token_covers(g, tbl, (int)(idx / g.N), idx % g.N, slot, w) : 0;
-    for (int q = 0; q < 16; ++q) {
-      const int owner = 2 * q + (lane >> 4);
-      const int nc = __shfl_sync(0xffffffffu, n, owner);
-      const int ncmax = max(nc, __shfl_xor_sync(0xffffffffu, nc, 16));
-      if (ncmax == 0) continue;
-      for (int f = lane & 15; f - (lane & 15) < F4; f += 16) {  // one or two 16-byte columns per lane
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, e = a;
+    int64_t slot[MAXC];
+    float w[MAXC];
+    int n = 0;
+    if (idx < total) {
+      n = token_covers(g, tbl, (int)(idx / g.N), idx % g.N, slot, w);
+      if (n > MAXC) {  // the host chose MAXC from the largest cover count
+        set_status(kStatusBounds);
+        n = 0;
+      }
+    }
+    int len;
+    RowRef* mine = rows[wid][lane & 1] + parity_offset(n, lane, len);
 #pragma unroll
-        for (int c = 0; c < kMaxCover; ++c) {
-          if (c >= ncmax) break;
-          const int64_t off = __shfl_sync(0xffffffffu, slot[c], owner) * g.d;
-          if (c < nc && f < F4) {
-            const float4 x = __ldg(reinterpret_cast<const float4*>(dq_s + off) + f);
-            const float4 y = __ldg(reinterpret_cast<const float4*>(dk_s + off) + f);
-            const float4 z = __ldg(reinterpret_cast<const float4*>(dv_s + off) + f);
-            a.x += x.x; a.y += x.y; a.z += x.z; a.w += x.w;
-            b.x += y.x; b.y += y.y; b.z += y.z; b.w += y.w;
-            e.x += z.x; e.y += z.y; e.z += z.z; e.w += z.w;
-          }
+    for (int c = 0; c < MAXC; ++c)
+      if (c < n) {
+        RowRef e;
+        e.p = reinterpret_cast<const void*>(slot[c] * g.d);  // element offset of the slot's rows
+        e.w = 0.f;
+        e.flags = lane | (c == n - 1 ? kRowLast : 0);
+        mine[c] = e;
+      }
+    __syncwarp();
+    const int lmax = max(len, __shfl_xor_sync(0xffffffffu, len, 16));
+    float4 a[U], b[U], e[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] = b[u] = e[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int e0 = 0; e0 < lmax; e0 += R) {
+      const int nv = len - e0;  // rows of this half's list from e0 on
+      float4 x[R][U], y[R][U], z[R][U];
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (j < nv) {
+          const int64_t off = (int64_t)row_addr(list + e0 + j);
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (f0 + 16 * u < F4) {
+              x[j][u] = __ldg(reinterpret_cast<const float4*>(dq_s + off) + f0 + 16 * u);
+              y[j][u] = __ldg(reinterpret_cast<const float4*>(dk_s + off) + f0 + 16 * u);
+              z[j][u] = __ldg(reinterpret_cast<const float4*>(dv_s + off) + f0 + 16 * u);
+            }
         }
-        if (nc > 0 && f < F4) {
-          const int64_t o = (base + owner) * g.d + 4 * f;
-          store4<OutT>(dq + o, a);
-          store4<OutT>(dk + o, b);
-          store4<OutT>(dv + o, e);
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        if (j >= nv) break;
+        float wr;
+        int fl;
+        row_weight_flags(list + e0 + j, wr, fl);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          a[u].x += x[j][u].x; a[u].y += x[j][u].y; a[u].z += x[j][u].z; a[u].w += x[j][u].w;
+          b[u].x += y[j][u].x; b[u].y += y[j][u].y; b[u].z += y[j][u].z; b[u].w += y[j][u].w;
+          e[u].x += z[j][u].x; e[u].y += z[j][u].y; e[u].z += z[j][u].z; e[u].w += z[j][u].w;
+        }
+        if (fl & kRowLast) {
+          const int64_t o0 = (base + (fl & 31)) * g.d;
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int f = f0 + 16 * u;
+            if (f < F4) {
+              store4<OutT>(dq + o0 + 4 * f, a[u]);
+              store4<OutT>(dk + o0 + 4 * f, b[u]);
+              store4<OutT>(dv + o0 + 4 * f, e[u]);
+            }
+            a[u] = b[u] = e[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
         }
       }
     }
+    __syncwarp();  // the lists are rewritten for the next 32 tokens
   }
 }
 
@@ -471,12 +517,27 @@ cudaError_t launch_bwd_prep(const Geom& g, const void* out, int out_dtype, const
 cudaError_t launch_merge_bwd(const Geom& g, const float* dq_s, const float* dk_s, const float* dv_s, void* dq,
                              void* dk, void* dv, int out_dtype, cudaStream_t st) {
   using bf = __nv_bfloat16;
-  if (max_covers(g) <= kMaxCover) {
+  const int mc = max_covers(g);
+  if (mc <= kMaxCover) {
     const unsigned grid = grid_warp((int64_t)g.B * g.nh * g.N);
-    if (out_dtype == GATTN_BF16)
-      merge_bwd_warp_kernel<bf><<<grid, kThreads, 0, st>>>(g, dq_s, dk_s, dv_s, (bf*)dq, (bf*)dk, (bf*)dv);
-    else
-      merge_bwd_warp_kernel<float><<<grid, kThreads, 0, st>>>(g, dq_s, dk_s, dv_s, (float*)dq, (float*)dk, (float*)dv);
+    const bool b16 = out_dtype == GATTN_BF16, wide = g.d > 64;
+#define GATTN_MERGE_BWD(MC)                                                                                      \
+  if (b16)                                                                                                       \
+    wide ? merge_bwd_warp_kernel<bf, MC, 2><<<grid, kThreads, 0, st>>>(g, dq_s, dk_s, dv_s, (bf*)dq, (bf*)dk, (bf*)dv) \
+         : merge_bwd_warp_kernel<bf, MC, 1><<<grid, kThreads, 0, st>>>(g, dq_s, dk_s, dv_s, (bf*)dq, (bf*)dk, (bf*)dv); \
+  else                                                                                                           \
+    wide ? merge_bwd_warp_kernel<float, MC, 2><<<grid, kThreads, 0, st>>>(g, dq_s, dk_s, dv_s, (float*)dq, (float*)dk, \
+                                                                          (float*)dv)                            \
+         : merge_bwd_warp_kernel<float, MC, 1><<<grid, kThreads, 0, st>>>(g, dq_s, dk_s, dv_s, (float*)dq, (float*)dk, \
+                                                                          (float*)dv);
+    if (mc <= 2) {
+      GATTN_MERGE_BWD(2)
+    } else if (mc <= 4) {
+      GATTN_MERGE_BWD(4)
+    } else {
+      GATTN_MERGE_BWD(kMaxCover)
+    }
+#undef GATTN_MERGE_BWD
     return cudaGetLastError();
   }
   const int64_t total = (int64_t)g.B * g.nh * g.N * (g.d / 4);
