@@ -7,8 +7,9 @@
 // window_dim in geom.cuh), so a token's weights cost three table reads per
 // covering tile.  A token's covering tiles (at most kMaxCover, which the host
 // checks with max_covers) are listed with their slot and weight by the lane
-// that owns the token; the data rows are then read by half-warps, one token
-// at a time, as contiguous 256-byte runs.
+// that owns the token, into per-warp shared-memory lists (RowRef); groups of
+// lanes (half- or quarter-warps) then read the listed rows as contiguous
+// runs, several rows at a time with all their loads in flight.
 #pragma once
 
 #include "internal.cuh"
@@ -18,10 +19,11 @@ namespace gattn {
 constexpr int kMaxCover = 8;    // covering tiles a lane lists for its token
 constexpr int kWinMax = 2048;   // table entries (sum of c_a + 2 h_a) kept in shared memory
 
-// One row in a half-warp's list of rows to read (the flattened merge loops):
-// the row's address, its weight and flags (bits 0-4: the lane that owns the
-// row's token; kRowLast: the token's last covering row; kRowBf16: a BF16 row,
-// else FP32; kRowState: the token's state row, read, updated and written back).
+// One row in a lane group's list of rows to read (the flattened merge loops):
+// the row's address (or, in the gradient merge, its slot's element offset),
+// its weight and flags (bits 0-4: the lane that owns the row's token;
+// kRowLast: the token's last covering row; kRowBf16: a BF16 row, else FP32;
+// kRowState: the token's state row, read, updated and written back).
 struct alignas(16) RowRef {
   const void* p;
   float w;
