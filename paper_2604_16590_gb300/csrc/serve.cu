@@ -4,10 +4,12 @@
 // Hann-weighted merge being the per-step propagation of Sec. III-C.
 //
 // Host side (C++): FIFO admission under a slot limit and an HBM budget,
-// per-request device state kept across steps, one descriptor table per engine
-// iteration, retirement with the result copied to host memory, latency
-// statistics.  Device side: one persistent ragged tcgen05 attention launch over
-// the work items of all active requests (sm103_fwd.cu, RAGGED mode) and one
+// per-request device memory from a stream-ordered pool kept across steps, one
+// descriptor table per engine iteration, retirement that keeps the final state
+// in device memory until its client takes it (at once, or on a copy stream
+// while the engine keeps stepping) or releases it, latency statistics.  Device
+// side: one persistent ragged tcgen05 attention launch over the work items of
+// all active requests (sm103_fwd64.cu / sm103_fwd.cu, RAGGED mode) and one
 // merge-and-update launch over all their (head, token) rows (below), both
 // captured once in a CUDA graph that reads the active set from device memory.
 #include <algorithm>
